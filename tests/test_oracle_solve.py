@@ -1,0 +1,180 @@
+"""Pins of the oracle's whole solve: closed-form optima, hand-built points
+for each verdict of the stopping rule (readings P5/P6), the constructed
+infeasible instances with their certificates, and the Grone/Agler and
+fixed-point invariants at convergence (Theorems 1-2, Eq. ADMMForm)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dense, hsde, symbolic
+
+
+def _sym_from_lower(n, r, c, v):
+    M = np.zeros((n, n))
+    M[r, c] = v
+    M[c, r] = v
+    return M
+
+
+def _random_C_on_block_arrow(l, d, h, seed):
+    rng = np.random.default_rng(seed)
+    r, c = [], []
+    for mem in synth.block_arrow_cliques(l, d, h):
+        for b in range(len(mem)):
+            for a in range(b, len(mem)):
+                r.append(mem[a]); c.append(mem[b])
+    key = sorted(set(zip(r, c)), key=lambda t: (t[1], t[0]))
+    r = np.array([k[0] for k in key], np.int32); c = np.array([k[1] for k in key], np.int32)
+    return r, c, rng.standard_normal(len(r))
+
+
+@pytest.mark.parametrize("l,d,h,seed", [(3, 3, 2, 0), (4, 2, 1, 1), (2, 4, 2, 2)])
+def test_trace_one_gives_lambda_min(l, d, h, seed):
+    n = l * d + h
+    r, c, v = _random_C_on_block_arrow(l, d, h, seed)
+    p = synth.trace_one(r, c, v, n)
+    lam_min = np.linalg.eigvalsh(_sym_from_lower(n, r, c, v)).min()
+    res = hsde.HSDE(p).solve(eps=1e-7, max_iter=50000)
+    assert res.status == hsde.SOLVED
+    assert abs(res.info["pobj"] - lam_min) <= 1e-4 * max(1.0, abs(lam_min))
+    assert abs(res.info["dobj"] - lam_min) <= 1e-4 * max(1.0, abs(lam_min))
+
+
+@pytest.mark.parametrize("w", [1.0, -1.0, 2.5, -0.3])
+def test_two_node_maxcut(w):
+    """min <L_w, X> s.t. X_11 = X_22 = 1, X psd: 2w - 2|w| (X_12 = sign(w))."""
+    p = synth.Problem("mc2", 2, 2, np.array([0, 1, 1], np.int32), np.array([0, 0, 1], np.int32),
+                      np.array([w, -w, w]), np.array([0, 1, 2], np.int64), np.array([0, 1], np.int32),
+                      np.array([0, 1], np.int32), np.ones(2), np.ones(2))
+    res = hsde.HSDE(p).solve(eps=1e-8, max_iter=50000)
+    assert res.status == hsde.SOLVED
+    assert abs(res.info["pobj"] - (2 * w - 2 * abs(w))) <= 1e-5
+
+
+def _dense_trace_one(n, seed):
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((n, n)); Cm = 0.5 * (G + G.T)
+    ii, jj = np.tril_indices(n)
+    order = np.lexsort((ii, jj))
+    return synth.trace_one(ii[order], jj[order], Cm[ii[order], jj[order]], n), Cm
+
+
+def test_verdict_solved_on_hand_built_optimum():
+    p, Cm = _dense_trace_one(4, 3)
+    hs = hsde.HSDE(p)
+    lam, V = np.linalg.eigh(Cm)
+    X = np.outer(V[:, 0], V[:, 0]); Z = Cm - lam[0] * np.eye(4)
+    vec = lambda M: np.array([M[i, j] for (i, j) in hs.V.ent])
+    x = vec(X); s = hs.V.H @ x; z = hs.V.H @ vec(Z)
+    u = np.concatenate([x, s, [lam[0]], z, [1.0]])
+    nu = np.concatenate([np.zeros(hs.nF), z, [0.0], np.zeros(hs.nd), [0.0]])
+    info = hs.residuals(u, nu)
+    assert info["pres"] < 1e-12 and info["dres"] < 1e-12 and info["gap"] < 1e-12
+    assert hs.verdict(info, 1e-4) == hsde.SOLVED
+    # a wrong sign on y must not pass
+    u_bad = u.copy(); u_bad[hs.nF + hs.nd] = -lam[0]
+    assert hs.verdict(hs.residuals(u_bad, nu), 1e-4) != hsde.SOLVED
+    # nu = Q u at this point (Eq. ADMMForm), with kappa = 0
+    assert np.allclose(dense.build_Q(hs) @ u, nu, atol=1e-12)
+
+
+def test_verdict_primal_infeasible_closed_form_certificate():
+    """tr X = -1 appended: y = -e_{m+1}, z_k = diag(1/D) on each clique gives
+    A^T y + H^T z = 0 and b^T y = 1."""
+    p = synth.config0(infeasible=True)
+    hs = hsde.HSDE(p)
+    st = hs.V.st
+    y = np.zeros(hs.m); y[-1] = -1.0
+    Dfull = hs.D
+    z = np.zeros(hs.nd)
+    for k, mem in enumerate(st.cliques):
+        c = len(mem)
+        for a in range(c):
+            e = hs.V.fpos[(int(mem[a]), int(mem[a]))]
+            z[hs.V.s_off[k] + a + a * c] = 1.0 / Dfull[e]
+    u = np.concatenate([np.zeros(hs.nF), np.zeros(hs.nd), y, np.zeros(hs.nd), [0.0]])
+    nu = np.concatenate([np.zeros(hs.nF), z, np.zeros(hs.m), np.zeros(hs.nd), [1.0]])
+    info = hs.residuals(u, nu)
+    assert info["bty"] == pytest.approx(1.0)
+    assert info["pinf_ratio"] < 1e-14
+    assert hs.verdict(info, 1e-4) == hsde.PRIMAL_INFEASIBLE
+
+
+def test_verdict_dual_infeasible_hand_built_direction():
+    base = synth.block_arrow(3, 3, 2, 5, synth.rng_for(9), kappa=50.0, assign="roundrobin")
+    p = synth.make_dual_infeasible(base, np.random.default_rng(1))
+    hs = hsde.HSDE(p)
+    Dr, Dc, Dv = p.meta["Dd"]
+    Dm = _sym_from_lower(p.n, Dr, Dc, Dv)
+    x = np.array([Dm[i, j] for (i, j) in hs.V.ent]); s = hs.V.H @ x
+    u = np.concatenate([x, s, np.zeros(hs.m), np.zeros(hs.nd), [0.0]])
+    nu = np.concatenate([np.zeros(hs.nF), np.zeros(hs.nd), np.zeros(hs.m), np.zeros(hs.nd), [1.0]])
+    info = hs.residuals(u, nu)
+    assert info["ctx"] == pytest.approx(-1.0)
+    assert info["dinf_ratio"] < 1e-12
+    assert hs.verdict(info, 1e-4) == hsde.DUAL_INFEASIBLE
+
+
+def test_config0_solution_invariants():
+    p = synth.config0()
+    hs = hsde.HSDE(p)
+    res = hs.solve(eps=1e-6, max_iter=20000)
+    assert res.status == hsde.SOLVED
+    X, y, Z = hs.solution(res.u, res.nu)
+    st = hs.V.st
+    scale = np.abs(X).max()
+    # Grone (Theorem 1): every clique block of X psd
+    for mem in st.cliques:
+        Xk = np.array([[X[hs.V.fpos[(int(a), int(b))]] for b in mem] for a in mem])
+        assert np.linalg.eigvalsh(Xk).min() >= -1e-5 * scale
+    # Agler (Theorem 2): Z = sum_k E_k^T Z_k E_k with psd Z_k (z is psd exactly)
+    z = res.nu[hs.nF:hs.nF + hs.nd] / res.u[-1]
+    for k, mem in enumerate(st.cliques):
+        c = len(mem)
+        Zk = z[hs.V.s_off[k]:hs.V.s_off[k] + c * c].reshape((c, c), order="F")
+        assert np.linalg.eigvalsh(0.5 * (Zk + Zk.T)).min() >= -1e-9 * np.abs(Zk).max()
+    # C - sum_i y_i A_i - Z ~ 0 on the pattern
+    r = hs.V.c - hs.V.A.T @ y - Z
+    assert np.linalg.norm(r) <= 1e-5 * (1 + np.linalg.norm(hs.V.c))
+    # complementarity <s, z> ~ 0 and tau*kappa = 0
+    s = res.u[hs.nF:hs.nF + hs.nd]
+    assert abs(s @ res.nu[hs.nF:hs.nF + hs.nd]) <= 1e-6 * np.linalg.norm(s) * np.linalg.norm(res.nu[hs.nF:hs.nF + hs.nd]) + 1e-12
+    assert res.u[-1] * res.nu[-1] == 0.0
+    # fixed point of Eq. ADMMForm: nu ~ Q u
+    Q = dense.build_Q(hs)
+    assert np.linalg.norm(Q @ res.u - res.nu) <= 1e-4 * np.linalg.norm(res.u)
+
+
+def test_primal_infeasible_instance_gives_valid_certificate():
+    p = synth.config0(infeasible=True)
+    hs = hsde.HSDE(p)
+    res = hs.solve()
+    assert res.status == hsde.PRIMAL_INFEASIBLE
+    y, Z = hs.certificate(res.u, res.nu, res.status)
+    assert hs.V.b @ y == pytest.approx(1.0)
+    assert np.linalg.norm(hs.V.A.T @ y + Z) <= 1e-4
+    z = res.nu[hs.nF:hs.nF + hs.nd]
+    for k, mem in enumerate(hs.V.st.cliques):
+        c = len(mem)
+        Zk = z[hs.V.s_off[k]:hs.V.s_off[k] + c * c].reshape((c, c), order="F")
+        assert np.linalg.eigvalsh(0.5 * (Zk + Zk.T)).min() >= -1e-9 * np.abs(Zk).max()
+
+
+def test_dual_infeasible_instance_gives_valid_certificate():
+    base = synth.block_arrow(4, 4, 2, 8, synth.rng_for(8), kappa=100.0, assign="roundrobin")
+    p = synth.make_dual_infeasible(base, np.random.default_rng(2))
+    hs = hsde.HSDE(p)
+    res = hs.solve(max_iter=20000)
+    assert res.status == hsde.DUAL_INFEASIBLE
+    x, s = hs.certificate(res.u, res.nu, res.status)
+    assert hs.V.c @ x == pytest.approx(-1.0)
+    assert np.sqrt(np.sum((hs.V.A @ x) ** 2) + np.sum((hs.V.H @ x - s) ** 2)) <= 1e-4
+    for k, mem in enumerate(hs.V.st.cliques):
+        c = len(mem)
+        Sk = s[hs.V.s_off[k]:hs.V.s_off[k] + c * c].reshape((c, c), order="F")
+        assert np.linalg.eigvalsh(0.5 * (Sk + Sk.T)).min() >= -1e-9 * max(1e-30, np.abs(Sk).max())
+
+
+def test_feasible_config0_reaches_tolerance():
+    res = hsde.HSDE(synth.config0()).solve()
+    assert res.status == hsde.SOLVED and res.iterations < 2000
