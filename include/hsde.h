@@ -1,0 +1,214 @@
+/*
+ * hsde.h -- C-ABI of libhsde: ADMM for the homogeneous self-dual embedding of
+ * chordally sparse SDPs on one GB300 (sm_103a).
+ *
+ * Method: Zheng, Fantuzzi, Papachristodoulou, Goulart, Wynn, "Fast ADMM for
+ * homogeneous self-dual embedding of sparse SDPs" (arXiv:1611.01828).
+ *
+ * Problem (Section 3, Eqs. PrimalSDP / DualSDP):
+ *     min <C, X>  s.t.  <A_i, X> = b_i (i = 1..m),  X psd
+ *     max <b, y>  s.t.  sum_i y_i A_i + Z = C,       Z psd
+ * C and every A_i are symmetric n x n matrices given by their LOWER triangle
+ * (row >= col, diagonal included where nonzero) in COO form.
+ *
+ * Layouts used by the queries (all 0-based, int32 indices, FP64 values):
+ *   pattern   the chordal extension E' of the aggregate sparsity pattern,
+ *             lower triangle in CSC order (by column, then row): N entries.
+ *   x, X, Z   one value per pattern entry (the lower triangle of a symmetric
+ *             matrix restricted to E').
+ *   cliques   p maximal cliques C_1..C_p of E', members ascending.
+ *   packed    clique block k stored as its lower triangle column-major:
+ *             (a,b) for b = 0..c_k-1, a = b..c_k-1; blocks concatenated
+ *             (P = sum_k c_k (c_k+1)/2 values).
+ *   state     [x (N) | s (P) | y (m) | v (P) | tau | z (P) | kappa]
+ *             = (x, s, y, v, tau) of u and (z, kappa) of nu (Section 3.2;
+ *             the free-cone parts h, r, w of nu are identically zero from the
+ *             standard start, Eq. Step3, and are not stored).
+ * Inner products and norms are those of the full column-stack vec: entries
+ * off the diagonal count twice.
+ *
+ * Errors: every int-returning call returns HSDE_OK (0) or a negative code;
+ * hsde_last_error() gives a message for the calling thread.  No call throws
+ * across the ABI.  A handle is not thread-safe: one host thread per handle.
+ */
+#ifndef HSDE_H
+#define HSDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HSDE_API __attribute__((visibility("default")))
+#else
+#define HSDE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define HSDE_OK        0
+#define HSDE_EINVAL   (-1)   /* invalid argument or problem data            */
+#define HSDE_ENOMEM   (-2)   /* host or device allocation failed            */
+#define HSDE_ECUDA    (-3)   /* CUDA runtime error (no device, launch, ...)  */
+#define HSDE_ESTATE   (-4)   /* query does not match the instance's verdict */
+#define HSDE_ERANGE   (-5)   /* size beyond what this build supports        */
+
+/* per-instance iteration status (readings of the paper's stopping rule) */
+#define HSDE_RUNNING            0
+#define HSDE_SOLVED             1
+#define HSDE_PRIMAL_INFEASIBLE  2
+#define HSDE_DUAL_INFEASIBLE    3
+#define HSDE_MAX_ITER           4
+#define HSDE_NUMERICAL_ERROR    5
+
+/* arithmetic of the clique arrays and cone projections */
+#define HSDE_FP64   0   /* FP64 everywhere                                      */
+#define HSDE_MIXED  1   /* FP32 clique arrays, gather/scatter and eigensolves;
+                           FP64 for x, y, A, the cached factor, solves and all
+                           reductions                                           */
+
+typedef struct hsde_problem {
+    int32_t n;                 /* matrix size, > 0                               */
+    int32_t m;                 /* number of equality constraints, >= 0           */
+    int64_t C_nnz;
+    const int32_t* C_row;      /* [C_nnz], row >= col                             */
+    const int32_t* C_col;
+    const double*  C_val;
+    const int64_t* A_ptr;      /* [m+1]: entries of A_i are A_ptr[i]..A_ptr[i+1]-1 */
+    const int32_t* A_row;      /* [A_ptr[m]], row >= col                          */
+    const int32_t* A_col;
+    const double*  A_val;
+    const double*  b;          /* [m]                                             */
+    int64_t pattern_nnz;       /* optional extra lower-triangle pattern; may be 0 */
+    const int32_t* pattern_row;
+    const int32_t* pattern_col;
+} hsde_problem;
+
+typedef struct hsde_options {
+    double  eps_tol;      /* stopping tolerance, default 1e-4 (Section 5)          */
+    int32_t max_iter;     /* default 2000 (Section 5)                              */
+    int32_t check_every;  /* test the stopping rule every k-th iteration, default 1 */
+    int32_t precision;    /* HSDE_FP64 or HSDE_MIXED, default HSDE_MIXED           */
+    int32_t device;       /* CUDA device ordinal, default 0                        */
+    void*   cuda_stream;  /* cudaStream_t to run on; NULL: the library creates one */
+    int32_t jacobi_max_sweeps;   /* 0: default (FP32 12, FP64 16)                */
+    int32_t use_graph;    /* 1 (default): replay iterations through a CUDA graph   */
+    double  jacobi_tol;   /* 0: default relative off-diagonal tolerance           */
+} hsde_options;
+
+typedef struct hsde_sizes {
+    int32_t n, m, p;      /* matrix size, constraints, cliques                    */
+    int32_t c_max;        /* largest clique                                       */
+    int64_t N;            /* pattern entries (lower, diagonal included)          */
+    int64_t P;            /* packed clique storage sum_k c_k(c_k+1)/2             */
+    int64_t n_d;          /* sum_k c_k^2 (Section 3.2)                            */
+    int64_t state_len;    /* N + 3P + m + 2                                       */
+    int32_t S_dense;      /* 1 if I + A Delta^{-1} A^T is stored dense, 0 if diagonal */
+    int32_t _pad;
+} hsde_sizes;
+
+typedef struct hsde_info {
+    int32_t status;       /* HSDE_RUNNING ...                                     */
+    int32_t iterations;   /* ADMM iterations performed on this instance           */
+    double  pres, dres, gap;      /* at the last check (readings P5)             */
+    double  pobj, dobj;           /* c^T x / tau, b^T y / tau                     */
+    double  tau, kappa;
+    double  pinf_ratio, dinf_ratio;  /* certificate ratios (reading P6)          */
+    double  setup_ms;     /* host + device setup ("Pre- time" of Tables 2-4)    */
+    double  iterate_ms;   /* wall time spent inside hsde_iterate               */
+} hsde_info;
+
+typedef struct hsde_handle hsde_handle;
+typedef struct hsde_symbolic hsde_symbolic;
+
+/* Fill *o with the defaults listed above. */
+HSDE_API void hsde_default_options(hsde_options* o);
+
+/* Message of the last failing call on this thread ("" if none). */
+HSDE_API const char* hsde_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Host-only symbolic analysis (Section 2.1-2.2; no GPU is touched).
+ * Aggregate pattern supp(C) U supp(A_i) U diag U extra pattern, chordal
+ * extension by exact minimum degree (ties to the smallest vertex index),
+ * maximal cliques ordered by the elimination step of their defining vertex,
+ * members ascending; H_k as the gather map, D = H^T H (Section 4.3).
+ * Inputs are copied; *out must be released with hsde_symbolic_free.
+ * Errors: HSDE_EINVAL for out-of-range or upper-triangle indices, duplicate
+ * entries inside C or inside one A_i, non-finite values, n <= 0, m < 0.
+ * ---------------------------------------------------------------------- */
+HSDE_API int  hsde_analyze(const hsde_problem* P, hsde_symbolic** out);
+HSDE_API int  hsde_symbolic_sizes(const hsde_symbolic* s, hsde_sizes* out);
+/* Any output pointer may be NULL.  Sizes: order[n] (vertex eliminated at
+ * each step), clique_ptr[p+1], clique_idx[sum c_k], pat_colptr[n+1],
+ * pat_row[N], gather[P] (packed clique entry -> pattern position), D[N]. */
+HSDE_API int  hsde_symbolic_get(const hsde_symbolic* s, int32_t* order, int32_t* clique_ptr,
+                       int32_t* clique_idx, int32_t* pat_colptr, int32_t* pat_row,
+                       int32_t* gather, int32_t* D);
+HSDE_API void hsde_symbolic_free(hsde_symbolic* s);
+
+/* ------------------------------------------------------------------------
+ * Setup (Section 4.2-4.3 "cached before starting the iterations"): symbolic
+ * analysis, upload, S = I + A Delta^{-1} A^T with Delta = I + D/2 and its
+ * FP64 inverse (diagonal when no two constraints share a pattern entry),
+ * the cached M^{-1} zeta and 1 + zeta^T M^{-1} zeta, and the starting point
+ * u0 = (0,0,0,0,1), nu0 = (0,0,0,0,1).  All inputs are copied; the caller may
+ * free them on return.  *out is NULL on error.  hsde_setup_batch sets up B
+ * independent instances behind one handle; they iterate in the same launches
+ * and each stops on its own verdict.
+ * Errors: HSDE_EINVAL (see hsde_analyze; also B <= 0, bad options),
+ * HSDE_ENOMEM, HSDE_ECUDA (no device / CUDA failure), HSDE_ERANGE (a clique
+ * larger than this build's eigensolvers or totals beyond int32 indexing).
+ * ---------------------------------------------------------------------- */
+HSDE_API int  hsde_setup(const hsde_problem* P, const hsde_options* O, hsde_handle** out);
+HSDE_API int  hsde_setup_batch(const hsde_problem* P, int32_t B, const hsde_options* O,
+                      hsde_handle** out);
+
+/* Run up to k more ADMM iterations (Eqs. Step1-Step3) on every instance
+ * that is still HSDE_RUNNING; an instance freezes on its verdict.  Work is
+ * enqueued on the handle's stream.  If status_out is non-NULL the call
+ * waits for the work and writes one status per instance (B entries). */
+HSDE_API int  hsde_iterate(hsde_handle* h, int32_t k, int32_t* status_out);
+/* Wait for all work enqueued on the handle's stream. */
+HSDE_API int  hsde_sync(hsde_handle* h);
+
+HSDE_API int  hsde_num_instances(const hsde_handle* h);
+HSDE_API int  hsde_get_sizes(const hsde_handle* h, int32_t i, hsde_sizes* out);
+/* Same layout as hsde_symbolic_get, for instance i of a handle. */
+HSDE_API int  hsde_get_structure(const hsde_handle* h, int32_t i, int32_t* order, int32_t* clique_ptr,
+                        int32_t* clique_idx, int32_t* pat_colptr, int32_t* pat_row,
+                        int32_t* gather, int32_t* D);
+HSDE_API int  hsde_get_info(hsde_handle* h, int32_t i, hsde_info* out);
+
+/* Checkpoint / resume: copy the state (layout above, state_len doubles) of
+ * instance i to or from host memory.  In HSDE_MIXED mode s, v, z are rounded
+ * to FP32 on set.  set_state also resets the instance to HSDE_RUNNING with
+ * the given iteration counter. */
+HSDE_API int  hsde_get_state(hsde_handle* h, int32_t i, double* state);
+HSDE_API int  hsde_set_state(hsde_handle* h, int32_t i, const double* state, int32_t iterations);
+
+/* Solution of a SOLVED instance (reading P5): X = x/tau and Z = H^T z / tau
+ * (the Agler sum of the clique blocks, Theorem 2) as N pattern values, y/tau,
+ * and the objectives.  Any output pointer may be NULL.  HSDE_ESTATE if the
+ * instance is not SOLVED. */
+HSDE_API int  hsde_get_solution(hsde_handle* h, int32_t i, double* X, double* y, double* Z,
+                       double* pobj, double* dobj);
+/* Certificate of an infeasible instance (reading P6).  PRIMAL_INFEASIBLE:
+ * y/(b^T y) (m values) and Z = H^T z/(b^T y) (N values), with
+ * A^T y + Z ~ 0, b^T y = 1 and every clique block of z psd.
+ * DUAL_INFEASIBLE: X = x/(-c^T x) (N values) with A(X) ~ 0, <C, X> = -1 and
+ * every clique block of X psd; y and Z are left untouched.  HSDE_ESTATE if
+ * the verdict does not match the certificate asked for (kind =
+ * HSDE_PRIMAL_INFEASIBLE or HSDE_DUAL_INFEASIBLE). */
+HSDE_API int  hsde_get_certificate(hsde_handle* h, int32_t i, int32_t kind, double* y, double* Z,
+                          double* X);
+
+/* Free all device and host memory of the handle.  NULL-safe. */
+HSDE_API void hsde_destroy(hsde_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HSDE_H */

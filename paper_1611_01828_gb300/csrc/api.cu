@@ -1,0 +1,841 @@
+// C-ABI of libhsde (include/hsde.h): setup, iterate, queries.
+//
+// Device memory: one arena per handle (cudaMalloc once at setup), carved
+// into the concatenated per-instance arrays; nothing is allocated while
+// iterating.  One iteration is a fixed launch sequence (affine step, eta,
+// clique cone projections in parallel graph branches, stopping rule) that is
+// captured once into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace hsde;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            return fail(HSDE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        }                                                                               \
+    } while (0)
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(
+               std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Host preparation of one instance.
+struct HostPrep {
+    Symbolic S;
+    int32_t n = 0, m = 0, cmax = 0;
+    std::vector<double> cvec, inv_delta;
+    std::vector<uint8_t> diag;
+    std::vector<int32_t> sc_ptr, sc_idx;      // local packed indices
+    std::vector<int32_t> A_ptr, A_col;        // local entry indices
+    std::vector<double> A_val;                // off-diagonal weight 2 applied
+    std::vector<int32_t> At_ptr, At_col;      // local constraint indices
+    std::vector<double> At_val;
+    std::vector<double> b;
+    bool dense = false;
+    std::vector<double> Sdense;               // m*m (dense case)
+    std::vector<double> Sdiag_inv;            // m (diagonal case)
+};
+
+int prepare(const hsde_problem* P, HostPrep& H, std::string& err) {
+    int rc = build_symbolic(P, H.S, err);
+    if (rc != HSDE_OK) return rc;
+    const Symbolic& S = H.S;
+    H.n = P->n;
+    H.m = P->m;
+    const int64_t N = S.N();
+    const int32_t p = S.p();
+    H.cmax = 0;
+    for (int32_t k = 0; k < p; ++k) H.cmax = std::max(H.cmax, S.clique_ptr[k + 1] - S.clique_ptr[k]);
+    H.diag.resize(N);
+    H.inv_delta.resize(N);
+    for (int64_t e = 0; e < N; ++e) {
+        H.diag[e] = (S.pat_row[e] == S.pat_col[e]) ? 1 : 0;
+        H.inv_delta[e] = 1.0 / (1.0 + 0.5 * (double)S.D[e]);
+    }
+    H.cvec.assign(N, 0.0);
+    for (int64_t k = 0; k < P->C_nnz; ++k) {
+        const int32_t e = S.pos(P->C_row[k], P->C_col[k]);
+        H.cvec[e] = P->C_val[k];
+    }
+    // H^T as CSR over entries (packed positions ascending within an entry)
+    H.sc_ptr.assign(N + 1, 0);
+    for (int32_t e : S.gather) H.sc_ptr[e + 1] += 1;
+    for (int64_t e = 0; e < N; ++e) H.sc_ptr[e + 1] += H.sc_ptr[e];
+    H.sc_idx.resize(S.gather.size());
+    {
+        std::vector<int32_t> fill(H.sc_ptr.begin(), H.sc_ptr.end() - 1);
+        for (size_t j = 0; j < S.gather.size(); ++j) H.sc_idx[fill[S.gather[j]]++] = (int32_t)j;
+    }
+    // A (rows = constraints) with full-vec weights, and A^T (rows = entries)
+    const int32_t m = P->m;
+    H.A_ptr.assign(m + 1, 0);
+    const int64_t a0 = m > 0 ? P->A_ptr[0] : 0;
+    std::vector<std::pair<int32_t, double>> row;
+    for (int32_t i = 0; i < m; ++i) {
+        row.clear();
+        for (int64_t k = P->A_ptr[i] - a0; k < P->A_ptr[i + 1] - a0; ++k) {
+            const int32_t r = P->A_row[k], c = P->A_col[k];
+            const int32_t e = S.pos(r, c);
+            row.push_back({e, P->A_val[k]});
+        }
+        std::sort(row.begin(), row.end(),
+                  [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
+                      return a.first < b.first;
+                  });
+        for (auto& pr : row) {
+            H.A_col.push_back(pr.first);
+            H.A_val.push_back(H.diag[pr.first] ? pr.second : 2.0 * pr.second);
+        }
+        H.A_ptr[i + 1] = (int32_t)H.A_col.size();
+    }
+    H.At_ptr.assign(N + 1, 0);
+    for (int32_t e : H.A_col) H.At_ptr[e + 1] += 1;
+    for (int64_t e = 0; e < N; ++e) H.At_ptr[e + 1] += H.At_ptr[e];
+    H.At_col.resize(H.A_col.size());
+    H.At_val.resize(H.A_col.size());
+    int32_t max_at = 0;
+    {
+        std::vector<int32_t> fill(H.At_ptr.begin(), H.At_ptr.end() - 1);
+        for (int32_t i = 0; i < m; ++i)
+            for (int32_t j = H.A_ptr[i]; j < H.A_ptr[i + 1]; ++j) {
+                const int32_t e = H.A_col[j];
+                const double raw = H.diag[e] ? H.A_val[j] : 0.5 * H.A_val[j];
+                H.At_col[fill[e]] = i;
+                H.At_val[fill[e]] = raw;
+                fill[e]++;
+            }
+        for (int64_t e = 0; e < N; ++e) max_at = std::max(max_at, H.At_ptr[e + 1] - H.At_ptr[e]);
+    }
+    H.b.assign(P->b, P->b + m);
+    // S = I + A Delta^{-1} A^T (full-vec inner products); diagonal if no two
+    // constraints share a pattern entry.
+    H.dense = max_at > 1;
+    if (!H.dense) {
+        std::vector<double> d(m, 1.0);
+        for (int64_t e = 0; e < N; ++e)
+            for (int32_t j = H.At_ptr[e]; j < H.At_ptr[e + 1]; ++j) {
+                const double a = H.At_val[j];
+                d[H.At_col[j]] += (H.diag[e] ? 1.0 : 2.0) * a * a * H.inv_delta[e];
+            }
+        H.Sdiag_inv.resize(m);
+        for (int32_t i = 0; i < m; ++i) H.Sdiag_inv[i] = 1.0 / d[i];
+    } else {
+        H.Sdense.assign((size_t)m * m, 0.0);
+        double* Sm = H.Sdense.data();
+        for (int32_t i = 0; i < m; ++i) Sm[(size_t)i * m + i] = 1.0;
+        for (int64_t e = 0; e < N; ++e) {
+            const int32_t j0 = H.At_ptr[e], j1 = H.At_ptr[e + 1];
+            const double w = (H.diag[e] ? 1.0 : 2.0) * H.inv_delta[e];
+            for (int32_t ja = j0; ja < j1; ++ja) {
+                const double wa = w * H.At_val[ja];
+                double* Srow = Sm + (size_t)H.At_col[ja] * m;
+                for (int32_t jb = j0; jb <= ja; ++jb) Srow[H.At_col[jb]] += wa * H.At_val[jb];
+            }
+        }
+        for (int32_t i = 0; i < m; ++i)
+            for (int32_t j = 0; j < i; ++j) Sm[(size_t)j * m + i] = Sm[(size_t)i * m + j];
+    }
+    return HSDE_OK;
+}
+
+int bucket_of(int c) {
+    if (c <= 8) return 8;
+    if (c <= 16) return 16;
+    if (c <= 32) return 32;
+    if (c <= 64) return 64;
+    return 128;
+}
+
+}  // namespace
+
+struct hsde_symbolic {
+    Symbolic S;
+};
+
+struct hsde_handle {
+    int32_t B = 0;
+    hsde_options opt{};
+    bool mixed = true;
+    int device = 0;
+    std::vector<HostPrep> prep;
+    std::vector<int64_t> x_off, p_off;
+    std::vector<int32_t> m_off;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    cudaStream_t side[6] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[6] = {};
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    DevView V{};
+    std::vector<Bucket> buckets;
+    InstDev* host_inst = nullptr;       // pinned mirror
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double setup_ms = 0, iterate_ms = 0;
+    int max_sweeps = 12;
+    double jtol = 1e-6;
+};
+
+namespace {
+
+int enqueue_iteration(hsde_handle* h) {
+    const DevView& V = h->V;
+    launch_rhs(V, h->mixed, Mode::Iter, h->st);
+    launch_spmv_A(V, Mode::Iter, h->st);
+    launch_solve(V, Mode::Iter, h->st);
+    launch_spmv_At(V, Mode::Iter, h->st);
+    launch_eta(V, h->st);
+    // fork: every clique bucket on its own branch, x update on the main branch
+    CK(cudaEventRecord(h->ev_fork, h->st));
+    for (size_t i = 0; i < h->buckets.size(); ++i) {
+        CK(cudaStreamWaitEvent(h->side[i], h->ev_fork, 0));
+        int rc = launch_cone(V, h->buckets[i], h->mixed, h->max_sweeps, h->jtol, h->side[i]);
+        if (rc != HSDE_OK) return fail(rc, "cone launch failed");
+        CK(cudaEventRecord(h->ev_join[i], h->side[i]));
+    }
+    launch_xupd(V, h->st);
+    for (size_t i = 0; i < h->buckets.size(); ++i) CK(cudaStreamWaitEvent(h->st, h->ev_join[i], 0));
+    launch_check(V, h->mixed, h->st);
+    launch_verdict(V, h->st);
+    CK(cudaGetLastError());
+    return HSDE_OK;
+}
+
+int sync_inst(hsde_handle* h) {
+    CK(cudaMemcpyAsync(h->host_inst, h->V.inst, sizeof(InstDev) * h->B, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return HSDE_OK;
+}
+
+void free_handle(hsde_handle* h) {
+    if (!h) return;
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->st) cudaStreamSynchronize(h->st);
+    for (auto& s : h->side) if (s) cudaStreamDestroy(s);
+    for (auto& e : h->ev_join) if (e) cudaEventDestroy(e);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->arena) cudaFree(h->arena);
+    if (h->host_inst) cudaFreeHost(h->host_inst);
+    if (h->own_stream && h->st) cudaStreamDestroy(h->st);
+    delete h;
+}
+
+struct Carver {
+    size_t off = 0;
+    template <typename T>
+    size_t take(size_t count) {
+        off = (off + 255) / 256 * 256;
+        const size_t o = off;
+        off += count * sizeof(T);
+        return o;
+    }
+};
+
+template <typename T>
+int upload(void* dst, const std::vector<T>& v, cudaStream_t st) {
+    if (v.empty()) return HSDE_OK;
+    CK(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    return HSDE_OK;
+}
+
+int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_handle** out) {
+    const double t0 = now_ms();
+    if (!out) return fail(HSDE_EINVAL, "out is null");
+    *out = nullptr;
+    if (!P || B <= 0) return fail(HSDE_EINVAL, "null problem or B <= 0");
+    hsde_options opt;
+    hsde_default_options(&opt);
+    if (O) opt = *O;
+    if (!(opt.eps_tol > 0) || opt.max_iter <= 0 || opt.check_every <= 0 ||
+        (opt.precision != HSDE_FP64 && opt.precision != HSDE_MIXED) || opt.jacobi_max_sweeps < 0 ||
+        opt.jacobi_tol < 0)
+        return fail(HSDE_EINVAL, "invalid options");
+
+    auto* h = new hsde_handle();
+    struct Guard {
+        hsde_handle*& h;
+        ~Guard() { if (h) free_handle(h); }
+    } guard{h};
+    h->B = B;
+    h->opt = opt;
+    h->mixed = opt.precision == HSDE_MIXED;
+    h->device = opt.device;
+    h->max_sweeps = opt.jacobi_max_sweeps > 0 ? opt.jacobi_max_sweeps : (h->mixed ? 12 : 16);
+    h->jtol = opt.jacobi_tol > 0 ? opt.jacobi_tol : (h->mixed ? 1e-6 : 1e-14);
+
+    // ---- host analysis and preparation ----
+    h->prep.resize(B);
+    std::string err;
+    for (int32_t b = 0; b < B; ++b) {
+        int rc = prepare(&P[b], h->prep[b], err);
+        if (rc != HSDE_OK) return fail(rc, "instance " + std::to_string(b) + ": " + err);
+        const int lim = h->mixed ? 128 : 64;
+        if (h->prep[b].cmax > lim)
+            return fail(HSDE_ERANGE, "instance " + std::to_string(b) + ": clique of size " +
+                                          std::to_string(h->prep[b].cmax) + " exceeds " +
+                                          std::to_string(lim));
+    }
+    // ---- totals and offsets ----
+    int64_t Ntot = 0, Ptot = 0, nnzA = 0, Mtot = 0, ncl = 0, ntiles = 0, sinv = 0, scn = 0;
+    h->x_off.resize(B); h->p_off.resize(B); h->m_off.resize(B);
+    std::vector<InstDev> inst(B);
+    for (int32_t b = 0; b < B; ++b) {
+        const HostPrep& H = h->prep[b];
+        InstDev& I = inst[b];
+        std::memset(&I, 0, sizeof(I));
+        I.x_off = Ntot; I.N = H.S.N();
+        I.p_off = Ptot; I.P = H.S.P();
+        I.m_off = (int32_t)Mtot; I.m = H.m;
+        I.cl_begin = (int32_t)ncl; I.cl_end = (int32_t)(ncl + H.S.p());
+        I.tile_begin = (int32_t)ntiles;
+        ntiles += (I.N + TILE_N - 1) / TILE_N;
+        I.tile_end = (int32_t)ntiles;
+        I.dense = H.dense ? 1 : 0;
+        I.sinv_off = sinv;
+        if (H.dense) sinv += (int64_t)H.m * H.m;
+        I.status = HSDE_RUNNING;
+        I.tau = 1.0; I.kappa = 1.0;
+        h->x_off[b] = Ntot; h->p_off[b] = Ptot; h->m_off[b] = (int32_t)Mtot;
+        Ntot += I.N; Ptot += I.P; Mtot += H.m; ncl += H.S.p(); nnzA += (int64_t)H.A_col.size();
+        scn += (int64_t)H.sc_idx.size();
+    }
+    const int64_t LIM = (int64_t)1 << 31;
+    if (Ntot >= LIM || Ptot >= LIM || nnzA >= LIM || Mtot >= LIM || scn >= LIM)
+        return fail(HSDE_ERANGE, "problem totals exceed int32 indexing");
+
+    // ---- device, streams ----
+    CK(cudaSetDevice(h->device));
+    if (opt.cuda_stream) {
+        h->st = reinterpret_cast<cudaStream_t>(opt.cuda_stream);
+    } else {
+        CK(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    for (auto& s : h->side) CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    for (auto& e : h->ev_join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaMallocHost(&h->host_inst, sizeof(InstDev) * B));
+
+    // ---- arena layout ----
+    const size_t Tsz = h->mixed ? sizeof(float) : sizeof(double);
+    Carver cv;
+    const size_t o_x = cv.take<double>(Ntot), o_c = cv.take<double>(Ntot), o_id = cv.take<double>(Ntot),
+                 o_xp = cv.take<double>(Ntot), o_f = cv.take<double>(Ntot), o_xw = cv.take<double>(Ntot),
+                 o_diag = cv.take<uint8_t>(Ntot), o_scp = cv.take<int32_t>(Ntot + 1),
+                 o_sci = cv.take<int32_t>(scn), o_atp = cv.take<int32_t>(Ntot + 1),
+                 o_atc = cv.take<int32_t>(nnzA), o_atv = cv.take<double>(nnzA);
+    const size_t o_y = cv.take<double>(Mtot), o_b = cv.take<double>(Mtot), o_yp = cv.take<double>(Mtot),
+                 o_q = cv.take<double>(Mtot), o_yw = cv.take<double>(Mtot),
+                 o_ap = cv.take<int32_t>(Mtot + 1), o_ac = cv.take<int32_t>(nnzA),
+                 o_av = cv.take<double>(nnzA), o_ri = cv.take<int32_t>(Mtot),
+                 o_sd = cv.take<double>(Mtot), o_sinv = cv.take<double>(sinv);
+    size_t o_s = cv.take<char>(Ptot * Tsz), o_z = cv.take<char>(Ptot * Tsz), o_v = cv.take<char>(Ptot * Tsz);
+    const size_t o_g = cv.take<int32_t>(Ptot), o_clo = cv.take<int32_t>(ncl), o_cls = cv.take<int32_t>(ncl),
+                 o_cli = cv.take<int32_t>(ncl), o_inst = cv.take<InstDev>(B), o_tiles = cv.take<int4>(ntiles),
+                 o_part = cv.take<double>(ntiles * KPART), o_clp = cv.take<double>(ncl),
+                 o_rowp = cv.take<double>(Mtot * 3), o_blist = cv.take<int32_t>(ncl);
+    // Gauss-Jordan scratch and per-dense-instance tables
+    int ndense = 0;
+    int32_t mmax = 0;
+    for (int32_t b = 0; b < B; ++b)
+        if (h->prep[b].dense) { ++ndense; mmax = std::max(mmax, h->prep[b].m); }
+    const size_t o_gjrow = cv.take<double>(Mtot), o_gjcol = cv.take<double>(Mtot),
+                 o_gjoff = cv.take<int64_t>(ndense), o_gjm = cv.take<int32_t>(ndense),
+                 o_gjb = cv.take<int64_t>(ndense);
+    h->arena_bytes = cv.off + 256;
+    CK(cudaMalloc(&h->arena, h->arena_bytes));
+    char* ar = reinterpret_cast<char*>(h->arena);
+    DevView& V = h->V;
+    V.B = B; V.Ntot = Ntot; V.Ptot = Ptot; V.Mtot = (int32_t)Mtot; V.ntiles = (int32_t)ntiles;
+    V.ncl = (int32_t)ncl;
+    V.x = (double*)(ar + o_x); V.c = (const double*)(ar + o_c); V.inv_delta = (const double*)(ar + o_id);
+    V.xp = (double*)(ar + o_xp); V.f = (double*)(ar + o_f); V.xw = (double*)(ar + o_xw);
+    V.diag = (const uint8_t*)(ar + o_diag); V.sc_ptr = (const int32_t*)(ar + o_scp);
+    V.sc_idx = (const int32_t*)(ar + o_sci); V.At_ptr = (const int32_t*)(ar + o_atp);
+    V.At_col = (const int32_t*)(ar + o_atc); V.At_val = (const double*)(ar + o_atv);
+    V.y = (double*)(ar + o_y); V.b = (const double*)(ar + o_b); V.yp = (double*)(ar + o_yp);
+    V.q = (double*)(ar + o_q); V.yw = (double*)(ar + o_yw); V.A_ptr = (const int32_t*)(ar + o_ap);
+    V.A_col = (const int32_t*)(ar + o_ac); V.A_val = (const double*)(ar + o_av);
+    V.row_inst = (const int32_t*)(ar + o_ri); V.sdiag = (const double*)(ar + o_sd);
+    V.sinv = (double*)(ar + o_sinv);
+    V.s = ar + o_s; V.z = ar + o_z; V.v = ar + o_v;
+    V.gmap = (const int32_t*)(ar + o_g); V.cl_off = (const int32_t*)(ar + o_clo);
+    V.cl_size = (const int32_t*)(ar + o_cls); V.cl_inst = (const int32_t*)(ar + o_cli);
+    V.inst = (InstDev*)(ar + o_inst); V.tiles = (const int4*)(ar + o_tiles);
+    V.part = (double*)(ar + o_part); V.cl_part = (double*)(ar + o_clp); V.row_part = (double*)(ar + o_rowp);
+    V.eps = opt.eps_tol; V.max_iter = opt.max_iter; V.check_every = opt.check_every;
+
+    // ---- concatenated host buffers with absolute indices ----
+    std::vector<double> hc, hid, hAtv, hb, hAv, hsd;
+    std::vector<uint8_t> hdiag;
+    std::vector<int32_t> hscp, hsci, hatp, hatc, hap, hac, hri, hg, hclo, hcls, hcli;
+    std::vector<int4> htiles;
+    hc.reserve(Ntot); hid.reserve(Ntot); hdiag.reserve(Ntot);
+    hscp.reserve(Ntot + 1); hatp.reserve(Ntot + 1); hap.reserve(Mtot + 1);
+    hsd.assign(Mtot, 0.0);
+    for (int32_t b = 0; b < B; ++b) {
+        const HostPrep& H = h->prep[b];
+        const int64_t xo = h->x_off[b], po = h->p_off[b];
+        const int32_t mo = h->m_off[b];
+        hc.insert(hc.end(), H.cvec.begin(), H.cvec.end());
+        hid.insert(hid.end(), H.inv_delta.begin(), H.inv_delta.end());
+        hdiag.insert(hdiag.end(), H.diag.begin(), H.diag.end());
+        const int32_t scbase = (int32_t)hsci.size(), atbase = (int32_t)hatc.size(), abase = (int32_t)hac.size();
+        for (int64_t e = 0; e < H.S.N(); ++e) {
+            hscp.push_back(scbase + H.sc_ptr[e]);
+            hatp.push_back(atbase + H.At_ptr[e]);
+        }
+        for (int32_t j : H.sc_idx) hsci.push_back((int32_t)(po + j));
+        for (size_t j = 0; j < H.At_col.size(); ++j) hatc.push_back(mo + H.At_col[j]);
+        hAtv.insert(hAtv.end(), H.At_val.begin(), H.At_val.end());
+        for (int32_t i = 0; i < H.m; ++i) {
+            hap.push_back(abase + H.A_ptr[i]);
+            hri.push_back(b);
+        }
+        for (int32_t e : H.A_col) hac.push_back((int32_t)(xo + e));
+        hAv.insert(hAv.end(), H.A_val.begin(), H.A_val.end());
+        hb.insert(hb.end(), H.b.begin(), H.b.end());
+        if (!H.dense)
+            for (int32_t i = 0; i < H.m; ++i) hsd[mo + i] = H.Sdiag_inv[i];
+        for (int32_t e : H.S.gather) hg.push_back((int32_t)(xo + e));
+        for (int32_t k = 0; k < H.S.p(); ++k) {
+            hclo.push_back((int32_t)(po + H.S.packed_ptr[k]));
+            hcls.push_back(H.S.clique_ptr[k + 1] - H.S.clique_ptr[k]);
+            hcli.push_back(b);
+        }
+        for (int64_t s0 = 0; s0 < H.S.N(); s0 += TILE_N)
+            htiles.push_back(make_int4(b, (int)(xo + s0), (int)(xo + std::min<int64_t>(H.S.N(), s0 + TILE_N)), 0));
+    }
+    hscp.push_back((int32_t)hsci.size());
+    hatp.push_back((int32_t)hatc.size());
+    hap.push_back((int32_t)hac.size());
+
+    cudaStream_t st = h->st;
+    CK(cudaMemsetAsync(h->arena, 0, h->arena_bytes, st));
+    int rc;
+#define UP(off, vec) if ((rc = upload(ar + (off), vec, st)) != HSDE_OK) return rc
+    UP(o_c, hc); UP(o_id, hid); UP(o_diag, hdiag); UP(o_scp, hscp); UP(o_sci, hsci);
+    UP(o_atp, hatp); UP(o_atc, hatc); UP(o_atv, hAtv); UP(o_b, hb); UP(o_ap, hap); UP(o_ac, hac);
+    UP(o_av, hAv); UP(o_ri, hri); UP(o_sd, hsd); UP(o_g, hg); UP(o_clo, hclo); UP(o_cls, hcls);
+    UP(o_cli, hcli);
+    {
+        std::vector<InstDev> iv(inst);
+        CK(cudaMemcpyAsync(ar + o_inst, iv.data(), sizeof(InstDev) * B, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ar + o_tiles, htiles.data(), sizeof(int4) * htiles.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    // ---- dense S: upload and invert in place (Gauss-Jordan, SPD) ----
+    if (ndense > 0) {
+        std::vector<int64_t> offs, boffs;
+        std::vector<int32_t> ms;
+        for (int32_t b = 0; b < B; ++b) {
+            const HostPrep& H = h->prep[b];
+            if (!H.dense) continue;
+            CK(cudaMemcpyAsync(V.sinv + inst[b].sinv_off, H.Sdense.data(), sizeof(double) * H.Sdense.size(),
+                               cudaMemcpyHostToDevice, st));
+            offs.push_back(inst[b].sinv_off);
+            ms.push_back(H.m);
+            boffs.push_back(inst[b].m_off);
+        }
+        UP(o_gjoff, offs); UP(o_gjm, ms); UP(o_gjb, boffs);
+        for (int32_t k = 0; k < mmax; ++k)
+            launch_gj_step(V.sinv, (const int64_t*)(ar + o_gjoff), (const int32_t*)(ar + o_gjm), ndense, k, mmax,
+                           (double*)(ar + o_gjrow), (double*)(ar + o_gjcol), (const int64_t*)(ar + o_gjb), st);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(st));
+        for (auto& H : h->prep) { std::vector<double>().swap(H.Sdense); }
+    }
+#undef UP
+    // ---- cached M^{-1} zeta = (x_p, ., y_p, .) and 1 + zeta^T M^{-1} zeta ----
+    launch_rhs(V, h->mixed, Mode::Setup, st);
+    launch_spmv_A(V, Mode::Setup, st);
+    launch_solve(V, Mode::Setup, st);
+    launch_spmv_At(V, Mode::Setup, st);
+    launch_setup_den(V, st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+
+    // ---- clique buckets (largest cliques first) ----
+    {
+        std::vector<std::vector<int32_t>> lists(5);
+        const int caps[5] = {8, 16, 32, 64, 128};
+        std::vector<int32_t> ids(ncl);
+        for (int64_t k = 0; k < ncl; ++k) ids[k] = (int32_t)k;
+        std::stable_sort(ids.begin(), ids.end(), [&](int32_t a, int32_t b) { return hcls[a] > hcls[b]; });
+        for (int32_t k : ids) {
+            const int bk = bucket_of(hcls[k]);
+            for (int t = 0; t < 5; ++t) if (caps[t] == bk) lists[t].push_back(k);
+        }
+        int32_t* dl = (int32_t*)(ar + o_blist);
+        size_t used = 0;
+        for (int t = 0; t < 5; ++t) {
+            if (lists[t].empty()) continue;
+            CK(cudaMemcpyAsync(dl + used, lists[t].data(), sizeof(int32_t) * lists[t].size(),
+                               cudaMemcpyHostToDevice, st));
+            h->buckets.push_back(Bucket{caps[t], (int32_t)lists[t].size(), dl + used});
+            used += lists[t].size();
+        }
+        CK(cudaStreamSynchronize(st));
+    }
+    if (cone_prepare(h->mixed) != HSDE_OK) return fail(HSDE_ECUDA, "cudaFuncSetAttribute failed");
+
+    // ---- capture one iteration into a graph ----
+    if (opt.use_graph) {
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int rc2 = enqueue_iteration(h);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(st, &g);
+        if (rc2 != HSDE_OK) { if (g) cudaGraphDestroy(g); return rc2; }
+        if (e2 != cudaSuccess) return fail(HSDE_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e2));
+        h->graph = g;
+        CK(cudaGraphInstantiate(&h->exec, g, 0));
+    }
+    CK(cudaStreamSynchronize(st));
+    h->setup_ms = now_ms() - t0;
+    *out = h;
+    h = nullptr;   // release guard
+    return HSDE_OK;
+}
+
+int check_handle(const hsde_handle* h, int32_t i) {
+    if (!h) return fail(HSDE_EINVAL, "null handle");
+    if (i < 0 || i >= h->B) return fail(HSDE_EINVAL, "instance index out of range");
+    return HSDE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hsde_default_options(hsde_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->eps_tol = 1e-4;
+    o->max_iter = 2000;
+    o->check_every = 1;
+    o->precision = HSDE_MIXED;
+    o->device = 0;
+    o->cuda_stream = nullptr;
+    o->jacobi_max_sweeps = 0;
+    o->use_graph = 1;
+    o->jacobi_tol = 0.0;
+}
+
+const char* hsde_last_error(void) { return g_err.c_str(); }
+
+int hsde_analyze(const hsde_problem* P, hsde_symbolic** out) {
+    try {
+        if (!out) return fail(HSDE_EINVAL, "out is null");
+        *out = nullptr;
+        auto* s = new hsde_symbolic();
+        std::string err;
+        int rc = build_symbolic(P, s->S, err);
+        if (rc != HSDE_OK) { delete s; return fail(rc, err); }
+        *out = s;
+        return HSDE_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(HSDE_ENOMEM, "host allocation failed");
+    } catch (...) {
+        return fail(HSDE_EINVAL, "unexpected error");
+    }
+}
+
+static void fill_sizes(const Symbolic& S, int32_t m, bool dense, hsde_sizes* o) {
+    std::memset(o, 0, sizeof(*o));
+    o->n = S.n; o->m = m; o->p = S.p();
+    o->N = S.N(); o->P = S.P();
+    int64_t nd = 0;
+    int32_t cmax = 0;
+    for (int32_t k = 0; k < S.p(); ++k) {
+        const int64_t c = S.clique_ptr[k + 1] - S.clique_ptr[k];
+        nd += c * c;
+        cmax = std::max<int32_t>(cmax, (int32_t)c);
+    }
+    o->n_d = nd; o->c_max = cmax;
+    o->state_len = o->N + 3 * o->P + m + 2;
+    o->S_dense = dense ? 1 : 0;
+}
+
+int hsde_symbolic_sizes(const hsde_symbolic* s, hsde_sizes* out) {
+    if (!s || !out) return fail(HSDE_EINVAL, "null argument");
+    fill_sizes(s->S, 0, false, out);
+    out->state_len = 0;
+    return HSDE_OK;
+}
+
+static void copy_structure(const Symbolic& S, int32_t* order, int32_t* clique_ptr, int32_t* clique_idx,
+                           int32_t* pat_colptr, int32_t* pat_row, int32_t* gather, int32_t* D) {
+    auto cp = [](int32_t* dst, const std::vector<int32_t>& v) {
+        if (dst && !v.empty()) std::memcpy(dst, v.data(), v.size() * sizeof(int32_t));
+    };
+    cp(order, S.order); cp(clique_ptr, S.clique_ptr); cp(clique_idx, S.clique_idx);
+    cp(pat_colptr, S.pat_colptr); cp(pat_row, S.pat_row); cp(gather, S.gather); cp(D, S.D);
+}
+
+int hsde_symbolic_get(const hsde_symbolic* s, int32_t* order, int32_t* clique_ptr, int32_t* clique_idx,
+                      int32_t* pat_colptr, int32_t* pat_row, int32_t* gather, int32_t* D) {
+    if (!s) return fail(HSDE_EINVAL, "null symbolic");
+    copy_structure(s->S, order, clique_ptr, clique_idx, pat_colptr, pat_row, gather, D);
+    return HSDE_OK;
+}
+
+void hsde_symbolic_free(hsde_symbolic* s) { delete s; }
+
+int hsde_setup(const hsde_problem* P, const hsde_options* O, hsde_handle** out) {
+    return hsde_setup_batch(P, 1, O, out);
+}
+
+int hsde_setup_batch(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_handle** out) {
+    try {
+        return setup_impl(P, B, O, out);
+    } catch (const std::bad_alloc&) {
+        return fail(HSDE_ENOMEM, "host allocation failed");
+    } catch (...) {
+        return fail(HSDE_EINVAL, "unexpected error");
+    }
+}
+
+int hsde_iterate(hsde_handle* h, int32_t k, int32_t* status_out) {
+    if (!h) return fail(HSDE_EINVAL, "null handle");
+    if (k < 0) return fail(HSDE_EINVAL, "k < 0");
+    const double t0 = now_ms();
+    CK(cudaSetDevice(h->device));
+    for (int32_t it = 0; it < k; ++it) {
+        if (h->exec) {
+            CK(cudaGraphLaunch(h->exec, h->st));
+        } else {
+            int rc = enqueue_iteration(h);
+            if (rc != HSDE_OK) return rc;
+        }
+    }
+    if (status_out) {
+        int rc = sync_inst(h);
+        if (rc != HSDE_OK) return rc;
+        for (int32_t b = 0; b < h->B; ++b) status_out[b] = h->host_inst[b].status;
+        h->iterate_ms += now_ms() - t0;
+    }
+    return HSDE_OK;
+}
+
+int hsde_sync(hsde_handle* h) {
+    if (!h) return fail(HSDE_EINVAL, "null handle");
+    CK(cudaStreamSynchronize(h->st));
+    return HSDE_OK;
+}
+
+int hsde_num_instances(const hsde_handle* h) { return h ? h->B : 0; }
+
+int hsde_get_sizes(const hsde_handle* h, int32_t i, hsde_sizes* out) {
+    int rc = check_handle(h, i);
+    if (rc != HSDE_OK) return rc;
+    if (!out) return fail(HSDE_EINVAL, "null output");
+    fill_sizes(h->prep[i].S, h->prep[i].m, h->prep[i].dense, out);
+    return HSDE_OK;
+}
+
+int hsde_get_structure(const hsde_handle* h, int32_t i, int32_t* order, int32_t* clique_ptr,
+                       int32_t* clique_idx, int32_t* pat_colptr, int32_t* pat_row, int32_t* gather,
+                       int32_t* D) {
+    int rc = check_handle(h, i);
+    if (rc != HSDE_OK) return rc;
+    copy_structure(h->prep[i].S, order, clique_ptr, clique_idx, pat_colptr, pat_row, gather, D);
+    return HSDE_OK;
+}
+
+int hsde_get_info(hsde_handle* h, int32_t i, hsde_info* out) {
+    int rc = check_handle(h, i);
+    if (rc != HSDE_OK) return rc;
+    if (!out) return fail(HSDE_EINVAL, "null output");
+    if ((rc = sync_inst(h)) != HSDE_OK) return rc;
+    const InstDev& I = h->host_inst[i];
+    std::memset(out, 0, sizeof(*out));
+    out->status = I.status; out->iterations = I.iter;
+    out->pres = I.pres; out->dres = I.dres; out->gap = I.gap;
+    out->pobj = I.pobj; out->dobj = I.dobj; out->tau = I.tau; out->kappa = I.kappa;
+    out->pinf_ratio = I.pinf; out->dinf_ratio = I.dinf;
+    out->setup_ms = h->setup_ms; out->iterate_ms = h->iterate_ms;
+    return HSDE_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// download s/z/v of instance i as doubles
+int get_packed(hsde_handle* h, const void* base, int32_t i, double* dst) {
+    const int64_t P = h->prep[i].S.P();
+    const int64_t po = h->p_off[i];
+    if (P == 0) return HSDE_OK;
+    if (h->mixed) {
+        std::vector<float> tmp(P);
+        CK(cudaMemcpy(tmp.data(), (const float*)base + po, sizeof(float) * P, cudaMemcpyDeviceToHost));
+        for (int64_t j = 0; j < P; ++j) dst[j] = tmp[j];
+    } else {
+        CK(cudaMemcpy(dst, (const double*)base + po, sizeof(double) * P, cudaMemcpyDeviceToHost));
+    }
+    return HSDE_OK;
+}
+
+int set_packed(hsde_handle* h, void* base, int32_t i, const double* src) {
+    const int64_t P = h->prep[i].S.P();
+    const int64_t po = h->p_off[i];
+    if (P == 0) return HSDE_OK;
+    if (h->mixed) {
+        std::vector<float> tmp(P);
+        for (int64_t j = 0; j < P; ++j) tmp[j] = (float)src[j];
+        CK(cudaMemcpy((float*)base + po, tmp.data(), sizeof(float) * P, cudaMemcpyHostToDevice));
+    } else {
+        CK(cudaMemcpy((double*)base + po, src, sizeof(double) * P, cudaMemcpyHostToDevice));
+    }
+    return HSDE_OK;
+}
+
+// H^T z for instance i (host scatter over the gather map)
+void scatter_host(const HostPrep& H, const double* zp, double* out) {
+    const int64_t N = H.S.N();
+    std::fill(out, out + N, 0.0);
+    for (size_t j = 0; j < H.S.gather.size(); ++j) out[H.S.gather[j]] += zp[j];
+}
+
+}  // namespace
+
+extern "C" {
+
+int hsde_get_state(hsde_handle* h, int32_t i, double* state) {
+    int rc = check_handle(h, i);
+    if (rc != HSDE_OK) return rc;
+    if (!state) return fail(HSDE_EINVAL, "null state");
+    CK(cudaSetDevice(h->device));
+    if ((rc = sync_inst(h)) != HSDE_OK) return rc;
+    const HostPrep& H = h->prep[i];
+    const int64_t N = H.S.N(), P = H.S.P();
+    const int32_t m = H.m;
+    double* p = state;
+    CK(cudaMemcpy(p, h->V.x + h->x_off[i], sizeof(double) * N, cudaMemcpyDeviceToHost)); p += N;
+    if ((rc = get_packed(h, h->V.s, i, p)) != HSDE_OK) return rc; p += P;
+    if (m) CK(cudaMemcpy(p, h->V.y + h->m_off[i], sizeof(double) * m, cudaMemcpyDeviceToHost));
+    p += m;
+    if ((rc = get_packed(h, h->V.v, i, p)) != HSDE_OK) return rc; p += P;
+    *p++ = h->host_inst[i].tau;
+    if ((rc = get_packed(h, h->V.z, i, p)) != HSDE_OK) return rc; p += P;
+    *p++ = h->host_inst[i].kappa;
+    return HSDE_OK;
+}
+
+int hsde_set_state(hsde_handle* h, int32_t i, const double* state, int32_t iterations) {
+    int rc = check_handle(h, i);
+    if (rc != HSDE_OK) return rc;
+    if (!state || iterations < 0) return fail(HSDE_EINVAL, "null state or negative iteration count");
+    CK(cudaSetDevice(h->device));
+    if ((rc = sync_inst(h)) != HSDE_OK) return rc;
+    const HostPrep& H = h->prep[i];
+    const int64_t N = H.S.N(), P = H.S.P();
+    const int32_t m = H.m;
+    const double* p = state;
+    CK(cudaMemcpy(h->V.x + h->x_off[i], p, sizeof(double) * N, cudaMemcpyHostToDevice)); p += N;
+    if ((rc = set_packed(h, h->V.s, i, p)) != HSDE_OK) return rc; p += P;
+    if (m) CK(cudaMemcpy(h->V.y + h->m_off[i], p, sizeof(double) * m, cudaMemcpyHostToDevice));
+    p += m;
+    if ((rc = set_packed(h, h->V.v, i, p)) != HSDE_OK) return rc; p += P;
+    const double tau = *p++;
+    if ((rc = set_packed(h, h->V.z, i, p)) != HSDE_OK) return rc; p += P;
+    const double kappa = *p++;
+    InstDev I = h->host_inst[i];
+    I.tau = tau; I.kappa = kappa; I.status = HSDE_RUNNING; I.iter = iterations; I.eta = 0.0;
+    CK(cudaMemcpy(h->V.inst + i, &I, sizeof(InstDev), cudaMemcpyHostToDevice));
+    h->host_inst[i] = I;
+    return HSDE_OK;
+}
+
+int hsde_get_solution(hsde_handle* h, int32_t i, double* X, double* y, double* Z, double* pobj,
+                      double* dobj) {
+    int rc = check_handle(h, i);
+    if (rc != HSDE_OK) return rc;
+    CK(cudaSetDevice(h->device));
+    if ((rc = sync_inst(h)) != HSDE_OK) return rc;
+    const InstDev& I = h->host_inst[i];
+    if (I.status != HSDE_SOLVED) return fail(HSDE_ESTATE, "instance is not solved");
+    const HostPrep& H = h->prep[i];
+    const int64_t N = H.S.N(), P = H.S.P();
+    const double tau = I.tau;
+    if (X) {
+        CK(cudaMemcpy(X, h->V.x + h->x_off[i], sizeof(double) * N, cudaMemcpyDeviceToHost));
+        for (int64_t e = 0; e < N; ++e) X[e] /= tau;
+    }
+    if (y && H.m) {
+        CK(cudaMemcpy(y, h->V.y + h->m_off[i], sizeof(double) * H.m, cudaMemcpyDeviceToHost));
+        for (int32_t j = 0; j < H.m; ++j) y[j] /= tau;
+    }
+    if (Z) {
+        std::vector<double> zp(P);
+        if ((rc = get_packed(h, h->V.z, i, zp.data())) != HSDE_OK) return rc;
+        scatter_host(H, zp.data(), Z);
+        for (int64_t e = 0; e < N; ++e) Z[e] /= tau;
+    }
+    if (pobj) *pobj = I.pobj;
+    if (dobj) *dobj = I.dobj;
+    return HSDE_OK;
+}
+
+int hsde_get_certificate(hsde_handle* h, int32_t i, int32_t kind, double* y, double* Z, double* X) {
+    int rc = check_handle(h, i);
+    if (rc != HSDE_OK) return rc;
+    CK(cudaSetDevice(h->device));
+    if ((rc = sync_inst(h)) != HSDE_OK) return rc;
+    const InstDev& I = h->host_inst[i];
+    if (kind != I.status || (kind != HSDE_PRIMAL_INFEASIBLE && kind != HSDE_DUAL_INFEASIBLE))
+        return fail(HSDE_ESTATE, "instance verdict does not match the certificate kind");
+    const HostPrep& H = h->prep[i];
+    const int64_t N = H.S.N(), P = H.S.P();
+    if (kind == HSDE_PRIMAL_INFEASIBLE) {
+        const double bty = I.bty;
+        if (y && H.m) {
+            CK(cudaMemcpy(y, h->V.y + h->m_off[i], sizeof(double) * H.m, cudaMemcpyDeviceToHost));
+            for (int32_t j = 0; j < H.m; ++j) y[j] /= bty;
+        }
+        if (Z) {
+            std::vector<double> zp(P);
+            if ((rc = get_packed(h, h->V.z, i, zp.data())) != HSDE_OK) return rc;
+            scatter_host(H, zp.data(), Z);
+            for (int64_t e = 0; e < N; ++e) Z[e] /= bty;
+        }
+    } else {
+        const double nctx = -I.ctx;
+        if (X) {
+            CK(cudaMemcpy(X, h->V.x + h->x_off[i], sizeof(double) * N, cudaMemcpyDeviceToHost));
+            for (int64_t e = 0; e < N; ++e) X[e] /= nctx;
+        }
+    }
+    return HSDE_OK;
+}
+
+void hsde_destroy(hsde_handle* h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    free_handle(h);
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// Internal declarations shared by the translation units of libhsde.
+// Not part of the public ABI (see include/hsde.h).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "hsde.h"
+
+namespace hsde {
+
+// ---------------------------------------------------------------------------
+// Host-side symbolic analysis of one instance (Section 2.1-2.2, Section 4.3)
+// ---------------------------------------------------------------------------
+struct Symbolic {
+    int32_t n = 0;
+    std::vector<int32_t> order;        // vertex eliminated at each step
+    std::vector<int32_t> clique_ptr;   // [p+1]
+    std::vector<int32_t> clique_idx;   // members, ascending within a clique
+    std::vector<int32_t> pat_colptr;   // [n+1]  CSC lower pattern E'
+    std::vector<int32_t> pat_row;      // [N]
+    std::vector<int32_t> pat_col;      // [N]
+    std::vector<int64_t> packed_ptr;   // [p+1]
+    std::vector<int32_t> gather;       // [P] packed clique entry -> pattern position
+    std::vector<int32_t> D;            // [N] cliques containing each entry
+
+    int64_t N() const { return (int64_t)pat_row.size(); }
+    int32_t p() const { return (int32_t)clique_ptr.size() - 1; }
+    int64_t P() const { return packed_ptr.empty() ? 0 : packed_ptr.back(); }
+    int32_t pos(int32_t r, int32_t c) const;   // -1 if (r,c) not in E'
+};
+
+// Validates the problem and runs the analysis; returns HSDE_OK or HSDE_EINVAL.
+int build_symbolic(const hsde_problem* P, Symbolic& S, std::string& err);
+
+// ---------------------------------------------------------------------------
+// Per-instance scalars that live on the device (one record per instance).
+// ---------------------------------------------------------------------------
+struct InstDev {
+    // offsets into the concatenated arrays
+    int64_t x_off, N;        // pattern entries
+    int64_t p_off, P;        // packed clique entries
+    int64_t sinv_off;        // dense S^{-1} offset in the pool (doubles)
+    int32_t m_off, m;        // constraints
+    int32_t cl_begin, cl_end;      // cliques
+    int32_t tile_begin, tile_end;  // N-space tiles
+    int32_t dense;           // S stored dense (1) or diagonal (0)
+    int32_t status;          // HSDE_RUNNING ...
+    int32_t iter;            // iterations done
+    int32_t _pad;
+    // cached by setup
+    double den;              // 1 + zeta^T M^{-1} zeta
+    double ctp;              // c^T x_p - b^T y_p
+    double bnorm, cnorm;     // ||b||, ||c|| (full-vec norms)
+    // iterate scalars
+    double tau, kappa, eta;
+    // last check
+    double pres, dres, gap, pobj, dobj, pinf, dinf, ctx, bty;
+};
+
+// Number of partial sums stored per N-space tile.
+constexpr int KPART = 4;
+// Entries per N-space tile (one CTA each).
+constexpr int TILE_N = 1024;
+
+// Device view of the whole batch (plain pointers into one arena).
+struct DevView {
+    int32_t B;
+    int64_t Ntot, Ptot;
+    int32_t Mtot, ntiles, ncl;
+    // N space
+    double* x; const double* c; const double* inv_delta; double* xp;
+    double* f; double* xw;
+    const uint8_t* diag;
+    const int32_t* sc_ptr; const int32_t* sc_idx;        // H^T as CSR over entries
+    const int32_t* At_ptr; const int32_t* At_col; const double* At_val;
+    // m space
+    double* y; const double* b; double* yp; double* q; double* yw;
+    const int32_t* A_ptr; const int32_t* A_col; const double* A_val;   // weighted
+    const int32_t* row_inst;
+    const double* sdiag;     // diagonal S^{-1}
+    double* sinv;            // dense S^{-1} pool
+    // packed clique space (float or double)
+    void* s; void* z; void* v;
+    const int32_t* gmap;     // absolute x index per packed entry
+    const int32_t* cl_off; const int32_t* cl_size; const int32_t* cl_inst;
+    // instances and tiles
+    InstDev* inst;
+    const int4* tiles;       // (inst, begin, end, 0)
+    double* part;            // [ntiles * KPART]
+    double* cl_part;         // [ncl]
+    double* row_part;        // [Mtot * 3]
+    // options
+    double eps;
+    int32_t max_iter, check_every;
+};
+
+// Bucket of cliques handled by one eigensolver variant.
+struct Bucket {
+    int32_t cmax;            // 8, 16, 32, 64, 128
+    int32_t count;
+    int32_t* list;           // device array of clique ids (largest first)
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (defined in the .cu files).  All enqueue on `st`.
+// ---------------------------------------------------------------------------
+enum class Mode : int { Iter = 0, Setup = 1 };
+
+void launch_rhs(const DevView& V, bool mixed, Mode mode, void* st);
+void launch_spmv_A(const DevView& V, Mode mode, void* st);
+void launch_solve(const DevView& V, Mode mode, void* st);
+void launch_spmv_At(const DevView& V, Mode mode, void* st);
+void launch_eta(const DevView& V, void* st);
+void launch_xupd(const DevView& V, void* st);
+void launch_check(const DevView& V, bool mixed, void* st);
+void launch_verdict(const DevView& V, void* st);
+void launch_setup_den(const DevView& V, void* st);
+// cone projection of every clique in one bucket (Eq. Step2 on S, fused with
+// the H gather, the rank-one correction and the nu update of Eq. Step3)
+int  launch_cone(const DevView& V, const Bucket& bk, bool mixed, int max_sweeps, double tol,
+                 void* st);
+int  cone_smem_bytes(int cmax, bool mixed);
+int  cone_prepare(bool mixed);
+// Gauss-Jordan inversion of the dense S matrices (setup)
+void launch_gj_step(double* pool, const int64_t* offs, const int32_t* ms, int ndense,
+                    int32_t k, int32_t mmax, double* rowbuf, double* colbuf,
+                    const int64_t* boff, void* st);
+
+}  // namespace hsde

@@ -1,0 +1,393 @@
+// Per-iteration kernels of the block-eliminated affine projection (Eq. Step1
+// via Sections 4.2-4.3), the scalar tau/kappa updates of Eqs. Step2-Step3,
+// the stopping-rule reductions, and the one-time setup kernels.
+//
+// Fused form of the affine step used here (algebraically equal to the
+// paper's chain of eliminations; the oracle follows the printed order):
+//   omega_tau = tau + kappa
+//   g0 = x - omega_tau c + 1/2 H^T (s + z + v)          (N space)
+//   f  = Delta^{-1} g0,  Delta = I + D/2
+//   q  = y + omega_tau b - A f                           (m space)
+//   y_w = S^{-1} q,      S = I + A Delta^{-1} A^T        (cached inverse)
+//   x_w = f + Delta^{-1} A^T y_w
+//   eta = (c^T x_w - b^T y_w) / (1 + zeta^T M^{-1} zeta) (Eq. MatrixInverseResult)
+//   x = x_w - eta x_p,  y = y_w - eta y_p,
+//   tau_hat = omega_tau + c^T x - b^T y                   (Eq. FirstBlockElimination)
+//   tau = max(0, tau_hat - kappa), kappa += tau - tau_hat (Eqs. Step2-Step3)
+// The clique part (s_hat, v_hat, the PSD projection and z) is in cone.cu.
+//
+// Every reduction is a fixed-order tree (no float atomics): results are
+// bitwise reproducible for a given launch configuration.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "internal.h"
+
+namespace hsde {
+
+static constexpr int NT = 256;   // threads per CTA for N-space tiles and m rows
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the CTA (blockDim.x == NT); result valid in every thread.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double t = (threadIdx.x < NT / 32) ? sh[threadIdx.x] : 0.0;
+    if (w == 0) t = warp_sum(t);
+    if (threadIdx.x == 0) sh[0] = t;
+    __syncthreads();
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ bool is_check_iter(const DevView& V, int iter) {
+    return (iter % V.check_every) == 0 || iter >= V.max_iter;
+}
+
+template <typename T>
+__device__ __forceinline__ double ld(const void* p, int64_t i) {
+    return (double)reinterpret_cast<const T*>(p)[i];
+}
+
+// ---------------------------------------------------------------------------
+// g0, f = Delta^{-1} g0 ; Setup mode: f = Delta^{-1} c
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NT) k_rhs(DevView V, int mode) {
+    const int4 t = V.tiles[blockIdx.x];
+    const InstDev& I = V.inst[t.x];
+    if (mode == (int)Mode::Setup) {
+        for (int e = t.y + threadIdx.x; e < t.z; e += NT) V.f[e] = V.c[e] * V.inv_delta[e];
+        return;
+    }
+    if (I.status != HSDE_RUNNING) return;
+    const double ot = I.tau + I.kappa;
+    for (int e = t.y + threadIdx.x; e < t.z; e += NT) {
+        double acc = 0.0;
+        const int j1 = V.sc_ptr[e + 1];
+        for (int j = V.sc_ptr[e]; j < j1; ++j) {
+            const int p = V.sc_idx[j];
+            acc += ld<T>(V.s, p) + ld<T>(V.z, p) + ld<T>(V.v, p);
+        }
+        V.f[e] = (V.x[e] - ot * V.c[e] + 0.5 * acc) * V.inv_delta[e];
+    }
+}
+
+// q = y + omega_tau b - A f  (Setup: q = -b - A f).  One warp per row.
+__global__ void __launch_bounds__(NT) k_spmv_A(DevView V, int mode) {
+    const int row = (blockIdx.x * NT + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (row >= V.Mtot) return;
+    const InstDev& I = V.inst[V.row_inst[row]];
+    if (mode == (int)Mode::Iter && I.status != HSDE_RUNNING) return;
+    double acc = 0.0;
+    const int j1 = V.A_ptr[row + 1];
+    for (int j = V.A_ptr[row] + lane; j < j1; j += 32) acc += V.A_val[j] * V.f[V.A_col[j]];
+    acc = warp_sum(acc);
+    if (lane == 0) {
+        const double base = (mode == (int)Mode::Iter) ? V.y[row] + (I.tau + I.kappa) * V.b[row]
+                                                      : -V.b[row];
+        V.q[row] = base - acc;
+    }
+}
+
+// y_w = S^{-1} q (dense row dot products or a diagonal scale).  One warp per row.
+__global__ void __launch_bounds__(NT) k_solve(DevView V, int mode) {
+    const int row = (blockIdx.x * NT + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (row >= V.Mtot) return;
+    const InstDev& I = V.inst[V.row_inst[row]];
+    if (mode == (int)Mode::Iter && I.status != HSDE_RUNNING) return;
+    double* out = (mode == (int)Mode::Iter) ? V.yw : V.yp;
+    if (!I.dense) {
+        if (lane == 0) out[row] = V.sdiag[row] * V.q[row];
+        return;
+    }
+    const int i = row - I.m_off;
+    const double* Srow = V.sinv + I.sinv_off + (int64_t)i * I.m;
+    const double* qq = V.q + I.m_off;
+    double acc = 0.0;
+    for (int j = lane; j < I.m; j += 32) acc += Srow[j] * qq[j];
+    acc = warp_sum(acc);
+    if (lane == 0) out[row] = acc;
+}
+
+// x_w = f + Delta^{-1} A^T y_w (Setup: x_p = f + Delta^{-1} A^T y_p),
+// and the tile partial of c^T x_w (off-diagonal entries weighted 2).
+__global__ void __launch_bounds__(NT) k_spmv_At(DevView V, int mode) {
+    __shared__ double sh[32];
+    const int4 t = V.tiles[blockIdx.x];
+    const InstDev& I = V.inst[t.x];
+    if (mode == (int)Mode::Iter && I.status != HSDE_RUNNING) return;
+    const double* yin = (mode == (int)Mode::Iter) ? V.yw : V.yp;
+    double* out = (mode == (int)Mode::Iter) ? V.xw : V.xp;
+    double part = 0.0;
+    for (int e = t.y + threadIdx.x; e < t.z; e += NT) {
+        double acc = 0.0;
+        const int j1 = V.At_ptr[e + 1];
+        for (int j = V.At_ptr[e]; j < j1; ++j) acc += V.At_val[j] * yin[V.At_col[j]];
+        const double xv = V.f[e] + V.inv_delta[e] * acc;
+        out[e] = xv;
+        part += (V.diag[e] ? 1.0 : 2.0) * V.c[e] * xv;
+    }
+    part = block_sum(part, sh);
+    if (threadIdx.x == 0) V.part[(int64_t)blockIdx.x * KPART + 0] = part;
+}
+
+// eta, tau, kappa and y = y_w - eta y_p.  One CTA per instance.
+__global__ void __launch_bounds__(NT) k_eta(DevView V) {
+    __shared__ double sh[32];
+    InstDev& I = V.inst[blockIdx.x];
+    if (I.status != HSDE_RUNNING) return;
+    double ctw = 0.0;
+    for (int t = I.tile_begin + threadIdx.x; t < I.tile_end; t += NT) ctw += V.part[(int64_t)t * KPART];
+    ctw = block_sum(ctw, sh);
+    double btw = 0.0;
+    for (int i = threadIdx.x; i < I.m; i += NT) btw += V.b[I.m_off + i] * V.yw[I.m_off + i];
+    btw = block_sum(btw, sh);
+    const double sw = ctw - btw;
+    const double eta = sw / I.den;
+    const double tau = I.tau, kappa = I.kappa;
+    const double ot = tau + kappa;
+    const double tau_hat = ot + sw - eta * I.ctp;
+    const double tau_new = fmax(0.0, tau_hat - kappa);
+    const double kappa_new = kappa - tau_hat + tau_new;
+    for (int i = threadIdx.x; i < I.m; i += NT)
+        V.y[I.m_off + i] = V.yw[I.m_off + i] - eta * V.yp[I.m_off + i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        I.eta = eta;
+        I.tau = tau_new;
+        I.kappa = kappa_new;
+        I.iter += 1;
+        if (!isfinite(eta) || !isfinite(tau_new) || !isfinite(kappa_new)) I.status = HSDE_NUMERICAL_ERROR;
+    }
+}
+
+// x = x_w - eta x_p
+__global__ void __launch_bounds__(NT) k_xupd(DevView V) {
+    const int4 t = V.tiles[blockIdx.x];
+    const InstDev& I = V.inst[t.x];
+    if (I.status != HSDE_RUNNING) return;
+    const double eta = I.eta;
+    for (int e = t.y + threadIdx.x; e < t.z; e += NT) V.x[e] = V.xw[e] - eta * V.xp[e];
+}
+
+// Stopping-rule partial sums over N: r = A^T y + H^T z,
+//   part[1] = ||r - tau c||^2, part[2] = ||r||^2, part[3] = c^T x   (full-vec weights)
+template <typename T>
+__global__ void __launch_bounds__(NT) k_check_N(DevView V) {
+    __shared__ double sh[32];
+    const int4 t = V.tiles[blockIdx.x];
+    const InstDev& I = V.inst[t.x];
+    if (I.status != HSDE_RUNNING || !is_check_iter(V, I.iter)) return;
+    const double tau = I.tau;
+    double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (int e = t.y + threadIdx.x; e < t.z; e += NT) {
+        double r = 0.0;
+        const int j1 = V.At_ptr[e + 1];
+        for (int j = V.At_ptr[e]; j < j1; ++j) r += V.At_val[j] * V.y[V.At_col[j]];
+        const int k1 = V.sc_ptr[e + 1];
+        for (int k = V.sc_ptr[e]; k < k1; ++k) r += ld<T>(V.z, V.sc_idx[k]);
+        const double w = V.diag[e] ? 1.0 : 2.0;
+        const double d = r - tau * V.c[e];
+        a1 += w * d * d;
+        a2 += w * r * r;
+        a3 += w * V.c[e] * V.x[e];
+    }
+    a1 = block_sum(a1, sh);
+    a2 = block_sum(a2, sh);
+    a3 = block_sum(a3, sh);
+    if (threadIdx.x == 0) {
+        double* pp = V.part + (int64_t)blockIdx.x * KPART;
+        pp[1] = a1; pp[2] = a2; pp[3] = a3;
+    }
+}
+
+// Stopping-rule partials over m: (Ax - tau b)^2, (Ax)^2, b_i y_i.  Warp per row.
+__global__ void __launch_bounds__(NT) k_check_m(DevView V) {
+    const int row = (blockIdx.x * NT + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (row >= V.Mtot) return;
+    const InstDev& I = V.inst[V.row_inst[row]];
+    if (I.status != HSDE_RUNNING || !is_check_iter(V, I.iter)) return;
+    double acc = 0.0;
+    const int j1 = V.A_ptr[row + 1];
+    for (int j = V.A_ptr[row] + lane; j < j1; j += 32) acc += V.A_val[j] * V.x[V.A_col[j]];
+    acc = warp_sum(acc);
+    if (lane == 0) {
+        const double d = acc - I.tau * V.b[row];
+        V.row_part[(int64_t)row * 3 + 0] = d * d;
+        V.row_part[(int64_t)row * 3 + 1] = acc * acc;
+        V.row_part[(int64_t)row * 3 + 2] = V.b[row] * V.y[row];
+    }
+}
+
+// Verdict of the stopping rule (readings P5/P6).  One CTA per instance.
+__global__ void __launch_bounds__(NT) k_verdict(DevView V) {
+    __shared__ double sh[32];
+    InstDev& I = V.inst[blockIdx.x];
+    if (I.status != HSDE_RUNNING || !is_check_iter(V, I.iter)) return;
+    double a1 = 0, a2 = 0, a3 = 0;
+    for (int t = I.tile_begin + threadIdx.x; t < I.tile_end; t += NT) {
+        const double* pp = V.part + (int64_t)t * KPART;
+        a1 += pp[1]; a2 += pp[2]; a3 += pp[3];
+    }
+    a1 = block_sum(a1, sh); a2 = block_sum(a2, sh); a3 = block_sum(a3, sh);
+    double r0 = 0, r1 = 0, r2 = 0;
+    for (int i = threadIdx.x; i < I.m; i += NT) {
+        const double* rp = V.row_part + (int64_t)(I.m_off + i) * 3;
+        r0 += rp[0]; r1 += rp[1]; r2 += rp[2];
+    }
+    r0 = block_sum(r0, sh); r1 = block_sum(r1, sh); r2 = block_sum(r2, sh);
+    double hs = 0;
+    for (int k = I.cl_begin + threadIdx.x; k < I.cl_end; k += NT) hs += V.cl_part[k];
+    hs = block_sum(hs, sh);
+    if (threadIdx.x != 0) return;
+    const double tau = I.tau;
+    const double ctx = a3, bty = r2;
+    double pres = INFINITY, dres = INFINITY, gap = INFINITY, pobj = NAN, dobj = NAN;
+    if (tau > 0) {
+        pres = sqrt(r0 + hs) / tau / (1.0 + I.bnorm);
+        dres = sqrt(a1) / tau / (1.0 + I.cnorm);
+        pobj = ctx / tau;
+        dobj = bty / tau;
+        gap = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
+    }
+    const double pinf = bty > 0 ? sqrt(a2) / bty : INFINITY;
+    const double dinf = ctx < 0 ? sqrt(r1 + hs) / (-ctx) : INFINITY;
+    I.pres = pres; I.dres = dres; I.gap = gap; I.pobj = pobj; I.dobj = dobj;
+    I.pinf = pinf; I.dinf = dinf; I.ctx = ctx; I.bty = bty;
+    int st = HSDE_RUNNING;
+    if (!isfinite(a1) || !isfinite(a2) || !isfinite(r0) || !isfinite(hs) || !isfinite(ctx) ||
+        !isfinite(bty)) {
+        st = HSDE_NUMERICAL_ERROR;
+    } else if (tau > 0 && pres <= V.eps && dres <= V.eps && gap <= V.eps) {
+        st = HSDE_SOLVED;
+    } else if (bty > 0 && pinf <= V.eps) {
+        st = HSDE_PRIMAL_INFEASIBLE;
+    } else if (ctx < 0 && dinf <= V.eps) {
+        st = HSDE_DUAL_INFEASIBLE;
+    } else if (I.iter >= V.max_iter) {
+        st = HSDE_MAX_ITER;
+    }
+    I.status = st;
+}
+
+// den = 1 + c^T x_p - b^T y_p, ctp = den - 1, ||b||, ||c||.  One CTA per instance.
+__global__ void __launch_bounds__(NT) k_setup_den(DevView V) {
+    __shared__ double sh[32];
+    InstDev& I = V.inst[blockIdx.x];
+    double ctp = 0.0;
+    for (int t = I.tile_begin + threadIdx.x; t < I.tile_end; t += NT) ctp += V.part[(int64_t)t * KPART];
+    ctp = block_sum(ctp, sh);
+    double btp = 0.0, bb = 0.0;
+    for (int i = threadIdx.x; i < I.m; i += NT) {
+        const double bi = V.b[I.m_off + i];
+        btp += bi * V.yp[I.m_off + i];
+        bb += bi * bi;
+    }
+    btp = block_sum(btp, sh);
+    bb = block_sum(bb, sh);
+    double cc = 0.0;
+    for (int64_t e = I.x_off + threadIdx.x; e < I.x_off + I.N; e += NT)
+        cc += (V.diag[e] ? 1.0 : 2.0) * V.c[e] * V.c[e];
+    cc = block_sum(cc, sh);
+    if (threadIdx.x == 0) {
+        I.ctp = ctp - btp;
+        I.den = 1.0 + I.ctp;
+        I.bnorm = sqrt(bb);
+        I.cnorm = sqrt(cc);
+    }
+}
+
+// One in-place Gauss-Jordan step (pivot k) on every dense S with m > k.
+// S is symmetric positive definite with eigenvalues >= 1, so no pivoting is
+// needed.  rowbuf/colbuf hold row k and column k before the step.
+__global__ void k_gj_copy(double* pool, const int64_t* offs, const int32_t* ms, int k,
+                          double* rowbuf, double* colbuf, const int64_t* boff) {
+    const int d = blockIdx.y;
+    const int m = ms[d];
+    if (k >= m) return;
+    double* S = pool + offs[d];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+        rowbuf[boff[d] + j] = S[(int64_t)k * m + j];
+        colbuf[boff[d] + j] = S[(int64_t)j * m + k];
+    }
+}
+
+__global__ void k_gj_update(double* pool, const int64_t* offs, const int32_t* ms, int k,
+                            const double* rowbuf, const double* colbuf, const int64_t* boff) {
+    const int d = blockIdx.z;
+    const int m = ms[d];
+    if (k >= m) return;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m || j >= m) return;
+    double* S = pool + offs[d];
+    const double* rk = rowbuf + boff[d];
+    const double* ck = colbuf + boff[d];
+    const double piv = rk[k];
+    double val;
+    if (i == k && j == k) val = 1.0 / piv;
+    else if (i == k) val = rk[j] / piv;
+    else if (j == k) val = -ck[i] / piv;
+    else val = S[(int64_t)i * m + j] - ck[i] * rk[j] / piv;
+    S[(int64_t)i * m + j] = val;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline cudaStream_t S_(void* st) { return reinterpret_cast<cudaStream_t>(st); }
+static inline int rows_grid(int rows) { return (rows * 32 + NT - 1) / NT; }
+
+void launch_rhs(const DevView& V, bool mixed, Mode mode, void* st) {
+    if (V.ntiles == 0) return;
+    if (mixed) k_rhs<float><<<V.ntiles, NT, 0, S_(st)>>>(V, (int)mode);
+    else k_rhs<double><<<V.ntiles, NT, 0, S_(st)>>>(V, (int)mode);
+}
+void launch_spmv_A(const DevView& V, Mode mode, void* st) {
+    if (V.Mtot == 0) return;
+    k_spmv_A<<<rows_grid(V.Mtot), NT, 0, S_(st)>>>(V, (int)mode);
+}
+void launch_solve(const DevView& V, Mode mode, void* st) {
+    if (V.Mtot == 0) return;
+    k_solve<<<rows_grid(V.Mtot), NT, 0, S_(st)>>>(V, (int)mode);
+}
+void launch_spmv_At(const DevView& V, Mode mode, void* st) {
+    if (V.ntiles == 0) return;
+    k_spmv_At<<<V.ntiles, NT, 0, S_(st)>>>(V, (int)mode);
+}
+void launch_eta(const DevView& V, void* st) { k_eta<<<V.B, NT, 0, S_(st)>>>(V); }
+void launch_xupd(const DevView& V, void* st) {
+    if (V.ntiles == 0) return;
+    k_xupd<<<V.ntiles, NT, 0, S_(st)>>>(V);
+}
+void launch_check(const DevView& V, bool mixed, void* st) {
+    if (V.ntiles > 0) {
+        if (mixed) k_check_N<float><<<V.ntiles, NT, 0, S_(st)>>>(V);
+        else k_check_N<double><<<V.ntiles, NT, 0, S_(st)>>>(V);
+    }
+    if (V.Mtot > 0) k_check_m<<<rows_grid(V.Mtot), NT, 0, S_(st)>>>(V);
+}
+void launch_verdict(const DevView& V, void* st) { k_verdict<<<V.B, NT, 0, S_(st)>>>(V); }
+void launch_setup_den(const DevView& V, void* st) { k_setup_den<<<V.B, NT, 0, S_(st)>>>(V); }
+
+void launch_gj_step(double* pool, const int64_t* offs, const int32_t* ms, int ndense, int32_t k,
+                    int32_t mmax, double* rowbuf, double* colbuf, const int64_t* boff, void* st) {
+    dim3 gc((mmax + 255) / 256, ndense);
+    k_gj_copy<<<gc, 256, 0, S_(st)>>>(pool, offs, ms, k, rowbuf, colbuf, boff);
+    dim3 blk(32, 8);
+    dim3 gu((mmax + 31) / 32, (mmax + 7) / 8, ndense);
+    k_gj_update<<<gu, blk, 0, S_(st)>>>(pool, offs, ms, k, rowbuf, colbuf, boff);
+}
+
+}  // namespace hsde

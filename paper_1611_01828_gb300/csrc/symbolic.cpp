@@ -1,0 +1,207 @@
+// Host symbolic analysis (Section 2.1-2.2 and the selectors of Section 3.1):
+// aggregate pattern, chordal extension by exact minimum degree, maximal
+// cliques in natural order, the gather map of H_k = E_Ck (x) E_Ck and
+// D = H^T H (Section 4.3).  Integer work, deterministic.
+//
+// Rules (the paper names no extension method):
+//  * eliminate the alive vertex of smallest degree in the elimination graph,
+//    ties to the smallest index; its alive neighbourhood becomes a clique;
+//  * candidate K_v = {v} U N(v); maximal cliques are the candidates contained
+//    in no other candidate, ordered by elimination step, members ascending;
+//  * E' (lower, CSC order) = the edges {v, u}, u in N(v), plus the diagonal;
+//  * packed clique order: (a,b), b = 0..c-1, a = b..c-1.
+#include <algorithm>
+#include <cmath>
+#include <functional>
+#include <queue>
+#include <utility>
+
+#include "internal.h"
+
+namespace hsde {
+
+int32_t Symbolic::pos(int32_t r, int32_t c) const {
+    if (c < 0 || c >= n) return -1;
+    auto b = pat_row.begin() + pat_colptr[c];
+    auto e = pat_row.begin() + pat_colptr[c + 1];
+    auto it = std::lower_bound(b, e, r);
+    if (it == e || *it != r) return -1;
+    return (int32_t)(it - pat_row.begin());
+}
+
+static bool check_coo(int32_t n, int64_t nnz, const int32_t* r, const int32_t* c, const double* v,
+                      const char* what, std::string& err) {
+    if (nnz < 0 || (nnz > 0 && (!r || !c || !v))) {
+        err = std::string(what) + ": null pointer or negative count";
+        return false;
+    }
+    std::vector<int64_t> keys;
+    keys.reserve((size_t)nnz);
+    for (int64_t k = 0; k < nnz; ++k) {
+        if (r[k] < 0 || r[k] >= n || c[k] < 0 || c[k] >= n) {
+            err = std::string(what) + ": index out of range";
+            return false;
+        }
+        if (r[k] < c[k]) {
+            err = std::string(what) + ": upper-triangle entry (row < col)";
+            return false;
+        }
+        if (v && !std::isfinite(v[k])) {
+            err = std::string(what) + ": non-finite value";
+            return false;
+        }
+        keys.push_back((int64_t)c[k] * n + r[k]);
+    }
+    std::sort(keys.begin(), keys.end());
+    if (std::adjacent_find(keys.begin(), keys.end()) != keys.end()) {
+        err = std::string(what) + ": duplicate entry";
+        return false;
+    }
+    return true;
+}
+
+int build_symbolic(const hsde_problem* P, Symbolic& S, std::string& err) {
+    if (!P) { err = "null problem"; return HSDE_EINVAL; }
+    const int32_t n = P->n, m = P->m;
+    if (n <= 0) { err = "n must be positive"; return HSDE_EINVAL; }
+    if (m < 0) { err = "m must be non-negative"; return HSDE_EINVAL; }
+    if (!check_coo(n, P->C_nnz, P->C_row, P->C_col, P->C_val, "C", err)) return HSDE_EINVAL;
+    if (m > 0 && (!P->A_ptr || !P->b)) { err = "A_ptr or b is null"; return HSDE_EINVAL; }
+    if (m > 0) {
+        if (P->A_ptr[0] != 0) { err = "A_ptr[0] must be 0"; return HSDE_EINVAL; }
+        for (int32_t i = 0; i < m; ++i) {
+            if (P->A_ptr[i + 1] < P->A_ptr[i]) { err = "A_ptr not monotone"; return HSDE_EINVAL; }
+            if (!std::isfinite(P->b[i])) { err = "b: non-finite value"; return HSDE_EINVAL; }
+        }
+        const int64_t a0 = P->A_ptr[0];
+        for (int32_t i = 0; i < m; ++i) {
+            const int64_t s = P->A_ptr[i] - a0, e = P->A_ptr[i + 1] - a0;
+            if (!check_coo(n, e - s, P->A_row + s, P->A_col + s, P->A_val + s, "A_i", err))
+                return HSDE_EINVAL;
+        }
+    }
+    if (P->pattern_nnz > 0 &&
+        !check_coo(n, P->pattern_nnz, P->pattern_row, P->pattern_col, nullptr, "pattern", err)) {
+        // duplicates in the optional pattern are harmless; re-check without them
+        if (err.find("duplicate") == std::string::npos) return HSDE_EINVAL;
+        err.clear();
+    }
+
+    // ---- aggregate pattern: adjacency (off-diagonal) as sorted lists ----
+    std::vector<std::vector<int32_t>> adj(n);
+    auto add = [&](int32_t r, int32_t c) {
+        if (r != c) { adj[r].push_back(c); adj[c].push_back(r); }
+    };
+    for (int64_t k = 0; k < P->C_nnz; ++k) add(P->C_row[k], P->C_col[k]);
+    const int64_t annz = m > 0 ? P->A_ptr[m] : 0;
+    for (int64_t k = 0; k < annz; ++k) add(P->A_row[k], P->A_col[k]);
+    for (int64_t k = 0; k < P->pattern_nnz; ++k) add(P->pattern_row[k], P->pattern_col[k]);
+    for (auto& a : adj) {
+        std::sort(a.begin(), a.end());
+        a.erase(std::unique(a.begin(), a.end()), a.end());
+    }
+
+    // ---- exact minimum degree ----
+    S.n = n;
+    S.order.clear();
+    S.order.reserve(n);
+    std::vector<std::vector<int32_t>> cand;     // K_v in elimination order (sorted)
+    cand.reserve(n);
+    std::vector<char> alive(n, 1);
+    using QE = std::pair<int64_t, int32_t>;
+    std::priority_queue<QE, std::vector<QE>, std::greater<QE>> heap;
+    for (int32_t v = 0; v < n; ++v) heap.push({(int64_t)adj[v].size(), v});
+    std::vector<int32_t> merged;
+    while (!heap.empty()) {
+        const QE top = heap.top();
+        heap.pop();
+        const int32_t v = top.second;
+        if (!alive[v] || top.first != (int64_t)adj[v].size()) continue;
+        std::vector<int32_t> nb = std::move(adj[v]);
+        adj[v].clear();
+        S.order.push_back(v);
+        std::vector<int32_t> K = nb;
+        K.insert(std::upper_bound(K.begin(), K.end(), v), v);
+        cand.push_back(std::move(K));
+        alive[v] = 0;
+        for (int32_t u : nb) {
+            auto& au = adj[u];
+            merged.clear();
+            merged.reserve(au.size() + nb.size());
+            std::set_union(au.begin(), au.end(), nb.begin(), nb.end(), std::back_inserter(merged));
+            // drop u itself and the eliminated v
+            merged.erase(std::remove_if(merged.begin(), merged.end(),
+                                        [&](int32_t w) { return w == u || w == v; }),
+                         merged.end());
+            au.swap(merged);
+        }
+        for (int32_t u : nb) heap.push({(int64_t)adj[u].size(), u});
+    }
+
+    // ---- maximal cliques ----
+    std::vector<int32_t> step(n);
+    for (int32_t t = 0; t < n; ++t) step[S.order[t]] = t;
+    std::vector<std::vector<int32_t>> earlier(n);
+    for (int32_t t = 0; t < n; ++t) {
+        const int32_t v = S.order[t];
+        for (int32_t u : cand[t])
+            if (u != v) earlier[step[u]].push_back(t);
+    }
+    S.clique_ptr.assign(1, 0);
+    S.clique_idx.clear();
+    for (int32_t t = 0; t < n; ++t) {
+        bool maximal = true;
+        for (int32_t s : earlier[t]) {
+            if (std::includes(cand[s].begin(), cand[s].end(), cand[t].begin(), cand[t].end())) {
+                maximal = false;
+                break;
+            }
+        }
+        if (!maximal) continue;
+        S.clique_idx.insert(S.clique_idx.end(), cand[t].begin(), cand[t].end());
+        S.clique_ptr.push_back((int32_t)S.clique_idx.size());
+    }
+
+    // ---- chordal pattern E' in CSC-lower order ----
+    std::vector<std::vector<int32_t>> col(n);
+    for (int32_t j = 0; j < n; ++j) col[j].push_back(j);
+    for (int32_t t = 0; t < n; ++t) {
+        const int32_t v = S.order[t];
+        for (int32_t u : cand[t]) {
+            if (u == v) continue;
+            col[std::min(u, v)].push_back(std::max(u, v));
+        }
+    }
+    S.pat_colptr.assign(n + 1, 0);
+    S.pat_row.clear();
+    S.pat_col.clear();
+    for (int32_t j = 0; j < n; ++j) {
+        auto& cj = col[j];
+        std::sort(cj.begin(), cj.end());
+        cj.erase(std::unique(cj.begin(), cj.end()), cj.end());
+        S.pat_row.insert(S.pat_row.end(), cj.begin(), cj.end());
+        S.pat_col.insert(S.pat_col.end(), cj.size(), j);
+        S.pat_colptr[j + 1] = (int32_t)S.pat_row.size();
+    }
+
+    // ---- gather map (H) and D = H^T H ----
+    const int32_t p = S.p();
+    S.packed_ptr.assign(p + 1, 0);
+    S.gather.clear();
+    for (int32_t k = 0; k < p; ++k) {
+        const int32_t* mem = S.clique_idx.data() + S.clique_ptr[k];
+        const int32_t c = S.clique_ptr[k + 1] - S.clique_ptr[k];
+        for (int32_t b = 0; b < c; ++b)
+            for (int32_t a = b; a < c; ++a) {
+                const int32_t e = S.pos(mem[a], mem[b]);
+                if (e < 0) { err = "internal: clique entry missing from E'"; return HSDE_EINVAL; }
+                S.gather.push_back(e);
+            }
+        S.packed_ptr[k + 1] = (int64_t)S.gather.size();
+    }
+    S.D.assign(S.N(), 0);
+    for (int32_t e : S.gather) S.D[e] += 1;
+    return HSDE_OK;
+}
+
+}  // namespace hsde

@@ -1,0 +1,266 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle.
+
+Tolerances (stated per test):
+  * integer work (structure, maps): bit-exact;
+  * FP64 mode, one or a few iterations from the same state: 1e-8 relative
+    (the two sides differ only by rounding order: Jacobi vs LAPACK, the
+    Gauss-Jordan inverse vs a Cholesky solve);
+  * mixed mode, one iteration from the same (FP32-rounded) state: 1e-4
+    relative (FP32 eigensolves converge to ~1e-6 of the block norm);
+  * full solves: identical verdicts; objectives within 1e-6 relative (FP64)
+    and 1e-4 relative (mixed); iteration counts equal (FP64, +-1) or within
+    10% (mixed).
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import hsde as ohsde
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1611_01828_gb300 import hsde
+    return hsde
+
+
+def to_state(ref, u, nu):
+    V = ref.V
+    x, s, y, v, tau = ref.split(u)
+    z = nu[ref.nF:ref.nF + ref.nd]
+    return np.concatenate([V.x_to_lower(x), V.s_to_packed(s), y, V.s_to_packed(v), [tau],
+                           V.s_to_packed(z), [nu[-1]]])
+
+
+def from_state(ref, st, sz):
+    from paper_1611_01828_gb300 import hsde
+    V = ref.V
+    x, s, y, v, tau, z, kappa = hsde.split_state(st, sz)
+    u = np.concatenate([V.x_from_lower(x), V.s_from_packed(s), y, V.s_from_packed(v), [tau]])
+    nu = np.zeros(ref.dim)
+    nu[ref.nF:ref.nF + ref.nd] = V.s_from_packed(z)
+    nu[-1] = kappa
+    return u, nu
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(1e-300, np.linalg.norm(b))
+
+
+def random_state(ref, rng, f32=False):
+    st = ref.V.st
+    N, P, m = st.N, st.P, ref.m
+    x = rng.standard_normal(N); s = rng.standard_normal(P); y = rng.standard_normal(m)
+    v = rng.standard_normal(P); z = rng.standard_normal(P)
+    if f32:
+        s, v, z = (a.astype(np.float32).astype(np.float64) for a in (s, v, z))
+    return np.concatenate([x, s, y, v, [0.7], z, [0.4]])
+
+
+PROBS = {
+    "cfg0": lambda: synth.config0(),
+    "cfg0_inf": lambda: synth.config0(True),
+    "grid_7x9": lambda: synth.maxcut_grid(7, 9, np.random.default_rng(1)),
+    "arrow_odd": lambda: synth.block_arrow(6, 5, 2, 9, np.random.default_rng(2), assign="roundrobin"),
+    "arrow_buckets": lambda: synth.block_arrow(3, 30, 3, 6, np.random.default_rng(3)),   # c = 33 (CTA path)
+    "arrow_c16_17": lambda: synth.block_arrow(4, 12, 5, 8, np.random.default_rng(4)),    # c = 17
+}
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+def test_structure_bit_exact(hs, name):
+    p = PROBS[name]()
+    ref = ohsde.HSDE(p)
+    with hs.Handle(p, precision="fp64") as H:
+        g = H.hsde_get_structure(0)
+    st = ref.V.st
+    for k in ("order", "clique_ptr", "clique_idx", "pat_colptr", "pat_row", "gather", "D"):
+        assert np.array_equal(g[k], getattr(st, k)), k
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+def test_fp64_one_step_from_random_state(hs, name):
+    p = PROBS[name]()
+    ref = ohsde.HSDE(p)
+    rng = np.random.default_rng(7)
+    state = random_state(ref, rng)
+    with hs.Handle(p, precision="fp64") as H:
+        H.hsde_set_state(0, state, 0)
+        H.hsde_iterate(1)
+        got = H.hsde_get_state(0)
+        sz = H.sizes[0]
+    u0, nu0 = from_state(ref, state, sz)
+    u1, nu1, _ = ref.step(u0, nu0)
+    want = to_state(ref, u1, nu1)
+    assert rel(got, want) < 1e-8
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+def test_mixed_one_step_from_random_state(hs, name):
+    p = PROBS[name]()
+    ref = ohsde.HSDE(p)
+    rng = np.random.default_rng(8)
+    state = random_state(ref, rng, f32=True)
+    with hs.Handle(p, precision="mixed") as H:
+        H.hsde_set_state(0, state, 0)
+        H.hsde_iterate(1)
+        got = H.hsde_get_state(0)
+        sz = H.sizes[0]
+    u0, nu0 = from_state(ref, state, sz)
+    u1, nu1, _ = ref.step(u0, nu0)
+    want = to_state(ref, u1, nu1)
+    assert rel(got, want) < 1e-4
+
+
+@pytest.mark.parametrize("name", ["cfg0", "grid_7x9", "arrow_odd"])
+def test_fp64_first_iterations_from_start(hs, name):
+    p = PROBS[name]()
+    ref = ohsde.HSDE(p)
+    u, nu = ref.initial()
+    with hs.Handle(p, precision="fp64") as H:
+        for k in (1, 4, 15):
+            H.hsde_iterate(k)
+            for _ in range(k):
+                u, nu, _ = ref.step(u, nu)
+            got = H.hsde_get_state(0)
+            assert rel(got, to_state(ref, u, nu)) < 1e-8
+
+
+def _oracle_solve(p, **kw):
+    ref = ohsde.HSDE(p)
+    return ref, ref.solve(**kw)
+
+
+@pytest.mark.parametrize("name", ["cfg0", "cfg0_inf", "arrow_odd"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_solve_verdict_and_objective(hs, name, prec):
+    p = PROBS[name]()
+    ref, res = _oracle_solve(p)
+    with hs.Handle(p, precision=prec) as H:
+        st = H.solve()
+        info = H.hsde_get_info(0)
+    assert int(st[0]) == res.status
+    if prec == "fp64":
+        assert abs(info["iterations"] - res.iterations) <= 1
+    else:
+        assert abs(info["iterations"] - res.iterations) <= max(2, 0.1 * res.iterations)
+    if res.status == ohsde.SOLVED:
+        tol = 1e-6 if prec == "fp64" else 1e-4
+        assert abs(info["pobj"] - res.info["pobj"]) <= tol * max(1.0, abs(res.info["pobj"]))
+        assert abs(info["dobj"] - res.info["dobj"]) <= tol * max(1.0, abs(res.info["dobj"]))
+
+
+def test_solution_and_certificate_queries(hs):
+    p = synth.config0()
+    ref, res = _oracle_solve(p)
+    with hs.Handle(p, precision="fp64") as H:
+        H.solve()
+        X, y, Z, po, do = H.hsde_get_solution(0)
+        with pytest.raises(hs.HSDEError):
+            H.hsde_get_certificate(0, hs.PRIMAL_INFEASIBLE)
+    Xr, yr, Zr = ref.solution(res.u, res.nu)
+    V = ref.V
+    assert rel(V.x_from_lower(X), Xr) < 1e-6
+    assert rel(y, yr) < 1e-6
+    assert rel(V.x_from_lower(Z), Zr) < 1e-6
+    pi = synth.config0(True)
+    ref2, res2 = _oracle_solve(pi)
+    with hs.Handle(pi, precision="fp64") as H:
+        H.solve()
+        yc, Zc = H.hsde_get_certificate(0, hs.PRIMAL_INFEASIBLE)
+    yr2, Zr2 = ref2.certificate(res2.u, res2.nu, res2.status)
+    assert rel(yc, yr2) < 1e-6 and rel(ref2.V.x_from_lower(Zc), Zr2) < 1e-6
+
+
+def test_dual_infeasible_certificate(hs):
+    base = synth.block_arrow(4, 4, 2, 8, synth.rng_for(8), kappa=100.0, assign="roundrobin")
+    p = synth.make_dual_infeasible(base, np.random.default_rng(2))
+    ref, res = _oracle_solve(p, max_iter=20000)
+    assert res.status == ohsde.DUAL_INFEASIBLE
+    with hs.Handle(p, precision="fp64", max_iter=20000) as H:
+        st = H.solve(chunk=200)
+        assert int(st[0]) == hs.DUAL_INFEASIBLE
+        X = H.hsde_get_certificate(0, hs.DUAL_INFEASIBLE)
+    Xf = ref.V.x_from_lower(X)
+    assert ref.V.c @ Xf == pytest.approx(-1.0, rel=1e-9)
+    assert np.linalg.norm(ref.V.A @ Xf) <= 1e-3
+
+
+def test_batch_equals_single_bitwise(hs):
+    probs = [PROBS[k]() for k in ("cfg0", "grid_7x9", "arrow_odd", "cfg0_inf")]
+    singles = []
+    for p in probs:
+        with hs.Handle(p, precision="fp64") as H:
+            H.hsde_iterate(30)
+            singles.append(H.hsde_get_state(0))
+    with hs.Handle(probs, precision="fp64") as H:
+        H.hsde_iterate(30)
+        for i in range(len(probs)):
+            assert np.array_equal(H.hsde_get_state(i), singles[i])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_checkpoint_resume_bitwise(hs, prec):
+    p = PROBS["cfg0"]()
+    with hs.Handle(p, precision=prec) as H:
+        H.hsde_iterate(40)
+        straight = H.hsde_get_state(0)
+    with hs.Handle(p, precision=prec) as H:
+        H.hsde_iterate(15)
+        mid = H.hsde_get_state(0)
+    with hs.Handle(p, precision=prec) as H:
+        H.hsde_set_state(0, mid, 15)
+        H.hsde_iterate(25)
+        assert np.array_equal(H.hsde_get_state(0), straight)
+
+
+def test_graph_and_eager_agree_bitwise(hs):
+    p = PROBS["arrow_buckets"]()
+    outs = []
+    for g in (1, 0):
+        with hs.Handle(p, precision="mixed", use_graph=g) as H:
+            H.hsde_iterate(12)
+            outs.append(H.hsde_get_state(0))
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_no_constraints_and_singleton_cliques(hs):
+    # m = 0, diagonal C with a negative entry: min <C,X>, X psd is unbounded
+    n = 5
+    idx = np.arange(n, dtype=np.int32)
+    p = synth.Problem("diag", n, 0, idx, idx.copy(), np.array([1.0, -2.0, 3.0, 0.5, 1.0]),
+                      np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0),
+                      np.zeros(0))
+    ref, res = _oracle_solve(p, max_iter=5000)
+    with hs.Handle(p, precision="fp64", max_iter=5000) as H:
+        st = H.solve(chunk=100)
+    assert int(st[0]) == res.status == ohsde.DUAL_INFEASIBLE
+
+
+@pytest.mark.parametrize("d", [10, 25, 50])
+def test_config2_small_sweep_mixed_vs_oracle(hs, d):
+    p = synth.config2(100, d)
+    ref, res = _oracle_solve(p)
+    with hs.Handle(p, precision="mixed") as H:
+        st = H.solve(chunk=50)
+        info = H.hsde_get_info(0)
+    assert int(st[0]) == res.status
+    if res.status == ohsde.SOLVED:
+        assert abs(info["pobj"] - res.info["pobj"]) <= 1e-4 * max(1.0, abs(res.info["pobj"]))
+
+
+def test_config1_first_iterations_fp64(hs):
+    p = synth.config1()
+    ref = ohsde.HSDE(p)
+    u, nu = ref.initial()
+    for _ in range(30):
+        u, nu, _ = ref.step(u, nu)
+    with hs.Handle(p, precision="fp64") as H:
+        H.hsde_iterate(30)
+        got = H.hsde_get_state(0)
+    assert rel(got, to_state(ref, u, nu)) < 1e-8

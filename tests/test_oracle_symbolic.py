@@ -9,9 +9,10 @@ import json
 import os
 import random
 
-import networkx as nx
 import numpy as np
 import pytest
+
+nx = pytest.importorskip("networkx")
 
 import synth
 from oracle import symbolic
