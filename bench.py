@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Throughput of the HSDE-ADMM hot path on one GB300 (or N, one process each).
+
+Workload (default): the max-cut SDP on the open 20 x 100 grid, n = 2000,
+m = 2000 (diag(X) = 1), C the weighted Laplacian with +-1 weights, made
+chordal by exact minimum degree: 1530 cliques of size 3..45.  It stands in
+for the maxG32 row of Tables 1 and 3 (SDPLIB is not available).
+
+A step is one ADMM iteration of the whole hot path: scatter, SpMVs, cached
+S^{-1} solve, rank-one correction, clique eigen-projections, nu update and
+the stopping-rule reductions.  The timed region replays the library's CUDA
+graph one iteration at a time with CUDA events on the launching stream; the
+L2 cache (129 MB) is flushed by writing a 512 MB buffer between steps,
+outside the timed events.  `value` is mixed-precision iterations/s (all ranks);
+the plain FP64 form is timed the same way and reported beside it.
+
+Prints ONE JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import signal
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ADMM iters/s & time to 1e-4 residual: batched FP32 vs plain FP64 form, 1 GB300"
+UNIT = "iterations/s"
+WORKLOAD = "maxcut_grid20x100_n2000_m2000"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--oracle-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=0, help="0: same as --steps")
+    ap.add_argument("--skip-verdict", action="store_true", help="skip the time-to-verdict and e2e legs")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle sample (fresh process, single-threaded BLAS)
+# ----------------------------------------------------------------------------
+ORACLE_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import synth
+from oracle import hsde
+p = synth.config1(instance={inst})
+t0 = time.perf_counter()
+ref = hsde.HSDE(p)
+setup_s = time.perf_counter() - t0
+u, nu = ref.initial()
+for _ in range({warm}):
+    u, nu, _ = ref.step(u, nu)
+    ref.residuals(u, nu)
+budget = {secs}
+it = 0
+t0 = time.perf_counter()
+while True:
+    u, nu, _ = ref.step(u, nu)
+    ref.residuals(u, nu)
+    it += 1
+    el = time.perf_counter() - t0
+    if (it >= {min_it} and el >= budget) or it >= {max_it}:
+        break
+print(json.dumps(dict(iters=it, seconds=el, setup_s=setup_s)))
+"""
+
+
+def oracle_sample(seconds, warm=2, min_it=3, max_it=100000, inst=0):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ORACLE_SNIPPET.format(root=ROOT, warm=warm, secs=seconds, min_it=min_it, max_it=max_it, inst=inst)
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if res.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + res.stderr[-2000:])
+    d = json.loads(res.stdout.strip().splitlines()[-1])
+    d["value"] = d["iters"] / d["seconds"]
+    return d
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.send_signal(signal.SIGTERM)
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# algorithmic work per phase (for the roofline)
+# ----------------------------------------------------------------------------
+def cone_flops(c3):
+    """Algorithmic FLOPs of the clique projections: 9 c^3 for a symmetric
+    eigendecomposition with vectors (tridiagonalisation + implicit QR,
+    Golub & Van Loan's count) plus 2 c^3 for the rebuild V max(L,0) V^T."""
+    return 11.0 * c3
+
+
+def affine_bytes(sizes, mixed, nnzA):
+    """Compulsory HBM bytes of the affine phase (scatter, A, S^{-1}, A^T, eta)."""
+    N, P, m = sizes.N, sizes.P, sizes.m
+    T = 4 if mixed else 8
+    rhs = 8 * 3 * N + 4 * (N + 1) + 4 * P + 3 * T * P + 8 * N
+    spA = 4 * (m + 1) + 12 * nnzA + 8 * nnzA + 24 * m
+    solve = 8 * m * m if sizes.S_dense else 24 * m
+    spAt = 4 * (N + 1) + 12 * nnzA + 8 * nnzA + 8 * 3 * N + N + 8 * N
+    eta = 32 * m
+    return rhs + spA + solve + spAt + eta
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def fp32_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) per clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def traffic_from_profile(kernel_tag):
+    """Per-launch DRAM bytes from a committed ncu summary, if its source hash
+    still matches the kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    want = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            want[k.strip()] = v.strip().strip("`")
+    src = want.get("source")
+    sha = want.get("source_sha256")
+    tb = want.get("dram_bytes_per_launch")
+    if not (src and sha and tb):
+        return None
+    p = os.path.join(ROOT, src)
+    if not os.path.exists(p) or hashlib.sha256(open(p, "rb").read()).hexdigest() != sha:
+        return None
+    try:
+        return float(tb)
+    except ValueError:
+        return None
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import synth
+    from paper_1611_01828_gb300 import hsde
+
+    prob = synth.config1(instance=rank)
+    # a real stream shared by the library, the L2 flush and the timing events
+    # (torch's default stream is the legacy NULL stream)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed_steps(H, K, W, profile):
+        for _ in range(W):
+            flush.zero_()
+            H.hsde_iterate(1, want_status=False)
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        phases = {}
+        barrier()
+        for i in range(K):
+            flush.zero_()
+            ev[i][0].record(stream)
+            H.hsde_iterate(1, want_status=False)
+            ev[i][1].record(stream)
+            if profile:
+                pr = H.hsde_get_profile()
+                for k, (ms, units) in pr["phases"].items():
+                    a = phases.setdefault(k, [0.0, units, 0])
+                    a[0] += ms
+                    a[2] += 1
+        barrier()
+        total_ms = sum(a.elapsed_time(b) for a, b in ev)
+        return total_ms, phases
+
+    big = 1 << 30
+    t0 = time.perf_counter()
+    Hm = hsde.Handle(prob, precision="mixed", profile=1, max_iter=big,
+                     cuda_stream=stream.cuda_stream)
+    setup_mixed_ms = (time.perf_counter() - t0) * 1e3
+    sizes = Hm.sizes[0]
+    nnzA = int(prob.A_ptr[-1])
+    kern_per_it = Hm.hsde_get_profile()["kernels_per_iteration"]
+
+    clocks = Clocks(local)
+    clocks.start()
+    mixed_ms, phases = timed_steps(Hm, args.steps, args.warmup, True)
+    ck = clocks.stop()
+    st = Hm.hsde_iterate(0)
+    assert int(st[0]) == hsde.RUNNING, "instance stopped during the timed steps"
+
+    K64 = args.fp64_steps or args.steps
+    Hd = hsde.Handle(prob, precision="fp64", profile=0, max_iter=big, warm_start=0,
+                     cuda_stream=stream.cuda_stream)
+    fp64_ms, _ = timed_steps(Hd, K64, args.warmup, False)
+    Hd.close()
+
+    # time to the 1e-4 verdict (defaults: eps 1e-4, at most 2000 iterations)
+    def to_verdict(prec):
+        H = hsde.Handle(prob, precision=prec, cuda_stream=stream.cuda_stream,
+                        warm_start=(0 if prec == "fp64" else -1))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        st = H.solve(chunk=50)
+        dt = time.perf_counter() - t0
+        info = H.hsde_get_info(0)
+        H.close()
+        return dict(verdict=hsde.STATUS_NAMES[int(st[0])], iterations=info["iterations"], seconds=dt,
+                    pobj=info["pobj"], pres=info["pres"], dres=info["dres"], gap=info["gap"])
+
+    ttv_mixed = to_verdict("mixed") if not args.skip_verdict else None
+    ttv_fp64 = to_verdict("fp64") if not args.skip_verdict else None
+
+    # e2e through the C-ABI with pinned host buffers: per step the iterate goes
+    # host -> device (hsde_set_state), one iteration runs, and the iterate
+    # comes back device -> host (hsde_get_state).
+    L = int(sizes.state_len)
+    hbuf = torch.empty(L, dtype=torch.float64, pin_memory=True).numpy()
+    hbuf[:] = Hm.hsde_get_state(0)
+    it0 = Hm.hsde_get_info(0)["iterations"]
+    Ke = max(20, args.steps // 4) if not args.skip_verdict else 3
+    for _ in range(3):
+        Hm.hsde_set_state(0, hbuf, it0)
+        Hm.hsde_iterate(1, want_status=False)
+        hbuf[:] = Hm.hsde_get_state(0)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        Hm.hsde_set_state(0, hbuf, it0)
+        Hm.hsde_iterate(1, want_status=False)
+        hbuf[:] = Hm.hsde_get_state(0)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    Hm.close()
+
+    # aggregate over ranks (max time)
+    tt = torch.tensor([mixed_ms, fp64_ms, e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    mixed_ms, fp64_ms, e2e_s = [float(x) for x in tt.tolist()]
+    value = world * args.steps / (mixed_ms / 1e3)
+    fp64_value = world * K64 / (fp64_ms / 1e3)
+
+    # roofline of the dominant phase
+    peaks = load_peaks()
+    avg = {k: (a[0] / a[2], a[1]) for k, a in phases.items() if k != "iteration" and a[2]}
+    dom = max(avg, key=lambda k: avg[k][0])
+    dom_ms, dom_units = avg[dom]
+    if dom.startswith("cone_"):
+        sm_for_peak = 2070.0
+        peak = fp32_peak_tflops(sm_for_peak)
+        achieved = cone_flops(dom_units) / (dom_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": f"k_cone ({dom}, FP32 Jacobi)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (max SM clock)",
+                "traffic": traffic_from_profile(f"k_cone_{dom}_cfg1"),
+                "phase_ms": dom_ms, "algorithmic_flops_per_launch": cone_flops(dom_units)}
+    else:
+        peak = (peaks or {}).get("hbm_gbs", 6800.0)
+        byts = affine_bytes(sizes, True, nnzA)
+        achieved = byts / (dom_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)",
+                "traffic": None, "phase_ms": dom_ms, "algorithmic_bytes_per_launch": byts}
+    phase_avg = {k: round(v[0] * 1e3, 2) for k, v in avg.items()}
+    phase_avg_it = phases.get("iteration")
+    if phase_avg_it:
+        phase_avg["iteration"] = round(phase_avg_it[0] / phase_avg_it[2] * 1e3, 2)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        d = oracle_sample(args.oracle_seconds)
+        cpu = {"value": d["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{d['iters']} oracle iterations of the same n=2000 max-cut instance "
+                         f"({d['seconds']:.1f} s, FP64 NumPy/SciPy, single-threaded BLAS, after 2 warm-up "
+                         f"iterations and {d['setup_s']:.1f} s setup)"}
+
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mixed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded; SDPLIB stand-in)",
+        "config": {"workload": WORKLOAD, "n": sizes.n, "m": sizes.m, "cliques": sizes.p, "c_max": sizes.c_max,
+                   "N_pattern_lower": int(sizes.N), "P_packed": int(sizes.P), "instances_per_gpu": 1,
+                   "precision": "mixed: FP32 cone projections + gather/scatter, FP64 x/y/A/S^-1/reductions",
+                   "l2": "flushed between steps (512 MB write, outside the timed events)",
+                   "step": "one ADMM iteration incl. stopping-rule check", "parallelism": f"replicas x{world}"},
+        "fp64_plain": {"value": fp64_value, "unit": UNIT, "ms_per_step": fp64_ms / K64, "steps": K64,
+                       "dtype": "f64", "form": "FP64 everywhere, cold-start Jacobi every iteration"},
+        "mixed_over_fp64": value / fp64_value,
+        "time_to_verdict": {"mixed": ttv_mixed, "fp64": ttv_fp64, "eps_tol": 1e-4, "max_iter": 2000},
+        "setup_ms": setup_mixed_ms,
+        "phase_us": phase_avg,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * Ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": L * 8, "d2h_bytes_per_step": L * 8,
+                "how": "per step: hsde_set_state from pinned host memory, hsde_iterate(1), hsde_get_state to "
+                       "pinned host memory (full iterate both ways)"},
+        "gpu_launches": kern_per_it * (args.steps + 0),
+        "clocks": ck,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # each step is one oracle iteration on the same workload
+    d = oracle_sample(seconds=0.0, warm=args.warmup, min_it=args.steps, max_it=args.steps)
+    v = d["value"]
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * d["seconds"] / d["iters"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; SDPLIB stand-in)",
+           "config": {"workload": WORKLOAD, "step": "one ADMM iteration incl. stopping-rule check"},
+           "impl": "reference",
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{d['iters']} oracle iterations after {args.warmup} warm-up iterations "
+                                      f"(FP64 NumPy/SciPy, single-threaded BLAS)"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

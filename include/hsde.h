@@ -53,7 +53,8 @@ extern "C" {
 #define HSDE_ENOMEM   (-2)   /* host or device allocation failed            */
 #define HSDE_ECUDA    (-3)   /* CUDA runtime error (no device, launch, ...)  */
 #define HSDE_ESTATE   (-4)   /* query does not match the instance's verdict */
-#define HSDE_ERANGE   (-5)   /* size beyond what this build supports        */
+#define HSDE_ERANGE   (-5)   /* size beyond what this build supports (cliques
+                                larger than 64, totals beyond int32 indexing) */
 
 /* per-instance iteration status (readings of the paper's stopping rule) */
 #define HSDE_RUNNING            0
@@ -96,6 +97,15 @@ typedef struct hsde_options {
     int32_t jacobi_max_sweeps;   /* 0: default (FP32 12, FP64 16)                */
     int32_t use_graph;    /* 1 (default): replay iterations through a CUDA graph   */
     double  jacobi_tol;   /* 0: default relative off-diagonal tolerance           */
+    int32_t profile;      /* 1: record CUDA events around each phase of every
+                             iteration (read back with hsde_get_profile)        */
+    int32_t warm_start;   /* eigensolver warm start from the previous iteration's
+                             eigenbasis of each clique: -1 default (on), 0 off,
+                             1 on.  Results then depend on the solve history, so
+                             a resumed run (hsde_set_state) matches a straight
+                             run to rounding, not bitwise.                      */
+    int32_t warm_refresh; /* cold start every k-th iteration, default 32         */
+    int32_t _pad;
 } hsde_options;
 
 typedef struct hsde_sizes {
@@ -119,6 +129,18 @@ typedef struct hsde_info {
     double  setup_ms;     /* host + device setup ("Pre- time" of Tables 2-4)    */
     double  iterate_ms;   /* wall time spent inside hsde_iterate               */
 } hsde_info;
+
+#define HSDE_MAX_PHASES 16
+typedef struct hsde_profile {
+    int32_t kernels_per_iteration;   /* kernel launches in one iteration          */
+    int32_t nphases;
+    double  phase_ms[HSDE_MAX_PHASES];   /* device time of each phase in the last
+                                            iteration launched (profile = 1)    */
+    char    phase_name[HSDE_MAX_PHASES][24];
+    int64_t phase_units[HSDE_MAX_PHASES];  /* work units of the phase: pattern
+                                              entries (affine, check) or
+                                              sum_k c_k^3 (cone buckets)        */
+} hsde_profile;
 
 typedef struct hsde_handle hsde_handle;
 typedef struct hsde_symbolic hsde_symbolic;
@@ -204,6 +226,13 @@ HSDE_API int  hsde_get_solution(hsde_handle* h, int32_t i, double* X, double* y,
  * HSDE_PRIMAL_INFEASIBLE or HSDE_DUAL_INFEASIBLE). */
 HSDE_API int  hsde_get_certificate(hsde_handle* h, int32_t i, int32_t kind, double* y, double* Z,
                           double* X);
+
+/* Launch count of one iteration and, if the handle was set up with
+ * profile = 1, the device time of each phase of the last iteration (waits
+ * for the handle's stream).  Phases: "affine" (scatter, SpMVs, solve, eta),
+ * one "cone_cK" per clique bucket (cliques of size <= K, each on its own
+ * graph branch), "check" (stopping rule) and "iteration" (all of it). */
+HSDE_API int  hsde_get_profile(hsde_handle* h, hsde_profile* out);
 
 /* Free all device and host memory of the handle.  NULL-safe. */
 HSDE_API void hsde_destroy(hsde_handle* h);

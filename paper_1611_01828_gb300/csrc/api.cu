@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
@@ -160,13 +161,6 @@ int prepare(const hsde_problem* P, HostPrep& H, std::string& err) {
     return HSDE_OK;
 }
 
-int bucket_of(int c) {
-    if (c <= 8) return 8;
-    if (c <= 16) return 16;
-    if (c <= 32) return 32;
-    if (c <= 64) return 64;
-    return 128;
-}
 
 }  // namespace
 
@@ -184,8 +178,8 @@ struct hsde_handle {
     std::vector<int32_t> m_off;
     cudaStream_t st = nullptr;
     bool own_stream = false;
-    cudaStream_t side[6] = {};
-    cudaEvent_t ev_fork = nullptr, ev_join[6] = {};
+    cudaStream_t side[10] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[10] = {};
     void* arena = nullptr;
     size_t arena_bytes = 0;
     DevView V{};
@@ -196,31 +190,62 @@ struct hsde_handle {
     double setup_ms = 0, iterate_ms = 0;
     int max_sweeps = 12;
     double jtol = 1e-6;
+    int warm = 1, refresh = 32;
+    // phase timing (options.profile)
+    bool profile = false;
+    bool capturing = false;
+    cudaEvent_t ev_it0 = nullptr, ev_aff = nullptr, ev_chk = nullptr, ev_it1 = nullptr;
+    cudaEvent_t ev_cs[10] = {}, ev_ce[10] = {};
+    std::vector<int64_t> bucket_c3;
+    int kernels_per_iter = 0;
+    int64_t launched = 0;      // iterations enqueued since setup
 };
 
 namespace {
 
+cudaError_t rec(hsde_handle* h, cudaEvent_t ev, cudaStream_t s) {
+    if (!h->profile) return cudaSuccess;
+    return h->capturing ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal) : cudaEventRecord(ev, s);
+}
+
 int enqueue_iteration(hsde_handle* h) {
     const DevView& V = h->V;
+    CK(rec(h, h->ev_it0, h->st));
     launch_rhs(V, h->mixed, Mode::Iter, h->st);
     launch_spmv_A(V, Mode::Iter, h->st);
     launch_solve(V, Mode::Iter, h->st);
     launch_spmv_At(V, Mode::Iter, h->st);
     launch_eta(V, h->st);
+    CK(rec(h, h->ev_aff, h->st));
     // fork: every clique bucket on its own branch, x update on the main branch
     CK(cudaEventRecord(h->ev_fork, h->st));
     for (size_t i = 0; i < h->buckets.size(); ++i) {
         CK(cudaStreamWaitEvent(h->side[i], h->ev_fork, 0));
-        int rc = launch_cone(V, h->buckets[i], h->mixed, h->max_sweeps, h->jtol, h->side[i]);
+        CK(rec(h, h->ev_cs[i], h->side[i]));
+        int rc = launch_cone(V, h->buckets[i], h->mixed, h->max_sweeps, h->jtol, h->warm, h->refresh,
+                             h->side[i]);
         if (rc != HSDE_OK) return fail(rc, "cone launch failed");
+        CK(rec(h, h->ev_ce[i], h->side[i]));
         CK(cudaEventRecord(h->ev_join[i], h->side[i]));
     }
     launch_xupd(V, h->st);
     for (size_t i = 0; i < h->buckets.size(); ++i) CK(cudaStreamWaitEvent(h->st, h->ev_join[i], 0));
+    CK(rec(h, h->ev_chk, h->st));
     launch_check(V, h->mixed, h->st);
     launch_verdict(V, h->st);
+    CK(rec(h, h->ev_it1, h->st));
     CK(cudaGetLastError());
     return HSDE_OK;
+}
+
+int count_kernels(const hsde_handle* h) {
+    const DevView& V = h->V;
+    int k = 0;
+    if (V.ntiles > 0) k += 4;          // rhs, spmv_At, xupd, check_N
+    if (V.Mtot > 0) k += 3;            // spmv_A, solve, check_m
+    k += 2;                            // eta, verdict
+    for (const auto& b : h->buckets) k += b.count > 0 ? 1 : 0;
+    return k;
 }
 
 int sync_inst(hsde_handle* h) {
@@ -237,6 +262,9 @@ void free_handle(hsde_handle* h) {
     for (auto& s : h->side) if (s) cudaStreamDestroy(s);
     for (auto& e : h->ev_join) if (e) cudaEventDestroy(e);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    for (cudaEvent_t e : {h->ev_it0, h->ev_aff, h->ev_chk, h->ev_it1}) if (e) cudaEventDestroy(e);
+    for (auto& e : h->ev_cs) if (e) cudaEventDestroy(e);
+    for (auto& e : h->ev_ce) if (e) cudaEventDestroy(e);
     if (h->arena) cudaFree(h->arena);
     if (h->host_inst) cudaFreeHost(h->host_inst);
     if (h->own_stream && h->st) cudaStreamDestroy(h->st);
@@ -271,7 +299,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     if (O) opt = *O;
     if (!(opt.eps_tol > 0) || opt.max_iter <= 0 || opt.check_every <= 0 ||
         (opt.precision != HSDE_FP64 && opt.precision != HSDE_MIXED) || opt.jacobi_max_sweeps < 0 ||
-        opt.jacobi_tol < 0)
+        opt.jacobi_tol < 0 || opt.warm_start < -1 || opt.warm_start > 1 || opt.warm_refresh < 0)
         return fail(HSDE_EINVAL, "invalid options");
 
     auto* h = new hsde_handle();
@@ -285,6 +313,8 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     h->device = opt.device;
     h->max_sweeps = opt.jacobi_max_sweeps > 0 ? opt.jacobi_max_sweeps : (h->mixed ? 12 : 16);
     h->jtol = opt.jacobi_tol > 0 ? opt.jacobi_tol : (h->mixed ? 1e-6 : 1e-14);
+    h->warm = opt.warm_start == 0 ? 0 : 1;
+    h->refresh = opt.warm_refresh > 0 ? opt.warm_refresh : 32;
 
     // ---- host analysis and preparation ----
     h->prep.resize(B);
@@ -292,8 +322,8 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     for (int32_t b = 0; b < B; ++b) {
         int rc = prepare(&P[b], h->prep[b], err);
         if (rc != HSDE_OK) return fail(rc, "instance " + std::to_string(b) + ": " + err);
-        const int lim = h->mixed ? 128 : 64;
-        if (h->prep[b].cmax > lim)
+        const int lim = 64;
+        if (cone_bucket_of(h->prep[b].cmax) < 0)
             return fail(HSDE_ERANGE, "instance " + std::to_string(b) + ": clique of size " +
                                           std::to_string(h->prep[b].cmax) + " exceeds " +
                                           std::to_string(lim));
@@ -317,10 +347,22 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         I.sinv_off = sinv;
         if (H.dense) sinv += (int64_t)H.m * H.m;
         I.status = HSDE_RUNNING;
+        I.vcold = 1;
         I.tau = 1.0; I.kappa = 1.0;
         h->x_off[b] = Ntot; h->p_off[b] = Ptot; h->m_off[b] = (int32_t)Mtot;
         Ntot += I.N; Ptot += I.P; Mtot += H.m; ncl += H.S.p(); nnzA += (int64_t)H.A_col.size();
         scn += (int64_t)H.sc_idx.size();
+    }
+    std::vector<int64_t> hvso;
+    int64_t vsn = 0;
+    if (h->warm) {
+        for (int32_t b = 0; b < B; ++b) {
+            const Symbolic& S = h->prep[b].S;
+            for (int32_t k = 0; k < S.p(); ++k) {
+                hvso.push_back(vsn);
+                vsn += cone_vstore_elems(S.clique_ptr[k + 1] - S.clique_ptr[k]);
+            }
+        }
     }
     const int64_t LIM = (int64_t)1 << 31;
     if (Ntot >= LIM || Ptot >= LIM || nnzA >= LIM || Mtot >= LIM || scn >= LIM)
@@ -338,6 +380,12 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     for (auto& e : h->ev_join) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     CK(cudaMallocHost(&h->host_inst, sizeof(InstDev) * B));
+    h->profile = opt.profile != 0;
+    if (h->profile) {
+        for (cudaEvent_t* e : {&h->ev_it0, &h->ev_aff, &h->ev_chk, &h->ev_it1}) CK(cudaEventCreate(e));
+        for (auto& e : h->ev_cs) CK(cudaEventCreate(&e));
+        for (auto& e : h->ev_ce) CK(cudaEventCreate(&e));
+    }
 
     // ---- arena layout ----
     const size_t Tsz = h->mixed ? sizeof(float) : sizeof(double);
@@ -353,6 +401,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
                  o_av = cv.take<double>(nnzA), o_ri = cv.take<int32_t>(Mtot),
                  o_sd = cv.take<double>(Mtot), o_sinv = cv.take<double>(sinv);
     size_t o_s = cv.take<char>(Ptot * Tsz), o_z = cv.take<char>(Ptot * Tsz), o_v = cv.take<char>(Ptot * Tsz);
+    const size_t o_vst = cv.take<char>(vsn * Tsz), o_vso = cv.take<int64_t>(hvso.size());
     const size_t o_g = cv.take<int32_t>(Ptot), o_clo = cv.take<int32_t>(ncl), o_cls = cv.take<int32_t>(ncl),
                  o_cli = cv.take<int32_t>(ncl), o_inst = cv.take<InstDev>(B), o_tiles = cv.take<int4>(ntiles),
                  o_part = cv.take<double>(ntiles * KPART), o_clp = cv.take<double>(ncl),
@@ -382,6 +431,8 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     V.row_inst = (const int32_t*)(ar + o_ri); V.sdiag = (const double*)(ar + o_sd);
     V.sinv = (double*)(ar + o_sinv);
     V.s = ar + o_s; V.z = ar + o_z; V.v = ar + o_v;
+    V.vstore = h->warm ? (void*)(ar + o_vst) : nullptr;
+    V.vs_off = (const int64_t*)(ar + o_vso);
     V.gmap = (const int32_t*)(ar + o_g); V.cl_off = (const int32_t*)(ar + o_clo);
     V.cl_size = (const int32_t*)(ar + o_cls); V.cl_inst = (const int32_t*)(ar + o_cli);
     V.inst = (InstDev*)(ar + o_inst); V.tiles = (const int4*)(ar + o_tiles);
@@ -440,7 +491,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     UP(o_c, hc); UP(o_id, hid); UP(o_diag, hdiag); UP(o_scp, hscp); UP(o_sci, hsci);
     UP(o_atp, hatp); UP(o_atc, hatc); UP(o_atv, hAtv); UP(o_b, hb); UP(o_ap, hap); UP(o_ac, hac);
     UP(o_av, hAv); UP(o_ri, hri); UP(o_sd, hsd); UP(o_g, hg); UP(o_clo, hclo); UP(o_cls, hcls);
-    UP(o_cli, hcli);
+    UP(o_cli, hcli); UP(o_vso, hvso);
     {
         std::vector<InstDev> iv(inst);
         CK(cudaMemcpyAsync(ar + o_inst, iv.data(), sizeof(InstDev) * B, cudaMemcpyHostToDevice, st));
@@ -480,22 +531,26 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
 
     // ---- clique buckets (largest cliques first) ----
     {
-        std::vector<std::vector<int32_t>> lists(5);
-        const int caps[5] = {8, 16, 32, 64, 128};
+        constexpr int NB = 9;
+        std::vector<std::vector<int32_t>> lists(NB);
+        const int caps[NB] = {4, 8, 12, 16, 24, 32, 40, 48, 64};
         std::vector<int32_t> ids(ncl);
         for (int64_t k = 0; k < ncl; ++k) ids[k] = (int32_t)k;
         std::stable_sort(ids.begin(), ids.end(), [&](int32_t a, int32_t b) { return hcls[a] > hcls[b]; });
+        std::vector<int64_t> c3(NB, 0);
         for (int32_t k : ids) {
-            const int bk = bucket_of(hcls[k]);
-            for (int t = 0; t < 5; ++t) if (caps[t] == bk) lists[t].push_back(k);
+            const int bk = cone_bucket_of(hcls[k]);
+            for (int t = 0; t < NB; ++t)
+                if (caps[t] == bk) { lists[t].push_back(k); c3[t] += (int64_t)hcls[k] * hcls[k] * hcls[k]; }
         }
         int32_t* dl = (int32_t*)(ar + o_blist);
         size_t used = 0;
-        for (int t = 0; t < 5; ++t) {
+        for (int t = 0; t < NB; ++t) {
             if (lists[t].empty()) continue;
             CK(cudaMemcpyAsync(dl + used, lists[t].data(), sizeof(int32_t) * lists[t].size(),
                                cudaMemcpyHostToDevice, st));
             h->buckets.push_back(Bucket{caps[t], (int32_t)lists[t].size(), dl + used});
+            h->bucket_c3.push_back(c3[t]);
             used += lists[t].size();
         }
         CK(cudaStreamSynchronize(st));
@@ -503,9 +558,12 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     if (cone_prepare(h->mixed) != HSDE_OK) return fail(HSDE_ECUDA, "cudaFuncSetAttribute failed");
 
     // ---- capture one iteration into a graph ----
+    h->kernels_per_iter = count_kernels(h);
     if (opt.use_graph) {
         CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        h->capturing = true;
         int rc2 = enqueue_iteration(h);
+        h->capturing = false;
         cudaGraph_t g = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(st, &g);
         if (rc2 != HSDE_OK) { if (g) cudaGraphDestroy(g); return rc2; }
@@ -542,6 +600,9 @@ void hsde_default_options(hsde_options* o) {
     o->jacobi_max_sweeps = 0;
     o->use_graph = 1;
     o->jacobi_tol = 0.0;
+    o->profile = 0;
+    o->warm_start = -1;
+    o->warm_refresh = 0;
 }
 
 const char* hsde_last_error(void) { return g_err.c_str(); }
@@ -624,6 +685,7 @@ int hsde_iterate(hsde_handle* h, int32_t k, int32_t* status_out) {
     const double t0 = now_ms();
     CK(cudaSetDevice(h->device));
     for (int32_t it = 0; it < k; ++it) {
+        h->launched++;
         if (h->exec) {
             CK(cudaGraphLaunch(h->exec, h->st));
         } else {
@@ -765,6 +827,7 @@ int hsde_set_state(hsde_handle* h, int32_t i, const double* state, int32_t itera
     const double kappa = *p++;
     InstDev I = h->host_inst[i];
     I.tau = tau; I.kappa = kappa; I.status = HSDE_RUNNING; I.iter = iterations; I.eta = 0.0;
+    I.vcold = 1;
     CK(cudaMemcpy(h->V.inst + i, &I, sizeof(InstDev), cudaMemcpyHostToDevice));
     h->host_inst[i] = I;
     return HSDE_OK;
@@ -829,6 +892,37 @@ int hsde_get_certificate(hsde_handle* h, int32_t i, int32_t kind, double* y, dou
             for (int64_t e = 0; e < N; ++e) X[e] /= nctx;
         }
     }
+    return HSDE_OK;
+}
+
+int hsde_get_profile(hsde_handle* h, hsde_profile* out) {
+    if (!h || !out) return fail(HSDE_EINVAL, "null argument");
+    std::memset(out, 0, sizeof(*out));
+    out->kernels_per_iteration = h->kernels_per_iter;
+    if (!h->profile || h->launched == 0) return HSDE_OK;
+    CK(cudaSetDevice(h->device));
+    CK(cudaStreamSynchronize(h->st));
+    int np = 0;
+    auto put = [&](const char* name, cudaEvent_t a, cudaEvent_t b, int64_t units) -> int {
+        if (np >= HSDE_MAX_PHASES) return HSDE_OK;
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, a, b));
+        out->phase_ms[np] = ms;
+        std::snprintf(out->phase_name[np], sizeof(out->phase_name[np]), "%s", name);
+        out->phase_units[np] = units;
+        ++np;
+        return HSDE_OK;
+    };
+    int rc;
+    if ((rc = put("affine", h->ev_it0, h->ev_aff, h->V.Ntot)) != HSDE_OK) return rc;
+    for (size_t i = 0; i < h->buckets.size(); ++i) {
+        char nm[24];
+        std::snprintf(nm, sizeof(nm), "cone_c%d", h->buckets[i].cmax);
+        if ((rc = put(nm, h->ev_cs[i], h->ev_ce[i], h->bucket_c3[i])) != HSDE_OK) return rc;
+    }
+    if ((rc = put("check", h->ev_chk, h->ev_it1, h->V.Ntot)) != HSDE_OK) return rc;
+    if ((rc = put("iteration", h->ev_it0, h->ev_it1, h->V.Ntot)) != HSDE_OK) return rc;
+    out->nphases = np;
     return HSDE_OK;
 }
 

@@ -11,15 +11,22 @@
 //   z     = s - a,   v = v_hat
 // and the stopping-rule partial ||H_k xh - s||^2 (full-vec weights).
 //
-// Eigensolver: cyclic two-sided Jacobi (Golub & Van Loan, symmetric Schur
-// decomposition by 2x2 rotations) in shared memory, parallel ordering by the
-// round-robin ("circle") tournament so that the c/2 rotations of a round are
-// disjoint.  A rotation pair (kr, kc) updates the 2x2 block of rows
-// {p_kr, q_kr} x columns {p_kc, q_kc} as J_kr^T X J_kc in place, so one pass
-// applies the whole round to A; V <- V J in the same pass.  Odd sizes are
-// padded with a zero row/column that is never rotated.  A group of G threads
-// owns one clique (G = 8, 16 or 32 lanes of a warp, or a whole CTA for larger
-// cliques); groups never wait on each other.
+// Eigensolver: two-sided cyclic Jacobi (symmetric Schur decomposition by 2x2
+// rotations, Golub & Van Loan) with a parallel round-robin ordering.  The
+// matrix is padded to CP (the bucket's size, a compile-time constant) with
+// zero rows/columns that are never rotated.  Rows and columns live in "slots":
+// in every round slot pair (2k, 2k+1) is rotated, and the result of each 2x2
+// block J_r^T X J_c is written straight to the slots those indices occupy in
+// the next round (ping-pong buffers), following the circle tournament
+// (slot 0 fixed, the others advance one place), so every index pair meets
+// once per sweep.  V keeps original indices on its rows and slots on its
+// columns, so no permutation has to be tracked: s = V max(diag A, 0) V^T.
+// Warm start: V of the previous iteration (per clique, FP32/FP64 as the
+// clique arrays) seeds the next solve through A <- V^T A V, with a cold start
+// every `refresh` iterations to bound the loss of orthogonality.
+//
+// A group of G threads owns one clique; groups never wait on each other
+// (sub-warp shuffles for G < 32, named barriers for G > 32).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -28,18 +35,27 @@
 
 namespace hsde {
 
-template <typename T, int CMAX, int G>
+template <typename T, int CP_, int G_>
 struct ConeCfg {
-    static constexpr int LD = CMAX + 1;
-    static constexpr int K = CMAX / 2;
-    static constexpr int NTH = (G >= 128) ? G : 128;
-    static constexpr int GPB = NTH / G;
-    // per group: A, V, rot cos/sin/tan, lambda, reduction scratch (T), then rot p/q (int)
-    static constexpr size_t t_elems = 2 * CMAX * LD + 3 * K + CMAX + 32;
-    static constexpr size_t bytes = t_elems * sizeof(T) + 2 * K * sizeof(int);
-    static constexpr size_t group_bytes = (bytes + 15) / 16 * 16;
+    static constexpr int CP = CP_;
+    static constexpr int G = G_;
+    static constexpr int K = CP / 2;
+    static constexpr int LD = CP + 2;                 // even row stride: 2-vector loads stay aligned
+    static constexpr int NTH = (G >= 128) ? G : 128;  // threads per CTA
+    static constexpr int GPB = NTH / G;               // groups (cliques) per CTA
+    static constexpr int NBLK = K * K;
+    static constexpr int BPL = (NBLK + G - 1) / G;    // 2x2 blocks per thread per round
+    static constexpr int NVP = CP * K;
+    static constexpr int VPL = (NVP + G - 1) / G;     // V pairs per thread per round
+    // per group: A0, A1, V0, V1 (CP x LD), rot (cs,sn) K, tan K, lambda CP, red 32
+    static constexpr size_t t_elems = 4 * CP * LD + 2 * K + K + CP + 32;
+    static constexpr size_t group_bytes = (t_elems * sizeof(T) + 15) / 16 * 16;
     static constexpr size_t smem = GPB * group_bytes;
 };
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
 
 template <int G>
 __device__ __forceinline__ unsigned gmask() {
@@ -52,13 +68,18 @@ __device__ __forceinline__ unsigned gmask() {
 }
 
 template <int G>
-__device__ __forceinline__ void gsync() {
-    if constexpr (G <= 32) __syncwarp(gmask<G>());
-    else __syncthreads();
+__device__ __forceinline__ void gsync(int gid) {
+    if constexpr (G <= 32) {
+        __syncwarp(gmask<G>());
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(G) : "memory");
+    }
 }
 
+// Sum over the group; every thread of the group gets the same value, summed
+// in a fixed order.
 template <int G, typename T>
-__device__ __forceinline__ T gsum(T v, T* red) {
+__device__ __forceinline__ T gsum(T v, T* red, int gid) {
     if constexpr (G <= 32) {
         const unsigned mask = gmask<G>();
 #pragma unroll
@@ -67,26 +88,27 @@ __device__ __forceinline__ T gsum(T v, T* red) {
     } else {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-        __syncthreads();
+        const int w = (threadIdx.x % G) >> 5;
+        gsync<G>(gid);
+        if ((threadIdx.x & 31) == 0) red[w] = v;
+        gsync<G>(gid);
         T t = 0;
 #pragma unroll
         for (int i = 0; i < G / 32; ++i) t += red[i];
-        __syncthreads();
+        gsync<G>(gid);
         return t;
     }
 }
 
-__device__ __forceinline__ void rr_pair(int r, int k, int cp, int& p, int& q) {
-    const int mm = cp - 1;
-    if (k == 0) {
-        p = mm;
-        q = r;
-    } else {
-        p = (r + k) % mm;
-        q = (r - k + mm) % mm;
-    }
+// Circle-tournament slot map: slot 0 stays, the others advance along
+// T1 -> T2 -> ... -> T(K-1) -> B(K-1) -> ... -> B0 -> T1  (Tk = 2k, Bk = 2k+1).
+template <int CP>
+__device__ __forceinline__ int sigma(int j) {
+    constexpr int K = CP / 2;
+    if (j == 0) return 0;
+    const int k = j >> 1;
+    if (j & 1) return k == 0 ? 2 : j - 2;
+    return k == K - 1 ? j + 1 : j + 2;
 }
 
 template <typename T>
@@ -96,244 +118,268 @@ __device__ __forceinline__ float t_sqrt<float>(float x) { return sqrtf(x); }
 template <>
 __device__ __forceinline__ double t_sqrt<double>(double x) { return sqrt(x); }
 
-template <typename T, int CMAX, int G>
-__global__ void __launch_bounds__(ConeCfg<T, CMAX, G>::NTH)
-k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T tol2) {
-    using C = ConeCfg<T, CMAX, G>;
-    constexpr int LD = C::LD;
+template <typename Cfg, typename T>
+__device__ __forceinline__ void jacobi_round(const T* __restrict__ A, T* __restrict__ An,
+                                             const T* __restrict__ Vc, T* __restrict__ Vn,
+                                             T* __restrict__ rot, T* __restrict__ tan_, int lane, int gid) {
+    constexpr int CP = Cfg::CP, K = Cfg::K, LD = Cfg::LD, G = Cfg::G;
+    using V2 = typename Vec2<T>::type;
+    // rotation of every slot pair (2k, 2k+1)
+    if (lane < K) {
+        const int k = lane;
+        const T app = A[(2 * k) * LD + 2 * k], aqq = A[(2 * k + 1) * LD + 2 * k + 1];
+        const T apq = A[(2 * k) * LD + 2 * k + 1];
+        T cs = 1, sn = 0, t = 0;
+        if (apq != T(0)) {
+            const T theta = (aqq - app) / (T(2) * apq);
+            t = T(1) / (fabs(theta) + t_sqrt<T>(T(1) + theta * theta));
+            if (theta < T(0)) t = -t;
+            cs = T(1) / t_sqrt<T>(T(1) + t * t);
+            sn = t * cs;
+        }
+        rot[2 * k] = cs;
+        rot[2 * k + 1] = sn;
+        tan_[k] = t;
+    }
+    gsync<G>(gid);
+#pragma unroll
+    for (int i = 0; i < Cfg::BPL; ++i) {
+        const int b = lane + i * G;
+        if (Cfg::NBLK % G == 0 || b < Cfg::NBLK) {
+            const int kr = b / K, kc = b - (b / K) * K;
+            const int r0 = sigma<CP>(2 * kr), r1 = sigma<CP>(2 * kr + 1);
+            if (kr == kc) {
+                const T t = tan_[kr];
+                const T app = A[(2 * kr) * LD + 2 * kr], aqq = A[(2 * kr + 1) * LD + 2 * kr + 1];
+                const T apq = A[(2 * kr) * LD + 2 * kr + 1];
+                An[r0 * LD + r0] = app - t * apq;
+                An[r1 * LD + r1] = aqq + t * apq;
+                const T off = (t == T(0)) ? apq : T(0);
+                An[r0 * LD + r1] = off;
+                An[r1 * LD + r0] = off;
+            } else {
+                const int c0 = sigma<CP>(2 * kc), c1 = sigma<CP>(2 * kc + 1);
+                const V2 top = *reinterpret_cast<const V2*>(A + (2 * kr) * LD + 2 * kc);
+                const V2 bot = *reinterpret_cast<const V2*>(A + (2 * kr + 1) * LD + 2 * kc);
+                const V2 rr = *reinterpret_cast<const V2*>(rot + 2 * kr);
+                const V2 rc = *reinterpret_cast<const V2*>(rot + 2 * kc);
+                // J_r^T X
+                const T y00 = rr.x * top.x - rr.y * bot.x, y01 = rr.x * top.y - rr.y * bot.y;
+                const T y10 = rr.y * top.x + rr.x * bot.x, y11 = rr.y * top.y + rr.x * bot.y;
+                // (.) J_c
+                An[r0 * LD + c0] = rc.x * y00 - rc.y * y01;
+                An[r0 * LD + c1] = rc.y * y00 + rc.x * y01;
+                An[r1 * LD + c0] = rc.x * y10 - rc.y * y11;
+                An[r1 * LD + c1] = rc.y * y10 + rc.x * y11;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Cfg::VPL; ++i) {
+        const int b = lane + i * G;
+        if (Cfg::NVP % G == 0 || b < Cfg::NVP) {
+            const int row = b / K, kc = b - (b / K) * K;
+            const V2 vv = *reinterpret_cast<const V2*>(Vc + row * LD + 2 * kc);
+            const V2 rc = *reinterpret_cast<const V2*>(rot + 2 * kc);
+            Vn[row * LD + sigma<CP>(2 * kc)] = rc.x * vv.x - rc.y * vv.y;
+            Vn[row * LD + sigma<CP>(2 * kc + 1)] = rc.y * vv.x + rc.x * vv.y;
+        }
+    }
+    gsync<G>(gid);
+}
+
+template <typename T, int CP, int G>
+__global__ void __launch_bounds__(ConeCfg<T, CP, G>::NTH)
+k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T tol2, int warm, int refresh) {
+    using Cfg = ConeCfg<T, CP, G>;
+    constexpr int LD = Cfg::LD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int g = threadIdx.x / G, lane = threadIdx.x % G;
-    const int li = blockIdx.x * C::GPB + g;
+    const int gid = threadIdx.x / G, lane = threadIdx.x % G;
+    const int li = blockIdx.x * Cfg::GPB + gid;
     if (li >= nlist) return;
     const int k = list[li];
     const InstDev& I = V.inst[V.cl_inst[k]];
     if (I.status != HSDE_RUNNING) return;
 
-    unsigned char* base = smem_raw + (size_t)g * C::group_bytes;
-    T* A = reinterpret_cast<T*>(base);
-    T* Vm = A + CMAX * LD;
-    T* rc = Vm + CMAX * LD;
-    T* rs = rc + C::K;
-    T* rt = rs + C::K;
-    T* lam = rt + C::K;
-    T* red = lam + CMAX;
-    int* rp = reinterpret_cast<int*>(red + 32);
-    int* rq = rp + C::K;
+    T* A0 = reinterpret_cast<T*>(smem_raw + (size_t)gid * Cfg::group_bytes);
+    T* A1 = A0 + CP * LD;
+    T* V0 = A1 + CP * LD;
+    T* V1 = V0 + CP * LD;
+    T* rot = V1 + CP * LD;
+    T* tan_ = rot + 2 * Cfg::K;
+    T* lam = tan_ + Cfg::K;
+    T* red = lam + CP;
 
     T* s = reinterpret_cast<T*>(V.s);
     T* z = reinterpret_cast<T*>(V.z);
     T* v = reinterpret_cast<T*>(V.v);
     const int c = V.cl_size[k];
-    const int cp = (c + 1) & ~1;
-    const int K = cp >> 1;
     const int64_t off = V.cl_off[k];
     const double eta = I.eta;
+    T* Vst = V.vstore ? reinterpret_cast<T*>(V.vstore) + V.vs_off[k] : nullptr;
+    const bool use_warm = warm && Vst != nullptr && !I.vcold && refresh > 1 && (I.iter % refresh) != 1;
 
-    for (int idx = lane; idx < cp * cp; idx += G) {
-        const int i = idx / cp, j = idx - (idx / cp) * cp;
-        A[i * LD + j] = T(0);
-        Vm[i * LD + j] = (i == j) ? T(1) : T(0);
+    // zero A0 (padding included); V0 = I or the stored basis
+    for (int idx = lane; idx < CP * CP; idx += G) {
+        const int i = idx / CP, j = idx - (idx / CP) * CP;
+        A0[i * LD + j] = T(0);
+        V0[i * LD + j] = use_warm ? Vst[idx] : ((i == j) ? T(1) : T(0));
     }
-    gsync<G>();
-    // gather + rank-one correction: a = s_hat - z
-    for (int b = 0, colbase = 0; b < c; colbase += c - b, ++b) {
-        for (int a = b + lane; a < c; a += G) {
-            const int64_t j = off + colbase + (a - b);
-            const int gi = V.gmap[j];
-            const double gx = V.xw[gi] - eta * V.xp[gi];
-            const double av = 0.5 * ((double)s[j] - (double)z[j] - (double)v[j] + gx);
-            A[a * LD + b] = (T)av;
-            A[b * LD + a] = (T)av;
+    gsync<G>(gid);
+    // gather + rank-one correction: a = s_hat - z  (lower entries, mirrored)
+    for (int idx = lane; idx < c * c; idx += G) {
+        const int bcol = idx / c, arow = idx - bcol * c;
+        if (arow < bcol) continue;
+        const int64_t j = off + (int64_t)bcol * c - (bcol * (bcol - 1)) / 2 + (arow - bcol);
+        const int gi = V.gmap[j];
+        const double gx = V.xw[gi] - eta * V.xp[gi];
+        const double av = 0.5 * ((double)s[j] - (double)z[j] - (double)v[j] + gx);
+        A0[arow * LD + bcol] = (T)av;
+        A0[bcol * LD + arow] = (T)av;
+    }
+    gsync<G>(gid);
+    T* A = A0;
+    T* An = A1;
+    T* Vc = V0;
+    T* Vn = V1;
+    if (use_warm) {
+        // An = A Vc, then A = Vc^T An  (A symmetric); result kept symmetric
+        for (int idx = lane; idx < CP * CP; idx += G) {
+            const int i = idx / CP, j = idx - (idx / CP) * CP;
+            T acc = 0;
+#pragma unroll 8
+            for (int q = 0; q < CP; ++q) acc += A[i * LD + q] * Vc[q * LD + j];
+            An[i * LD + j] = acc;
         }
+        gsync<G>(gid);
+        for (int idx = lane; idx < CP * CP; idx += G) {
+            const int i = idx / CP, j = idx - (idx / CP) * CP;
+            if (i < j) continue;
+            T acc = 0;
+#pragma unroll 8
+            for (int q = 0; q < CP; ++q) acc += Vc[q * LD + i] * An[q * LD + j];
+            A[i * LD + j] = acc;
+            A[j * LD + i] = acc;
+        }
+        gsync<G>(gid);
     }
-    gsync<G>();
 
     for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
-        // convergence test on the off-diagonal mass
         T offd = 0, tot = 0;
-        for (int idx = lane; idx < c * c; idx += G) {
-            const int i = idx / c, j = idx - (idx / c) * c;
+        for (int idx = lane; idx < CP * CP; idx += G) {
+            const int i = idx / CP, j = idx - (idx / CP) * CP;
             const T a = A[i * LD + j];
             tot += a * a;
             if (i != j) offd += a * a;
         }
-        offd = gsum<G>(offd, red);
-        tot = gsum<G>(tot, red);
+        offd = gsum<G>(offd, red, gid);
+        tot = gsum<G>(tot, red, gid);
         if (offd <= tol2 * tot || sweep == max_sweeps) break;
-        for (int r = 0; r < cp - 1; ++r) {
-            if (lane < K) {
-                int p, q;
-                rr_pair(r, lane, cp, p, q);
-                const T app = A[p * LD + p], aqq = A[q * LD + q], apq = A[p * LD + q];
-                T cs = 1, sn = 0, t = 0;
-                if (apq != T(0)) {
-                    const T theta = (aqq - app) / (T(2) * apq);
-                    const T at = fabs(theta);
-                    t = T(1) / (at + t_sqrt<T>(T(1) + theta * theta));
-                    if (theta < T(0)) t = -t;
-                    cs = T(1) / t_sqrt<T>(T(1) + t * t);
-                    sn = t * cs;
-                }
-                rp[lane] = p; rq[lane] = q;
-                rc[lane] = cs; rs[lane] = sn; rt[lane] = t;
-            }
-            gsync<G>();
-            for (int idx = lane; idx < K * K; idx += G) {
-                const int kr = idx / K, kc = idx - (idx / K) * K;
-                const int pr = rp[kr], qr = rq[kr];
-                if (kr == kc) {
-                    const T t = rt[kr];
-                    if (t != T(0)) {
-                        const T apq = A[pr * LD + qr];
-                        A[pr * LD + pr] -= t * apq;
-                        A[qr * LD + qr] += t * apq;
-                        A[pr * LD + qr] = T(0);
-                        A[qr * LD + pr] = T(0);
-                    }
-                } else {
-                    const int pc = rp[kc], qc = rq[kc];
-                    const T cr = rc[kr], sr = rs[kr], cc = rc[kc], sc = rs[kc];
-                    const T x00 = A[pr * LD + pc], x01 = A[pr * LD + qc];
-                    const T x10 = A[qr * LD + pc], x11 = A[qr * LD + qc];
-                    const T y00 = cr * x00 - sr * x10, y01 = cr * x01 - sr * x11;
-                    const T y10 = sr * x00 + cr * x10, y11 = sr * x01 + cr * x11;
-                    A[pr * LD + pc] = cc * y00 - sc * y01;
-                    A[pr * LD + qc] = sc * y00 + cc * y01;
-                    A[qr * LD + pc] = cc * y10 - sc * y11;
-                    A[qr * LD + qc] = sc * y10 + cc * y11;
-                }
-            }
-            for (int idx = lane; idx < cp * K; idx += G) {
-                const int i = idx / K, kc = idx - (idx / K) * K;
-                const int pc = rp[kc], qc = rq[kc];
-                const T cc = rc[kc], sc = rs[kc];
-                const T vp = Vm[i * LD + pc], vq = Vm[i * LD + qc];
-                Vm[i * LD + pc] = cc * vp - sc * vq;
-                Vm[i * LD + qc] = sc * vp + cc * vq;
-            }
-            gsync<G>();
+        for (int r = 0; r < CP - 1; ++r) {
+            jacobi_round<Cfg>(A, An, Vc, Vn, rot, tan_, lane, gid);
+            T* t1 = A; A = An; An = t1;
+            T* t2 = Vc; Vc = Vn; Vn = t2;
         }
     }
-    for (int i = lane; i < cp; i += G) lam[i] = fmax(A[i * LD + i], T(0));
-    gsync<G>();
+    for (int i = lane; i < CP; i += G) lam[i] = fmax(A[i * LD + i], T(0));
+    if (Vst != nullptr && warm) {
+        for (int idx = lane; idx < CP * CP; idx += G) {
+            const int i = idx / CP, j = idx - (idx / CP) * CP;
+            Vst[idx] = Vc[i * LD + j];
+        }
+    }
+    gsync<G>(gid);
 
     double res = 0.0;
-    for (int b = 0, colbase = 0; b < c; colbase += c - b, ++b) {
-        for (int a = b + lane; a < c; a += G) {
-            T acc = 0;
-            for (int q = 0; q < c; ++q) acc += Vm[a * LD + q] * lam[q] * Vm[b * LD + q];
-            const int64_t j = off + colbase + (a - b);
-            const int gi = V.gmap[j];
-            const double gx = V.xw[gi] - eta * V.xp[gi];
-            const double so = s[j], zo = z[j], vo = v[j];
-            const double av = 0.5 * (so - zo - vo + gx);
-            const double vn = 0.5 * (so + zo + vo - gx);
-            const double sn = (double)acc;
-            s[j] = (T)sn;
-            z[j] = (T)(sn - av);
-            v[j] = (T)vn;
-            const double d = gx - sn;
-            res += (a == b ? 1.0 : 2.0) * d * d;
-        }
+    for (int idx = lane; idx < c * c; idx += G) {
+        const int bcol = idx / c, arow = idx - bcol * c;
+        if (arow < bcol) continue;
+        T acc = 0;
+#pragma unroll 8
+        for (int q = 0; q < CP; ++q) acc += Vc[arow * LD + q] * lam[q] * Vc[bcol * LD + q];
+        const int64_t j = off + (int64_t)bcol * c - (bcol * (bcol - 1)) / 2 + (arow - bcol);
+        const int gi = V.gmap[j];
+        const double gx = V.xw[gi] - eta * V.xp[gi];
+        const double so = s[j], zo = z[j], vo = v[j];
+        const double av = 0.5 * (so - zo - vo + gx);
+        const double vn = 0.5 * (so + zo + vo - gx);
+        const double sn = (double)acc;
+        s[j] = (T)sn;
+        z[j] = (T)(sn - av);
+        v[j] = (T)vn;
+        const double d = gx - sn;
+        res += (arow == bcol ? 1.0 : 2.0) * d * d;
     }
-    // fixed-order group reduction in double
-    if constexpr (G <= 32) {
-        const unsigned mask = gmask<G>();
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) res += __shfl_xor_sync(mask, res, o, G);
-        if (lane == 0) V.cl_part[k] = res;
-    } else {
-        double* dred = reinterpret_cast<double*>(A);   // A is no longer needed
-        __syncthreads();
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) res += __shfl_xor_sync(0xffffffffu, res, o);
-        if ((threadIdx.x & 31) == 0) dred[threadIdx.x >> 5] = res;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0;
-            for (int i = 0; i < G / 32; ++i) t += dred[i];
-            V.cl_part[k] = t;
-        }
-    }
+    res = gsum<G>(res, reinterpret_cast<double*>(red), gid);
+    if (lane == 0) V.cl_part[k] = res;
 }
 
-template <typename T, int CMAX, int G>
-static int launch_one(const DevView& V, const Bucket& bk, int max_sweeps, double tol, cudaStream_t st) {
-    using C = ConeCfg<T, CMAX, G>;
-    auto kern = k_cone<T, CMAX, G>;
-    const int grid = (bk.count + C::GPB - 1) / C::GPB;
-    kern<<<grid, C::NTH, C::smem, st>>>(V, bk.list, bk.count, max_sweeps, (T)(tol * tol));
-    return HSDE_OK;
-}
+// ---------------------------------------------------------------------------
+// buckets: padded size CP and threads per clique G
+// ---------------------------------------------------------------------------
+#define HSDE_CONE_BUCKETS(X) \
+    X(4, 4) X(8, 8) X(12, 16) X(16, 32) X(24, 64) X(32, 128) X(40, 128) X(48, 256) X(64, 256)
 
-template <typename T, int CMAX, int G>
+template <typename T, int CP, int G>
 static int prepare_one() {
-    using C = ConeCfg<T, CMAX, G>;
-    if (C::smem > 48 * 1024) {
-        if (cudaFuncSetAttribute(k_cone<T, CMAX, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)C::smem) != cudaSuccess)
+    using Cfg = ConeCfg<T, CP, G>;
+    if (Cfg::smem > 48 * 1024) {
+        if (cudaFuncSetAttribute(k_cone<T, CP, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Cfg::smem) != cudaSuccess)
             return HSDE_ECUDA;
     }
     return HSDE_OK;
 }
 
-// Opt every variant into its dynamic shared memory size (outside any capture).
+template <typename T, int CP, int G>
+static void launch_one(const DevView& V, const Bucket& bk, int max_sweeps, double tol, int warm, int refresh,
+                       cudaStream_t st) {
+    using Cfg = ConeCfg<T, CP, G>;
+    const int grid = (bk.count + Cfg::GPB - 1) / Cfg::GPB;
+    k_cone<T, CP, G><<<grid, Cfg::NTH, Cfg::smem, st>>>(V, bk.list, bk.count, max_sweeps, (T)(tol * tol), warm,
+                                                        refresh);
+}
+
+int cone_bucket_of(int c) {
+#define X(cp, g) if (c <= cp) return cp;
+    HSDE_CONE_BUCKETS(X)
+#undef X
+    return -1;
+}
+
+int cone_vstore_elems(int c) {
+    const int cp = cone_bucket_of(c);
+    return cp < 0 ? -1 : cp * cp;
+}
+
 int cone_prepare(bool mixed) {
     int rc = HSDE_OK;
-    if (mixed) {
-        rc |= prepare_one<float, 8, 8>();
-        rc |= prepare_one<float, 16, 16>();
-        rc |= prepare_one<float, 32, 32>();
-        rc |= prepare_one<float, 64, 128>();
-        rc |= prepare_one<float, 128, 256>();
-    } else {
-        rc |= prepare_one<double, 8, 8>();
-        rc |= prepare_one<double, 16, 16>();
-        rc |= prepare_one<double, 32, 32>();
-        rc |= prepare_one<double, 64, 128>();
-    }
+#define X(cp, g) rc |= mixed ? prepare_one<float, cp, g>() : prepare_one<double, cp, g>();
+    HSDE_CONE_BUCKETS(X)
+#undef X
     return rc == HSDE_OK ? HSDE_OK : HSDE_ECUDA;
 }
 
 int cone_smem_bytes(int cmax, bool mixed) {
-    if (mixed) {
-        switch (cmax) {
-            case 8: return (int)ConeCfg<float, 8, 8>::smem;
-            case 16: return (int)ConeCfg<float, 16, 16>::smem;
-            case 32: return (int)ConeCfg<float, 32, 32>::smem;
-            case 64: return (int)ConeCfg<float, 64, 128>::smem;
-            case 128: return (int)ConeCfg<float, 128, 256>::smem;
-        }
-    } else {
-        switch (cmax) {
-            case 8: return (int)ConeCfg<double, 8, 8>::smem;
-            case 16: return (int)ConeCfg<double, 16, 16>::smem;
-            case 32: return (int)ConeCfg<double, 32, 32>::smem;
-            case 64: return (int)ConeCfg<double, 64, 128>::smem;
-        }
-    }
+#define X(cp, g) \
+    if (cmax == cp) return mixed ? (int)ConeCfg<float, cp, g>::smem : (int)ConeCfg<double, cp, g>::smem;
+    HSDE_CONE_BUCKETS(X)
+#undef X
     return -1;
 }
 
-int launch_cone(const DevView& V, const Bucket& bk, bool mixed, int max_sweeps, double tol, void* stp) {
+int launch_cone(const DevView& V, const Bucket& bk, bool mixed, int max_sweeps, double tol, int warm, int refresh,
+                void* stp) {
     if (bk.count == 0) return HSDE_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stp);
-    if (mixed) {
-        switch (bk.cmax) {
-            case 8: return launch_one<float, 8, 8>(V, bk, max_sweeps, tol, st);
-            case 16: return launch_one<float, 16, 16>(V, bk, max_sweeps, tol, st);
-            case 32: return launch_one<float, 32, 32>(V, bk, max_sweeps, tol, st);
-            case 64: return launch_one<float, 64, 128>(V, bk, max_sweeps, tol, st);
-            case 128: return launch_one<float, 128, 256>(V, bk, max_sweeps, tol, st);
-        }
-    } else {
-        switch (bk.cmax) {
-            case 8: return launch_one<double, 8, 8>(V, bk, max_sweeps, tol, st);
-            case 16: return launch_one<double, 16, 16>(V, bk, max_sweeps, tol, st);
-            case 32: return launch_one<double, 32, 32>(V, bk, max_sweeps, tol, st);
-            case 64: return launch_one<double, 64, 128>(V, bk, max_sweeps, tol, st);
-        }
+#define X(cp, g)                                                                        \
+    if (bk.cmax == cp) {                                                                \
+        if (mixed) launch_one<float, cp, g>(V, bk, max_sweeps, tol, warm, refresh, st); \
+        else launch_one<double, cp, g>(V, bk, max_sweeps, tol, warm, refresh, st);     \
+        return HSDE_OK;                                                                 \
     }
+    HSDE_CONE_BUCKETS(X)
+#undef X
     return HSDE_ERANGE;
 }
 

@@ -48,7 +48,7 @@ struct InstDev {
     int32_t dense;           // S stored dense (1) or diagonal (0)
     int32_t status;          // HSDE_RUNNING ...
     int32_t iter;            // iterations done
-    int32_t _pad;
+    int32_t vcold;           // 1: the stored eigenbases are not valid (cold start next)
     // cached by setup
     double den;              // 1 + zeta^T M^{-1} zeta
     double ctp;              // c^T x_p - b^T y_p
@@ -84,6 +84,8 @@ struct DevView {
     // packed clique space (float or double)
     void* s; void* z; void* v;
     const int32_t* gmap;     // absolute x index per packed entry
+    void* vstore;            // per-clique eigenbasis of the last solve (warm start), or null
+    const int64_t* vs_off;   // [ncl] offset of each clique's CP x CP basis in vstore
     const int32_t* cl_off; const int32_t* cl_size; const int32_t* cl_inst;
     // instances and tiles
     InstDev* inst;
@@ -98,7 +100,7 @@ struct DevView {
 
 // Bucket of cliques handled by one eigensolver variant.
 struct Bucket {
-    int32_t cmax;            // 8, 16, 32, 64, 128
+    int32_t cmax;            // padded size CP of the bucket (4 ... 64)
     int32_t count;
     int32_t* list;           // device array of clique ids (largest first)
 };
@@ -120,8 +122,10 @@ void launch_setup_den(const DevView& V, void* st);
 // cone projection of every clique in one bucket (Eq. Step2 on S, fused with
 // the H gather, the rank-one correction and the nu update of Eq. Step3)
 int  launch_cone(const DevView& V, const Bucket& bk, bool mixed, int max_sweeps, double tol,
-                 void* st);
+                 int warm, int refresh, void* st);
 int  cone_smem_bytes(int cmax, bool mixed);
+int  cone_bucket_of(int c);          // padded size of the bucket of a clique of size c, -1 if none
+int  cone_vstore_elems(int c);       // stored basis size for a clique of size c
 int  cone_prepare(bool mixed);
 // Gauss-Jordan inversion of the dense S matrices (setup)
 void launch_gj_step(double* pool, const int64_t* offs, const int32_t* ms, int ndense,

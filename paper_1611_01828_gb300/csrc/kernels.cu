@@ -234,7 +234,11 @@ __global__ void __launch_bounds__(NT) k_check_m(DevView V) {
 __global__ void __launch_bounds__(NT) k_verdict(DevView V) {
     __shared__ double sh[32];
     InstDev& I = V.inst[blockIdx.x];
-    if (I.status != HSDE_RUNNING || !is_check_iter(V, I.iter)) return;
+    const int running = I.status == HSDE_RUNNING;
+    const int iter = I.iter;
+    __syncthreads();
+    if (threadIdx.x == 0 && running) I.vcold = 0;   // stored eigenbases are valid from now on
+    if (!running || !is_check_iter(V, iter)) return;
     double a1 = 0, a2 = 0, a3 = 0;
     for (int t = I.tile_begin + threadIdx.x; t < I.tile_end; t += NT) {
         const double* pp = V.part + (int64_t)t * KPART;

@@ -35,7 +35,9 @@ class hsde_problem(C.Structure):
 class hsde_options(C.Structure):
     _fields_ = [("eps_tol", C.c_double), ("max_iter", C.c_int32), ("check_every", C.c_int32),
                 ("precision", C.c_int32), ("device", C.c_int32), ("cuda_stream", C.c_void_p),
-                ("jacobi_max_sweeps", C.c_int32), ("use_graph", C.c_int32), ("jacobi_tol", C.c_double)]
+                ("jacobi_max_sweeps", C.c_int32), ("use_graph", C.c_int32), ("jacobi_tol", C.c_double),
+                ("profile", C.c_int32), ("warm_start", C.c_int32), ("warm_refresh", C.c_int32),
+                ("_pad", C.c_int32)]
 
 
 class hsde_sizes(C.Structure):
@@ -49,6 +51,15 @@ class hsde_info(C.Structure):
                 ("dres", C.c_double), ("gap", C.c_double), ("pobj", C.c_double), ("dobj", C.c_double),
                 ("tau", C.c_double), ("kappa", C.c_double), ("pinf_ratio", C.c_double),
                 ("dinf_ratio", C.c_double), ("setup_ms", C.c_double), ("iterate_ms", C.c_double)]
+
+
+MAX_PHASES = 16
+
+
+class hsde_profile(C.Structure):
+    _fields_ = [("kernels_per_iteration", C.c_int32), ("nphases", C.c_int32),
+                ("phase_ms", C.c_double * MAX_PHASES), ("phase_name", (C.c_char * 24) * MAX_PHASES),
+                ("phase_units", C.c_int64 * MAX_PHASES)]
 
 
 # Every function declared in include/hsde.h: name -> (restype, argtypes)
@@ -72,6 +83,7 @@ _SIGS = {
     "hsde_set_state": (C.c_int, [C.c_void_p, C.c_int32, _f64p, C.c_int32]),
     "hsde_get_solution": (C.c_int, [C.c_void_p, C.c_int32, _f64p, _f64p, _f64p, _f64p, _f64p]),
     "hsde_get_certificate": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _f64p, _f64p, _f64p]),
+    "hsde_get_profile": (C.c_int, [C.c_void_p, C.POINTER(hsde_profile)]),
     "hsde_destroy": (None, [C.c_void_p]),
 }
 
@@ -243,6 +255,13 @@ class Handle:
         _ck(lib.hsde_get_certificate(self.h, i, int(kind), _ptr(y, C.c_double), _ptr(Z, C.c_double),
                                      _ptr(X, C.c_double)), "hsde_get_certificate")
         return (y, Z) if kind == PRIMAL_INFEASIBLE else X
+
+    def hsde_get_profile(self) -> dict:
+        pr = hsde_profile()
+        _ck(lib.hsde_get_profile(self.h, C.byref(pr)), "hsde_get_profile")
+        phases = {pr.phase_name[i].value.decode(): (pr.phase_ms[i], int(pr.phase_units[i]))
+                  for i in range(pr.nphases)}
+        return dict(kernels_per_iteration=pr.kernels_per_iteration, phases=phases)
 
     # ---- convenience: run to a verdict in chunks ----
     def solve(self, chunk: int = 20):

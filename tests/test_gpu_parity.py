@@ -206,17 +206,30 @@ def test_batch_equals_single_bitwise(hs):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_checkpoint_resume_bitwise(hs, prec):
+    # bitwise only without the eigensolver warm start (its basis is not state)
     p = PROBS["cfg0"]()
-    with hs.Handle(p, precision=prec) as H:
+    with hs.Handle(p, precision=prec, warm_start=0) as H:
         H.hsde_iterate(40)
         straight = H.hsde_get_state(0)
-    with hs.Handle(p, precision=prec) as H:
+    with hs.Handle(p, precision=prec, warm_start=0) as H:
         H.hsde_iterate(15)
         mid = H.hsde_get_state(0)
-    with hs.Handle(p, precision=prec) as H:
+    with hs.Handle(p, precision=prec, warm_start=0) as H:
         H.hsde_set_state(0, mid, 15)
         H.hsde_iterate(25)
         assert np.array_equal(H.hsde_get_state(0), straight)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
+@pytest.mark.parametrize("name", ["cfg0", "arrow_buckets", "grid_7x9"])
+def test_warm_start_matches_cold_start(hs, prec, tol, name):
+    p = PROBS[name]()
+    out = {}
+    for w in (0, 1):
+        with hs.Handle(p, precision=prec, warm_start=w, warm_refresh=16) as H:
+            H.hsde_iterate(60)
+            out[w] = H.hsde_get_state(0)
+    assert rel(out[1], out[0]) < tol
 
 
 def test_graph_and_eager_agree_bitwise(hs):
