@@ -100,7 +100,8 @@ typedef struct hsde_options {
     int32_t profile;      /* 1: record CUDA events around each phase of every
                              iteration (read back with hsde_get_profile)        */
     int32_t warm_start;   /* eigensolver warm start from the previous iteration's
-                             eigenbasis of each clique: -1 default (on), 0 off,
+                             eigenbasis of each clique: -1 default (on in
+                             HSDE_MIXED, off in HSDE_FP64), 0 off,
                              1 on.  Results then depend on the solve history, so
                              a resumed run (hsde_set_state) matches a straight
                              run to rounding, not bitwise.                      */

@@ -313,7 +313,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     h->device = opt.device;
     h->max_sweeps = opt.jacobi_max_sweeps > 0 ? opt.jacobi_max_sweeps : (h->mixed ? 12 : 16);
     h->jtol = opt.jacobi_tol > 0 ? opt.jacobi_tol : (h->mixed ? 1e-6 : 1e-14);
-    h->warm = opt.warm_start == 0 ? 0 : 1;
+    h->warm = opt.warm_start == -1 ? (h->mixed ? 1 : 0) : opt.warm_start;
     h->refresh = opt.warm_refresh > 0 ? opt.warm_refresh : 32;
 
     // ---- host analysis and preparation ----
