@@ -235,6 +235,18 @@ HSDE_API int  hsde_get_certificate(hsde_handle* h, int32_t i, int32_t kind, doub
  * graph branch), "check" (stopping rule) and "iteration" (all of it). */
 HSDE_API int  hsde_get_profile(hsde_handle* h, hsde_profile* out);
 
+/* In-place inverse of a dense m x m symmetric positive definite matrix held
+ * in DEVICE memory (row-major, m*m doubles): the cached factor of Sections
+ * 4.2-4.3, kept as the explicit inverse of S = I + A Delta^{-1} A^T.
+ * Gauss-Jordan elimination without pivoting (every pivot of an SPD matrix is
+ * positive).  2m doubles of device scratch are allocated with
+ * cudaMallocAsync on the stream and released with cudaFreeAsync once the
+ * work is enqueued.  Asynchronous on cuda_stream (NULL: legacy default
+ * stream); the caller keeps ownership of S.  A matrix that is not SPD gives
+ * a meaningless result (no error is detected).
+ * Errors: HSDE_EINVAL (null S, m <= 0), HSDE_ENOMEM, HSDE_ECUDA. */
+HSDE_API int  hsde_spd_inverse(double* S, int32_t m, void* cuda_stream);
+
 /* Free all device and host memory of the handle.  NULL-safe. */
 HSDE_API void hsde_destroy(hsde_handle* h);
 

@@ -29,6 +29,12 @@ int fail(int code, const std::string& msg) {
     return code;
 }
 
+}  // namespace
+
+int hsde::set_error(int code, const std::string& msg) { return fail(code, msg); }
+
+namespace {
+
 #define CK(call)                                                                        \
     do {                                                                                \
         cudaError_t e_ = (call);                                                        \

@@ -31,6 +31,9 @@ struct Symbolic {
     int32_t pos(int32_t r, int32_t c) const;   // -1 if (r,c) not in E'
 };
 
+// Records the message returned by hsde_last_error() on this thread; returns code.
+int set_error(int code, const std::string& msg);
+
 // Validates the problem and runs the analysis; returns HSDE_OK or HSDE_EINVAL.
 int build_symbolic(const hsde_problem* P, Symbolic& S, std::string& err);
 

@@ -85,6 +85,7 @@ _SIGS = {
     "hsde_get_certificate": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _f64p, _f64p, _f64p]),
     "hsde_get_profile": (C.c_int, [C.c_void_p, C.POINTER(hsde_profile)]),
     "hsde_destroy": (None, [C.c_void_p]),
+    "hsde_spd_inverse": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
 }
 
 
@@ -269,6 +270,11 @@ class Handle:
             st = self.hsde_iterate(chunk)
             if np.all(st != RUNNING):
                 return st
+
+
+def hsde_spd_inverse(S_dev_ptr: int, m: int, stream: int = 0):
+    """In-place inverse of an SPD m x m row-major FP64 matrix at a device address."""
+    _ck(lib.hsde_spd_inverse(C.c_void_p(S_dev_ptr), int(m), C.c_void_p(stream)), "hsde_spd_inverse")
 
 
 def split_state(state: np.ndarray, sz: hsde_sizes):
