@@ -247,6 +247,24 @@ HSDE_API int  hsde_get_profile(hsde_handle* h, hsde_profile* out);
  * Errors: HSDE_EINVAL (null S, m <= 0), HSDE_ENOMEM, HSDE_ECUDA. */
 HSDE_API int  hsde_spd_inverse(double* S, int32_t m, void* cuda_stream);
 
+/* Same inverse as hsde_spd_inverse, for callers that must not allocate
+ * device memory during the call (for example code running under CUDA graph
+ * capture in a framework that forbids allocation there, real-time hosts with
+ * a fixed memory budget, or processes whose device memory is managed by a
+ * pooling allocator).  The paper has no counterpart: this is a deployment
+ * variant.  It allocates nothing: the 2m-double pivot scratch lives in a
+ * fixed array in device memory (limit m <= 8192, i.e. 128 KiB that every GPU
+ * loading the library keeps until the process exits).  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) and
+ * caches it; make that first call before any stream capture.  All calls on a
+ * device share the one scratch array, which keeps the last call's contents
+ * (nothing in it needs to start at zero): calls whose work overlaps on the
+ * GPU (different streams, or concurrent host threads) race and give wrong
+ * results; serialise them on one stream.  Asynchronous on cuda_stream.
+ * Errors: HSDE_EINVAL (null S, m <= 0), HSDE_ERANGE (m > 8192),
+ * HSDE_ECUDA (no current device, symbol lookup or launch failure). */
+HSDE_API int  hsde_spd_inverse_noalloc(double* S, int32_t m, void* cuda_stream);
+
 /* Free all device and host memory of the handle.  NULL-safe. */
 HSDE_API void hsde_destroy(hsde_handle* h);
 

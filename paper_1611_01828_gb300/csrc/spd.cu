@@ -64,3 +64,59 @@ extern "C" int hsde_spd_inverse(double* S, int32_t m, void* cuda_stream) {
     if (rc != HSDE_OK) return set_error(rc, "hsde_spd_inverse: kernel launch failed");
     return e == cudaSuccess ? HSDE_OK : set_error(HSDE_ECUDA, "hsde_spd_inverse: cudaFreeAsync failed");
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant.  Some callers cannot allocate device memory when
+// they invert: code that runs while a CUDA graph is being captured under a
+// framework that forbids allocation there, real-time or embedded hosts that
+// fix their memory budget up front, and processes whose memory is owned by a
+// pooling allocator that any stray cudaMalloc/cudaMallocAsync would bypass.
+// This entry point runs the same Gauss-Jordan kernels with their pivot row
+// and column taken from a fixed array in device memory instead.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr int32_t kNoAllocMaxM = 8192;   // largest m: 2 * 8192 doubles = 128 KiB per GPU
+constexpr int kMaxDevices = 64;
+
+// Pivot row and column scratch of hsde_spd_inverse_noalloc.  Every GPU that
+// loads the library holds this array until the process exits.
+static __device__ __align__(256) double g_gj_scratch[2 * kNoAllocMaxM];
+
+std::mutex g_scratch_mu;
+double* g_scratch_addr[kMaxDevices] = {};   // device address of g_gj_scratch, per device
+
+}  // namespace
+
+extern "C" int hsde_spd_inverse_noalloc(double* S, int32_t m, void* cuda_stream) {
+    using namespace hsde;
+    if (!S || m <= 0) return set_error(HSDE_EINVAL, "hsde_spd_inverse_noalloc: null matrix or m <= 0");
+    if (m > kNoAllocMaxM)
+        return set_error(HSDE_ERANGE, "hsde_spd_inverse_noalloc: m = " + std::to_string(m) +
+                                          " exceeds the static scratch limit of " + std::to_string(kNoAllocMaxM));
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return set_error(HSDE_ECUDA, "hsde_spd_inverse_noalloc: no usable current device");
+    double* scratch = nullptr;
+    {
+        // One-time set-up per device, with that device current: the host-side
+        // name g_gj_scratch is not a device address; ask the runtime for it.
+        std::lock_guard<std::mutex> lk(g_scratch_mu);
+        if (!g_scratch_addr[dev]) {
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_gj_scratch);
+            if (e != cudaSuccess || !p)
+                return set_error(HSDE_ECUDA, std::string("hsde_spd_inverse_noalloc: cudaGetSymbolAddress: ") +
+                                                 cudaGetErrorString(e));
+            g_scratch_addr[dev] = static_cast<double*>(p);
+        }
+        scratch = g_scratch_addr[dev];
+    }
+    // The scratch needs no clearing: each step writes the pivot row and
+    // column before the update kernel reads them.
+    const int rc = gj_inverse_single(S, m, scratch, reinterpret_cast<cudaStream_t>(cuda_stream));
+    if (rc != HSDE_OK) return set_error(rc, "hsde_spd_inverse_noalloc: kernel launch failed");
+    return HSDE_OK;
+}

@@ -86,6 +86,7 @@ _SIGS = {
     "hsde_get_profile": (C.c_int, [C.c_void_p, C.POINTER(hsde_profile)]),
     "hsde_destroy": (None, [C.c_void_p]),
     "hsde_spd_inverse": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "hsde_spd_inverse_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
 }
 
 
