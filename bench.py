@@ -160,6 +160,13 @@ def affine_bytes(sizes, mixed, nnzA):
     return rhs + spA + solve + spAt + eta
 
 
+def post_bytes(sizes, mixed, nnzA):
+    """Compulsory HBM bytes of the post phase (x update, stopping rule, next f)."""
+    N, P, m = sizes.N, sizes.P, sizes.m
+    T = 4 if mixed else 8
+    return 8 * 6 * N + 4 * (N + 1) + N + 4 * P + 3 * T * P + 4 * (N + 1) + 12 * nnzA + 8 * nnzA + 32 * m
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -338,7 +345,7 @@ def run_ours(args):
                 "phase_ms": dom_ms, "algorithmic_flops_per_launch": cone_flops(dom_units)}
     else:
         peak = (peaks or {}).get("hbm_gbs", 6800.0)
-        byts = affine_bytes(sizes, True, nnzA)
+        byts = affine_bytes(sizes, True, nnzA) if dom == "affine" else post_bytes(sizes, True, nnzA)
         achieved = byts / (dom_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)",

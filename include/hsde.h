@@ -141,6 +141,9 @@ typedef struct hsde_profile {
     int64_t phase_units[HSDE_MAX_PHASES];  /* work units of the phase: pattern
                                               entries (affine, check) or
                                               sum_k c_k^3 (cone buckets)        */
+    double  sweeps_mean;  /* Jacobi sweeps per clique in the last iteration      */
+    int32_t sweeps_max;
+    int32_t _pad;
 } hsde_profile;
 
 typedef struct hsde_handle hsde_handle;
@@ -230,9 +233,10 @@ HSDE_API int  hsde_get_certificate(hsde_handle* h, int32_t i, int32_t kind, doub
 
 /* Launch count of one iteration and, if the handle was set up with
  * profile = 1, the device time of each phase of the last iteration (waits
- * for the handle's stream).  Phases: "affine" (scatter, SpMVs, solve, eta),
+ * for the handle's stream).  Phases: "affine" (A f, S^{-1}, A^T y_w, eta),
  * one "cone_cK" per clique bucket (cliques of size <= K, each on its own
- * graph branch), "check" (stopping rule) and "iteration" (all of it). */
+ * graph branch), "post" (x update, stopping rule, verdict and the next
+ * right-hand side) and "iteration" (all of it). */
 HSDE_API int  hsde_get_profile(hsde_handle* h, hsde_profile* out);
 
 /* In-place inverse of a dense m x m symmetric positive definite matrix held

@@ -205,6 +205,8 @@ struct hsde_handle {
     std::vector<int64_t> bucket_c3;
     int kernels_per_iter = 0;
     int64_t launched = 0;      // iterations enqueued since setup
+    bool any_dense = false;
+    bool need_rhs = true;      // f must be formed before the next iteration (after setup / set_state)
 };
 
 namespace {
@@ -217,15 +219,14 @@ cudaError_t rec(hsde_handle* h, cudaEvent_t ev, cudaStream_t s) {
 int enqueue_iteration(hsde_handle* h) {
     const DevView& V = h->V;
     CK(rec(h, h->ev_it0, h->st));
-    launch_rhs(V, h->mixed, Mode::Iter, h->st);
-    launch_spmv_A(V, Mode::Iter, h->st);
-    launch_solve(V, Mode::Iter, h->st);
-    launch_spmv_At(V, Mode::Iter, h->st);
-    launch_eta(V, h->st);
+    launch_fwd(V, h->st);
+    if (h->any_dense) launch_solve_dense(V, h->st);
+    launch_bwd_eta(V, h->st);
     CK(rec(h, h->ev_aff, h->st));
-    // fork: every clique bucket on its own branch, x update on the main branch
+    // fork: every clique bucket on its own branch, A x for the check on another
     CK(cudaEventRecord(h->ev_fork, h->st));
-    for (size_t i = 0; i < h->buckets.size(); ++i) {
+    const size_t nb = h->buckets.size();
+    for (size_t i = 0; i < nb; ++i) {
         CK(cudaStreamWaitEvent(h->side[i], h->ev_fork, 0));
         CK(rec(h, h->ev_cs[i], h->side[i]));
         int rc = launch_cone(V, h->buckets[i], h->mixed, h->max_sweeps, h->jtol, h->warm, h->refresh,
@@ -234,11 +235,12 @@ int enqueue_iteration(hsde_handle* h) {
         CK(rec(h, h->ev_ce[i], h->side[i]));
         CK(cudaEventRecord(h->ev_join[i], h->side[i]));
     }
-    launch_xupd(V, h->st);
-    for (size_t i = 0; i < h->buckets.size(); ++i) CK(cudaStreamWaitEvent(h->st, h->ev_join[i], 0));
+    CK(cudaStreamWaitEvent(h->side[nb], h->ev_fork, 0));
+    launch_check_m(V, h->side[nb]);
+    CK(cudaEventRecord(h->ev_join[nb], h->side[nb]));
+    for (size_t i = 0; i <= nb; ++i) CK(cudaStreamWaitEvent(h->st, h->ev_join[i], 0));
     CK(rec(h, h->ev_chk, h->st));
-    launch_check(V, h->mixed, h->st);
-    launch_verdict(V, h->st);
+    launch_post(V, h->mixed, h->st);
     CK(rec(h, h->ev_it1, h->st));
     CK(cudaGetLastError());
     return HSDE_OK;
@@ -247,9 +249,9 @@ int enqueue_iteration(hsde_handle* h) {
 int count_kernels(const hsde_handle* h) {
     const DevView& V = h->V;
     int k = 0;
-    if (V.ntiles > 0) k += 4;          // rhs, spmv_At, xupd, check_N
-    if (V.Mtot > 0) k += 3;            // spmv_A, solve, check_m
-    k += 2;                            // eta, verdict
+    if (V.ntiles > 0) k += 2;          // bwd_eta, post
+    if (V.Mtot > 0) k += 2;            // fwd, check_m
+    if (h->any_dense) k += 1;          // solve_dense
     for (const auto& b : h->buckets) k += b.count > 0 ? 1 : 0;
     return k;
 }
@@ -411,12 +413,15 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     const size_t o_g = cv.take<int32_t>(Ptot), o_clo = cv.take<int32_t>(ncl), o_cls = cv.take<int32_t>(ncl),
                  o_cli = cv.take<int32_t>(ncl), o_inst = cv.take<InstDev>(B), o_tiles = cv.take<int4>(ntiles),
                  o_part = cv.take<double>(ntiles * KPART), o_clp = cv.take<double>(ncl),
-                 o_rowp = cv.take<double>(Mtot * 3), o_blist = cv.take<int32_t>(ncl);
+                 o_clsw = cv.take<int32_t>(ncl),
+                 o_rowp = cv.take<double>(Mtot * 3), o_blist = cv.take<int32_t>(ncl),
+                 o_rowb = cv.take<double>(Mtot), o_cnt = cv.take<int>(2 * (size_t)B);
     // Gauss-Jordan scratch and per-dense-instance tables
     int ndense = 0;
     int32_t mmax = 0;
     for (int32_t b = 0; b < B; ++b)
         if (h->prep[b].dense) { ++ndense; mmax = std::max(mmax, h->prep[b].m); }
+    h->any_dense = ndense > 0;
     const size_t o_gjrow = cv.take<double>(Mtot), o_gjcol = cv.take<double>(Mtot),
                  o_gjoff = cv.take<int64_t>(ndense), o_gjm = cv.take<int32_t>(ndense),
                  o_gjb = cv.take<int64_t>(ndense);
@@ -443,6 +448,9 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     V.cl_size = (const int32_t*)(ar + o_cls); V.cl_inst = (const int32_t*)(ar + o_cli);
     V.inst = (InstDev*)(ar + o_inst); V.tiles = (const int4*)(ar + o_tiles);
     V.part = (double*)(ar + o_part); V.cl_part = (double*)(ar + o_clp); V.row_part = (double*)(ar + o_rowp);
+    V.cl_sweeps = (int32_t*)(ar + o_clsw);
+    V.rowb = (double*)(ar + o_rowb);
+    V.counters = (int*)(ar + o_cnt);
     V.eps = opt.eps_tol; V.max_iter = opt.max_iter; V.check_every = opt.check_every;
 
     // ---- concatenated host buffers with absolute indices ----
@@ -690,6 +698,12 @@ int hsde_iterate(hsde_handle* h, int32_t k, int32_t* status_out) {
     if (k < 0) return fail(HSDE_EINVAL, "k < 0");
     const double t0 = now_ms();
     CK(cudaSetDevice(h->device));
+    if (k > 0 && h->need_rhs) {
+        // f of the first iteration (later iterations get it from the previous one)
+        launch_rhs(h->V, h->mixed, Mode::Iter, h->st);
+        CK(cudaGetLastError());
+        h->need_rhs = false;
+    }
     for (int32_t it = 0; it < k; ++it) {
         h->launched++;
         if (h->exec) {
@@ -834,6 +848,7 @@ int hsde_set_state(hsde_handle* h, int32_t i, const double* state, int32_t itera
     InstDev I = h->host_inst[i];
     I.tau = tau; I.kappa = kappa; I.status = HSDE_RUNNING; I.iter = iterations; I.eta = 0.0;
     I.vcold = 1;
+    h->need_rhs = true;
     CK(cudaMemcpy(h->V.inst + i, &I, sizeof(InstDev), cudaMemcpyHostToDevice));
     h->host_inst[i] = I;
     return HSDE_OK;
@@ -926,9 +941,18 @@ int hsde_get_profile(hsde_handle* h, hsde_profile* out) {
         std::snprintf(nm, sizeof(nm), "cone_c%d", h->buckets[i].cmax);
         if ((rc = put(nm, h->ev_cs[i], h->ev_ce[i], h->bucket_c3[i])) != HSDE_OK) return rc;
     }
-    if ((rc = put("check", h->ev_chk, h->ev_it1, h->V.Ntot)) != HSDE_OK) return rc;
+    if ((rc = put("post", h->ev_chk, h->ev_it1, h->V.Ntot)) != HSDE_OK) return rc;
     if ((rc = put("iteration", h->ev_it0, h->ev_it1, h->V.Ntot)) != HSDE_OK) return rc;
     out->nphases = np;
+    // Jacobi sweeps of the last solve of every clique
+    std::vector<int32_t> sw(h->V.ncl);
+    if (h->V.ncl > 0)
+        CK(cudaMemcpy(sw.data(), h->V.cl_sweeps, sizeof(int32_t) * sw.size(), cudaMemcpyDeviceToHost));
+    int64_t tot = 0;
+    int32_t mx = 0;
+    for (int32_t v : sw) { tot += v; mx = std::max(mx, v); }
+    out->sweeps_mean = sw.empty() ? 0.0 : (double)tot / (double)sw.size();
+    out->sweeps_max = mx;
     return HSDE_OK;
 }
 

@@ -111,79 +111,131 @@ __device__ __forceinline__ int sigma(int j) {
     return k == K - 1 ? j + 1 : j + 2;
 }
 
-template <typename T>
-__device__ __forceinline__ T t_sqrt(T x);
-template <>
-__device__ __forceinline__ float t_sqrt<float>(float x) { return sqrtf(x); }
-template <>
-__device__ __forceinline__ double t_sqrt<double>(double x) { return sqrt(x); }
+// Jacobi rotation (c, s, t = s/c) that zeroes a_pq of the 2x2 block
+// [[a_pp, a_pq], [a_pq, a_qq]] (Golub & Van Loan, symmetric Schur 2x2):
+// theta = (a_qq - a_pp) / (2 a_pq), t = sign(theta) / (|theta| + sqrt(1 + theta^2)).
+// FP32 uses the fast reciprocal / reciprocal-square-root instructions: the
+// rotation is applied exactly as the computed (c, s) pair, so their ~2 ulp
+// error only perturbs the angle, not the orthogonality of the update.
+__device__ __forceinline__ void rotation(float app, float aqq, float apq, float& cs, float& sn, float& t) {
+    cs = 1.f; sn = 0.f; t = 0.f;
+    if (apq != 0.f) {
+        const float theta = __fdividef(aqq - app, 2.f * apq);
+        const float r = __fsqrt_rn(fmaf(theta, theta, 1.f));
+        t = __frcp_rn(fabsf(theta) + r);
+        if (theta < 0.f) t = -t;
+        cs = rsqrtf(fmaf(t, t, 1.f));
+        sn = t * cs;
+    }
+}
+__device__ __forceinline__ void rotation(double app, double aqq, double apq, double& cs, double& sn, double& t) {
+    cs = 1.0; sn = 0.0; t = 0.0;
+    if (apq != 0.0) {
+        const double theta = (aqq - app) / (2.0 * apq);
+        t = 1.0 / (fabs(theta) + sqrt(1.0 + theta * theta));
+        if (theta < 0.0) t = -t;
+        cs = 1.0 / sqrt(1.0 + t * t);
+        sn = t * cs;
+    }
+}
+
+// Offsets (in elements of one CP x LD buffer) a thread uses in every round.
+// The thread-to-block assignment does not change between rounds, so the
+// tournament map is evaluated once per solve, not once per round.
+template <typename Cfg>
+struct RoundPlan {
+    int a_src[Cfg::BPL];       // top-left of the 2x2 block (rows 2kr, 2kr+1; cols 2kc, 2kc+1)
+    int a_dst[Cfg::BPL][4];    // (r0,c0) (r0,c1) (r1,c0) (r1,c1) in the next round's slots
+    int rot_r[Cfg::BPL], rot_c[Cfg::BPL];
+    int v_src[Cfg::VPL], v_dst0[Cfg::VPL], v_dst1[Cfg::VPL], v_rot[Cfg::VPL];
+    unsigned diag_mask, a_valid, v_valid;
+
+    __device__ __forceinline__ void build(int lane) {
+        constexpr int CP = Cfg::CP, K = Cfg::K, LD = Cfg::LD, G = Cfg::G;
+        diag_mask = 0u; a_valid = 0u; v_valid = 0u;
+#pragma unroll
+        for (int i = 0; i < Cfg::BPL; ++i) {
+            int b = lane + i * G;
+            if (b < Cfg::NBLK) a_valid |= 1u << i;
+            else b = 0;
+            const int kr = b / K, kc = b - (b / K) * K;
+            const int r0 = sigma<CP>(2 * kr), r1 = sigma<CP>(2 * kr + 1);
+            const int c0 = sigma<CP>(2 * kc), c1 = sigma<CP>(2 * kc + 1);
+            a_src[i] = (2 * kr) * LD + 2 * kc;
+            a_dst[i][0] = r0 * LD + c0;
+            a_dst[i][1] = r0 * LD + c1;
+            a_dst[i][2] = r1 * LD + c0;
+            a_dst[i][3] = r1 * LD + c1;
+            rot_r[i] = 2 * kr;
+            rot_c[i] = 2 * kc;
+            if (kr == kc) diag_mask |= 1u << i;
+        }
+#pragma unroll
+        for (int i = 0; i < Cfg::VPL; ++i) {
+            int b = lane + i * G;
+            if (b < Cfg::NVP) v_valid |= 1u << i;
+            else b = 0;
+            const int row = b / K, kc = b - (b / K) * K;
+            v_src[i] = row * LD + 2 * kc;
+            v_dst0[i] = row * LD + sigma<CP>(2 * kc);
+            v_dst1[i] = row * LD + sigma<CP>(2 * kc + 1);
+            v_rot[i] = 2 * kc;
+        }
+    }
+};
 
 template <typename Cfg, typename T>
-__device__ __forceinline__ void jacobi_round(const T* __restrict__ A, T* __restrict__ An,
-                                             const T* __restrict__ Vc, T* __restrict__ Vn,
+__device__ __forceinline__ void jacobi_round(const RoundPlan<Cfg>& pl, const T* __restrict__ A,
+                                             T* __restrict__ An, const T* __restrict__ Vc, T* __restrict__ Vn,
                                              T* __restrict__ rot, T* __restrict__ tan_, int lane, int gid) {
-    constexpr int CP = Cfg::CP, K = Cfg::K, LD = Cfg::LD, G = Cfg::G;
+    constexpr int K = Cfg::K, LD = Cfg::LD, G = Cfg::G;
     using V2 = typename Vec2<T>::type;
     // rotation of every slot pair (2k, 2k+1)
     if (lane < K) {
         const int k = lane;
-        const T app = A[(2 * k) * LD + 2 * k], aqq = A[(2 * k + 1) * LD + 2 * k + 1];
-        const T apq = A[(2 * k) * LD + 2 * k + 1];
-        T cs = 1, sn = 0, t = 0;
-        if (apq != T(0)) {
-            const T theta = (aqq - app) / (T(2) * apq);
-            t = T(1) / (fabs(theta) + t_sqrt<T>(T(1) + theta * theta));
-            if (theta < T(0)) t = -t;
-            cs = T(1) / t_sqrt<T>(T(1) + t * t);
-            sn = t * cs;
-        }
-        rot[2 * k] = cs;
-        rot[2 * k + 1] = sn;
+        const V2 top = *reinterpret_cast<const V2*>(A + (2 * k) * LD + 2 * k);
+        const T aqq = A[(2 * k + 1) * LD + 2 * k + 1];
+        T cs, sn, t;
+        rotation(top.x, aqq, top.y, cs, sn, t);
+        V2 cssn;
+        cssn.x = cs;
+        cssn.y = sn;
+        *reinterpret_cast<V2*>(rot + 2 * k) = cssn;
         tan_[k] = t;
     }
     gsync<G>(gid);
 #pragma unroll
     for (int i = 0; i < Cfg::BPL; ++i) {
-        const int b = lane + i * G;
-        if (Cfg::NBLK % G == 0 || b < Cfg::NBLK) {
-            const int kr = b / K, kc = b - (b / K) * K;
-            const int r0 = sigma<CP>(2 * kr), r1 = sigma<CP>(2 * kr + 1);
-            if (kr == kc) {
-                const T t = tan_[kr];
-                const T app = A[(2 * kr) * LD + 2 * kr], aqq = A[(2 * kr + 1) * LD + 2 * kr + 1];
-                const T apq = A[(2 * kr) * LD + 2 * kr + 1];
-                An[r0 * LD + r0] = app - t * apq;
-                An[r1 * LD + r1] = aqq + t * apq;
-                const T off = (t == T(0)) ? apq : T(0);
-                An[r0 * LD + r1] = off;
-                An[r1 * LD + r0] = off;
-            } else {
-                const int c0 = sigma<CP>(2 * kc), c1 = sigma<CP>(2 * kc + 1);
-                const V2 top = *reinterpret_cast<const V2*>(A + (2 * kr) * LD + 2 * kc);
-                const V2 bot = *reinterpret_cast<const V2*>(A + (2 * kr + 1) * LD + 2 * kc);
-                const V2 rr = *reinterpret_cast<const V2*>(rot + 2 * kr);
-                const V2 rc = *reinterpret_cast<const V2*>(rot + 2 * kc);
-                // J_r^T X
-                const T y00 = rr.x * top.x - rr.y * bot.x, y01 = rr.x * top.y - rr.y * bot.y;
-                const T y10 = rr.y * top.x + rr.x * bot.x, y11 = rr.y * top.y + rr.x * bot.y;
-                // (.) J_c
-                An[r0 * LD + c0] = rc.x * y00 - rc.y * y01;
-                An[r0 * LD + c1] = rc.y * y00 + rc.x * y01;
-                An[r1 * LD + c0] = rc.x * y10 - rc.y * y11;
-                An[r1 * LD + c1] = rc.y * y10 + rc.x * y11;
-            }
+        if ((Cfg::NBLK % G != 0) && !(pl.a_valid & (1u << i))) continue;
+        const V2 top = *reinterpret_cast<const V2*>(A + pl.a_src[i]);
+        const V2 bot = *reinterpret_cast<const V2*>(A + pl.a_src[i] + LD);
+        if (pl.diag_mask & (1u << i)) {
+            const T t = tan_[pl.rot_r[i] >> 1];
+            const T off = (t == T(0)) ? top.y : T(0);
+            An[pl.a_dst[i][0]] = top.x - t * top.y;
+            An[pl.a_dst[i][1]] = off;
+            An[pl.a_dst[i][2]] = off;
+            An[pl.a_dst[i][3]] = bot.y + t * top.y;
+        } else {
+            const V2 rr = *reinterpret_cast<const V2*>(rot + pl.rot_r[i]);
+            const V2 rc = *reinterpret_cast<const V2*>(rot + pl.rot_c[i]);
+            // J_r^T X
+            const T y00 = rr.x * top.x - rr.y * bot.x, y01 = rr.x * top.y - rr.y * bot.y;
+            const T y10 = rr.y * top.x + rr.x * bot.x, y11 = rr.y * top.y + rr.x * bot.y;
+            // (.) J_c
+            An[pl.a_dst[i][0]] = rc.x * y00 - rc.y * y01;
+            An[pl.a_dst[i][1]] = rc.y * y00 + rc.x * y01;
+            An[pl.a_dst[i][2]] = rc.x * y10 - rc.y * y11;
+            An[pl.a_dst[i][3]] = rc.y * y10 + rc.x * y11;
         }
     }
 #pragma unroll
     for (int i = 0; i < Cfg::VPL; ++i) {
-        const int b = lane + i * G;
-        if (Cfg::NVP % G == 0 || b < Cfg::NVP) {
-            const int row = b / K, kc = b - (b / K) * K;
-            const V2 vv = *reinterpret_cast<const V2*>(Vc + row * LD + 2 * kc);
-            const V2 rc = *reinterpret_cast<const V2*>(rot + 2 * kc);
-            Vn[row * LD + sigma<CP>(2 * kc)] = rc.x * vv.x - rc.y * vv.y;
-            Vn[row * LD + sigma<CP>(2 * kc + 1)] = rc.y * vv.x + rc.x * vv.y;
-        }
+        if ((Cfg::NVP % G != 0) && !(pl.v_valid & (1u << i))) continue;
+        const V2 vv = *reinterpret_cast<const V2*>(Vc + pl.v_src[i]);
+        const V2 rc = *reinterpret_cast<const V2*>(rot + pl.v_rot[i]);
+        Vn[pl.v_dst0[i]] = rc.x * vv.x - rc.y * vv.y;
+        Vn[pl.v_dst1[i]] = rc.y * vv.x + rc.x * vv.y;
     }
     gsync<G>(gid);
 }
@@ -264,7 +316,11 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
         gsync<G>(gid);
     }
 
+    RoundPlan<Cfg> plan;
+    plan.build(lane);
+    int sweeps_done = 0;
     for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
+        sweeps_done = sweep;
         T offd = 0, tot = 0;
         for (int idx = lane; idx < CP * CP; idx += G) {
             const int i = idx / CP, j = idx - (idx / CP) * CP;
@@ -276,7 +332,7 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
         tot = gsum<G>(tot, red, gid);
         if (offd <= tol2 * tot || sweep == max_sweeps) break;
         for (int r = 0; r < CP - 1; ++r) {
-            jacobi_round<Cfg>(A, An, Vc, Vn, rot, tan_, lane, gid);
+            jacobi_round<Cfg>(plan, A, An, Vc, Vn, rot, tan_, lane, gid);
             T* t1 = A; A = An; An = t1;
             T* t2 = Vc; Vc = Vn; Vn = t2;
         }
@@ -311,7 +367,10 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
         res += (arow == bcol ? 1.0 : 2.0) * d * d;
     }
     res = gsum<G>(res, reinterpret_cast<double*>(red), gid);
-    if (lane == 0) V.cl_part[k] = res;
+    if (lane == 0) {
+        V.cl_part[k] = res;
+        V.cl_sweeps[k] = sweeps_done;
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -64,8 +64,8 @@ struct InstDev {
 
 // Number of partial sums stored per N-space tile.
 constexpr int KPART = 4;
-// Entries per N-space tile (one CTA each).
-constexpr int TILE_N = 1024;
+// Entries per N-space tile (one CTA of 256 threads each).
+constexpr int TILE_N = 256;
 
 // Device view of the whole batch (plain pointers into one arena).
 struct DevView {
@@ -95,7 +95,10 @@ struct DevView {
     const int4* tiles;       // (inst, begin, end, 0)
     double* part;            // [ntiles * KPART]
     double* cl_part;         // [ncl]
+    int32_t* cl_sweeps;      // [ncl] Jacobi sweeps used by each clique in its last solve
     double* row_part;        // [Mtot * 3]
+    double* rowb;            // [Mtot] b_i (y_w)_i
+    int* counters;           // [2B] completion counters of k_bwd_eta and k_post
     // options
     double eps;
     int32_t max_iter, check_every;
@@ -117,10 +120,11 @@ void launch_rhs(const DevView& V, bool mixed, Mode mode, void* st);
 void launch_spmv_A(const DevView& V, Mode mode, void* st);
 void launch_solve(const DevView& V, Mode mode, void* st);
 void launch_spmv_At(const DevView& V, Mode mode, void* st);
-void launch_eta(const DevView& V, void* st);
-void launch_xupd(const DevView& V, void* st);
-void launch_check(const DevView& V, bool mixed, void* st);
-void launch_verdict(const DevView& V, void* st);
+void launch_fwd(const DevView& V, void* st);
+void launch_solve_dense(const DevView& V, void* st);
+void launch_bwd_eta(const DevView& V, void* st);
+void launch_check_m(const DevView& V, void* st);
+void launch_post(const DevView& V, bool mixed, void* st);
 void launch_setup_den(const DevView& V, void* st);
 // cone projection of every clique in one bucket (Eq. Step2 on S, fused with
 // the H gather, the rank-one correction and the nu update of Eq. Step3)

@@ -142,26 +142,110 @@ __global__ void __launch_bounds__(NT) k_spmv_At(DevView V, int mode) {
     if (threadIdx.x == 0) V.part[(int64_t)blockIdx.x * KPART + 0] = part;
 }
 
-// eta, tau, kappa and y = y_w - eta y_p.  One CTA per instance.
-__global__ void __launch_bounds__(NT) k_eta(DevView V) {
-    __shared__ double sh[32];
-    InstDev& I = V.inst[blockIdx.x];
+
+// ===========================================================================
+// Fused iteration kernels.  Per iteration (after the cone projections of the
+// previous one have produced s, z, v and k_post has produced f):
+//   k_fwd      q = y + omega_tau b - A f; diagonal S: y_w = S^{-1} q
+//   k_solve    dense S: y_w = S^{-1} q                     (only if any S is dense)
+//   k_bwd_eta  x_w = f + Delta^{-1} A^T y_w; the last CTA of each instance
+//              computes eta, tau, kappa and y = y_w - eta y_p
+//   k_cone ... per clique bucket, in parallel with k_check_m
+//   k_post     x = x_w - eta x_p; stopping-rule sums; the last CTA of each
+//              instance takes the verdict; f of the next iteration
+// "Last CTA" is the usual completion-counter pattern: every CTA publishes its
+// partial sums, fences, and increments a per-instance counter; the CTA that
+// sees the final count reduces the partials in tile order.  Nothing waits.
+// ===========================================================================
+
+__device__ __forceinline__ bool last_cta(int* counter, int total, int* flag_sh) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int prev = atomicAdd(counter, 1);
+        *flag_sh = (prev == total - 1);
+    }
+    __syncthreads();
+    const bool last = *flag_sh != 0;
+    if (last) __threadfence();
+    return last;
+}
+
+// q and, for diagonal S, y_w and b_i y_w,i.  One warp per row.
+__global__ void __launch_bounds__(NT) k_fwd(DevView V) {
+    const int row = (blockIdx.x * NT + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (row >= V.Mtot) return;
+    const InstDev& I = V.inst[V.row_inst[row]];
     if (I.status != HSDE_RUNNING) return;
+    double acc = 0.0;
+    const int j1 = V.A_ptr[row + 1];
+    for (int j = V.A_ptr[row] + lane; j < j1; j += 32) acc += V.A_val[j] * V.f[V.A_col[j]];
+    acc = warp_sum(acc);
+    if (lane == 0) {
+        const double q = V.y[row] + (I.tau + I.kappa) * V.b[row] - acc;
+        if (I.dense) {
+            V.q[row] = q;
+        } else {
+            const double yw = V.sdiag[row] * q;
+            V.yw[row] = yw;
+            V.rowb[row] = V.b[row] * yw;
+        }
+    }
+}
+
+// dense S: y_w = S^{-1} q and b_i y_w,i.  One warp per row.
+__global__ void __launch_bounds__(NT) k_solve_dense(DevView V) {
+    const int row = (blockIdx.x * NT + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (row >= V.Mtot) return;
+    const InstDev& I = V.inst[V.row_inst[row]];
+    if (I.status != HSDE_RUNNING || !I.dense) return;
+    const int i = row - I.m_off;
+    const double* Srow = V.sinv + I.sinv_off + (int64_t)i * I.m;
+    const double* qq = V.q + I.m_off;
+    double acc = 0.0;
+    for (int j = lane; j < I.m; j += 32) acc += Srow[j] * qq[j];
+    acc = warp_sum(acc);
+    if (lane == 0) {
+        V.yw[row] = acc;
+        V.rowb[row] = V.b[row] * acc;
+    }
+}
+
+// x_w = f + Delta^{-1} A^T y_w; last CTA per instance: eta, tau, kappa, y.
+__global__ void __launch_bounds__(NT) k_bwd_eta(DevView V) {
+    __shared__ double sh[32];
+    __shared__ int flag;
+    const int4 t = V.tiles[blockIdx.x];
+    InstDev& I = V.inst[t.x];
+    if (I.status != HSDE_RUNNING) return;
+    double part = 0.0;
+    for (int e = t.y + threadIdx.x; e < t.z; e += NT) {
+        double acc = 0.0;
+        const int j1 = V.At_ptr[e + 1];
+        for (int j = V.At_ptr[e]; j < j1; ++j) acc += V.At_val[j] * V.yw[V.At_col[j]];
+        const double xv = V.f[e] + V.inv_delta[e] * acc;
+        V.xw[e] = xv;
+        part += (V.diag[e] ? 1.0 : 2.0) * V.c[e] * xv;
+    }
+    part = block_sum(part, sh);
+    if (threadIdx.x == 0) V.part[(int64_t)blockIdx.x * KPART + 0] = part;
+    if (!last_cta(V.counters + 2 * t.x, I.tile_end - I.tile_begin, &flag)) return;
+    // ---- last CTA of this instance ----
     double ctw = 0.0;
-    for (int t = I.tile_begin + threadIdx.x; t < I.tile_end; t += NT) ctw += V.part[(int64_t)t * KPART];
+    for (int tt = I.tile_begin + threadIdx.x; tt < I.tile_end; tt += NT)
+        ctw += __ldcg(V.part + (int64_t)tt * KPART);
     ctw = block_sum(ctw, sh);
     double btw = 0.0;
-    for (int i = threadIdx.x; i < I.m; i += NT) btw += V.b[I.m_off + i] * V.yw[I.m_off + i];
+    for (int i = threadIdx.x; i < I.m; i += NT) btw += __ldcg(V.rowb + I.m_off + i);
     btw = block_sum(btw, sh);
     const double sw = ctw - btw;
     const double eta = sw / I.den;
     const double tau = I.tau, kappa = I.kappa;
-    const double ot = tau + kappa;
-    const double tau_hat = ot + sw - eta * I.ctp;
+    const double tau_hat = (tau + kappa) + sw - eta * I.ctp;
     const double tau_new = fmax(0.0, tau_hat - kappa);
     const double kappa_new = kappa - tau_hat + tau_new;
     for (int i = threadIdx.x; i < I.m; i += NT)
-        V.y[I.m_off + i] = V.yw[I.m_off + i] - eta * V.yp[I.m_off + i];
+        V.y[I.m_off + i] = __ldcg(V.yw + I.m_off + i) - eta * V.yp[I.m_off + i];
     __syncthreads();
     if (threadIdx.x == 0) {
         I.eta = eta;
@@ -169,58 +253,24 @@ __global__ void __launch_bounds__(NT) k_eta(DevView V) {
         I.kappa = kappa_new;
         I.iter += 1;
         if (!isfinite(eta) || !isfinite(tau_new) || !isfinite(kappa_new)) I.status = HSDE_NUMERICAL_ERROR;
+        V.counters[2 * t.x] = 0;
     }
 }
 
-// x = x_w - eta x_p
-__global__ void __launch_bounds__(NT) k_xupd(DevView V) {
-    const int4 t = V.tiles[blockIdx.x];
-    const InstDev& I = V.inst[t.x];
-    if (I.status != HSDE_RUNNING) return;
-    const double eta = I.eta;
-    for (int e = t.y + threadIdx.x; e < t.z; e += NT) V.x[e] = V.xw[e] - eta * V.xp[e];
-}
-
-// Stopping-rule partial sums over N: r = A^T y + H^T z,
-//   part[1] = ||r - tau c||^2, part[2] = ||r||^2, part[3] = c^T x   (full-vec weights)
-template <typename T>
-__global__ void __launch_bounds__(NT) k_check_N(DevView V) {
-    __shared__ double sh[32];
-    const int4 t = V.tiles[blockIdx.x];
-    const InstDev& I = V.inst[t.x];
-    if (I.status != HSDE_RUNNING || !is_check_iter(V, I.iter)) return;
-    const double tau = I.tau;
-    double a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    for (int e = t.y + threadIdx.x; e < t.z; e += NT) {
-        double r = 0.0;
-        const int j1 = V.At_ptr[e + 1];
-        for (int j = V.At_ptr[e]; j < j1; ++j) r += V.At_val[j] * V.y[V.At_col[j]];
-        const int k1 = V.sc_ptr[e + 1];
-        for (int k = V.sc_ptr[e]; k < k1; ++k) r += ld<T>(V.z, V.sc_idx[k]);
-        const double w = V.diag[e] ? 1.0 : 2.0;
-        const double d = r - tau * V.c[e];
-        a1 += w * d * d;
-        a2 += w * r * r;
-        a3 += w * V.c[e] * V.x[e];
-    }
-    a1 = block_sum(a1, sh);
-    a2 = block_sum(a2, sh);
-    a3 = block_sum(a3, sh);
-    if (threadIdx.x == 0) {
-        double* pp = V.part + (int64_t)blockIdx.x * KPART;
-        pp[1] = a1; pp[2] = a2; pp[3] = a3;
-    }
-}
-
-// Stopping-rule partials over m: (Ax - tau b)^2, (Ax)^2, b_i y_i.  Warp per row.
+// Stopping-rule partials over m on check iterations: (A x - tau b)^2, (A x)^2,
+// b_i y_i with x = x_w - eta x_p.  One warp per row (runs beside the cones).
 __global__ void __launch_bounds__(NT) k_check_m(DevView V) {
     const int row = (blockIdx.x * NT + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (row >= V.Mtot) return;
     const InstDev& I = V.inst[V.row_inst[row]];
     if (I.status != HSDE_RUNNING || !is_check_iter(V, I.iter)) return;
+    const double eta = I.eta;
     double acc = 0.0;
     const int j1 = V.A_ptr[row + 1];
-    for (int j = V.A_ptr[row] + lane; j < j1; j += 32) acc += V.A_val[j] * V.x[V.A_col[j]];
+    for (int j = V.A_ptr[row] + lane; j < j1; j += 32) {
+        const int e = V.A_col[j];
+        acc += V.A_val[j] * (V.xw[e] - eta * V.xp[e]);
+    }
     acc = warp_sum(acc);
     if (lane == 0) {
         const double d = acc - I.tau * V.b[row];
@@ -230,32 +280,77 @@ __global__ void __launch_bounds__(NT) k_check_m(DevView V) {
     }
 }
 
-// Verdict of the stopping rule (readings P5/P6).  One CTA per instance.
-__global__ void __launch_bounds__(NT) k_verdict(DevView V) {
+// x = x_w - eta x_p; stopping-rule partials over N (r = A^T y + H^T z):
+//   ||r - tau c||^2, ||r||^2, c^T x  (full-vec weights), on check iterations;
+// f = Delta^{-1}(x - omega_tau' c + 1/2 H^T (s+z+v)) for the next iteration;
+// the last CTA of each instance takes the verdict (readings P5/P6).
+template <typename T>
+__global__ void __launch_bounds__(NT) k_post(DevView V) {
     __shared__ double sh[32];
-    InstDev& I = V.inst[blockIdx.x];
-    const int running = I.status == HSDE_RUNNING;
-    const int iter = I.iter;
-    __syncthreads();
-    if (threadIdx.x == 0 && running) I.vcold = 0;   // stored eigenbases are valid from now on
-    if (!running || !is_check_iter(V, iter)) return;
-    double a1 = 0, a2 = 0, a3 = 0;
-    for (int t = I.tile_begin + threadIdx.x; t < I.tile_end; t += NT) {
-        const double* pp = V.part + (int64_t)t * KPART;
-        a1 += pp[1]; a2 += pp[2]; a3 += pp[3];
+    __shared__ int flag;
+    const int4 t = V.tiles[blockIdx.x];
+    InstDev& I = V.inst[t.x];
+    if (I.status != HSDE_RUNNING) return;
+    const bool check = is_check_iter(V, I.iter);
+    const double eta = I.eta, tau = I.tau;
+    const double ot = I.tau + I.kappa;            // omega_tau of the next iteration
+    double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (int e = t.y + threadIdx.x; e < t.z; e += NT) {
+        const double x = V.xw[e] - eta * V.xp[e];
+        V.x[e] = x;
+        double hz = 0.0, hall = 0.0;
+        const int k1 = V.sc_ptr[e + 1];
+        for (int k = V.sc_ptr[e]; k < k1; ++k) {
+            const int p = V.sc_idx[k];
+            const double zz = ld<T>(V.z, p);
+            hz += zz;
+            hall += ld<T>(V.s, p) + zz + ld<T>(V.v, p);
+        }
+        const double ce = V.c[e];
+        V.f[e] = (x - ot * ce + 0.5 * hall) * V.inv_delta[e];
+        if (check) {
+            double r = hz;
+            const int j1 = V.At_ptr[e + 1];
+            for (int j = V.At_ptr[e]; j < j1; ++j) r += V.At_val[j] * V.y[V.At_col[j]];
+            const double w = V.diag[e] ? 1.0 : 2.0;
+            const double d = r - tau * ce;
+            a1 += w * d * d;
+            a2 += w * r * r;
+            a3 += w * ce * x;
+        }
+    }
+    if (check) {
+        a1 = block_sum(a1, sh);
+        a2 = block_sum(a2, sh);
+        a3 = block_sum(a3, sh);
+        if (threadIdx.x == 0) {
+            double* pp = V.part + (int64_t)blockIdx.x * KPART;
+            pp[1] = a1; pp[2] = a2; pp[3] = a3;
+        }
+    }
+    if (!last_cta(V.counters + 2 * t.x + 1, I.tile_end - I.tile_begin, &flag)) return;
+    // ---- last CTA of this instance ----
+    if (threadIdx.x == 0) {
+        V.counters[2 * t.x + 1] = 0;
+        I.vcold = 0;                                // stored eigenbases are valid from now on
+    }
+    if (!check) return;
+    a1 = 0; a2 = 0; a3 = 0;
+    for (int tt = I.tile_begin + threadIdx.x; tt < I.tile_end; tt += NT) {
+        const double* pp = V.part + (int64_t)tt * KPART;
+        a1 += __ldcg(pp + 1); a2 += __ldcg(pp + 2); a3 += __ldcg(pp + 3);
     }
     a1 = block_sum(a1, sh); a2 = block_sum(a2, sh); a3 = block_sum(a3, sh);
     double r0 = 0, r1 = 0, r2 = 0;
     for (int i = threadIdx.x; i < I.m; i += NT) {
         const double* rp = V.row_part + (int64_t)(I.m_off + i) * 3;
-        r0 += rp[0]; r1 += rp[1]; r2 += rp[2];
+        r0 += __ldcg(rp); r1 += __ldcg(rp + 1); r2 += __ldcg(rp + 2);
     }
     r0 = block_sum(r0, sh); r1 = block_sum(r1, sh); r2 = block_sum(r2, sh);
     double hs = 0;
-    for (int k = I.cl_begin + threadIdx.x; k < I.cl_end; k += NT) hs += V.cl_part[k];
+    for (int k = I.cl_begin + threadIdx.x; k < I.cl_end; k += NT) hs += __ldcg(V.cl_part + k);
     hs = block_sum(hs, sh);
     if (threadIdx.x != 0) return;
-    const double tau = I.tau;
     const double ctx = a3, bty = r2;
     double pres = INFINITY, dres = INFINITY, gap = INFINITY, pobj = NAN, dobj = NAN;
     if (tau > 0) {
@@ -270,8 +365,7 @@ __global__ void __launch_bounds__(NT) k_verdict(DevView V) {
     I.pres = pres; I.dres = dres; I.gap = gap; I.pobj = pobj; I.dobj = dobj;
     I.pinf = pinf; I.dinf = dinf; I.ctx = ctx; I.bty = bty;
     int st = HSDE_RUNNING;
-    if (!isfinite(a1) || !isfinite(a2) || !isfinite(r0) || !isfinite(hs) || !isfinite(ctx) ||
-        !isfinite(bty)) {
+    if (!isfinite(a1) || !isfinite(a2) || !isfinite(r0) || !isfinite(hs) || !isfinite(ctx) || !isfinite(bty)) {
         st = HSDE_NUMERICAL_ERROR;
     } else if (tau > 0 && pres <= V.eps && dres <= V.eps && gap <= V.eps) {
         st = HSDE_SOLVED;
@@ -370,20 +464,25 @@ void launch_spmv_At(const DevView& V, Mode mode, void* st) {
     if (V.ntiles == 0) return;
     k_spmv_At<<<V.ntiles, NT, 0, S_(st)>>>(V, (int)mode);
 }
-void launch_eta(const DevView& V, void* st) { k_eta<<<V.B, NT, 0, S_(st)>>>(V); }
-void launch_xupd(const DevView& V, void* st) {
-    if (V.ntiles == 0) return;
-    k_xupd<<<V.ntiles, NT, 0, S_(st)>>>(V);
+void launch_setup_den(const DevView& V, void* st) { k_setup_den<<<V.B, NT, 0, S_(st)>>>(V); }
+
+void launch_fwd(const DevView& V, void* st) {
+    if (V.Mtot > 0) k_fwd<<<rows_grid(V.Mtot), NT, 0, S_(st)>>>(V);
 }
-void launch_check(const DevView& V, bool mixed, void* st) {
-    if (V.ntiles > 0) {
-        if (mixed) k_check_N<float><<<V.ntiles, NT, 0, S_(st)>>>(V);
-        else k_check_N<double><<<V.ntiles, NT, 0, S_(st)>>>(V);
-    }
+void launch_solve_dense(const DevView& V, void* st) {
+    if (V.Mtot > 0) k_solve_dense<<<rows_grid(V.Mtot), NT, 0, S_(st)>>>(V);
+}
+void launch_bwd_eta(const DevView& V, void* st) {
+    if (V.ntiles > 0) k_bwd_eta<<<V.ntiles, NT, 0, S_(st)>>>(V);
+}
+void launch_check_m(const DevView& V, void* st) {
     if (V.Mtot > 0) k_check_m<<<rows_grid(V.Mtot), NT, 0, S_(st)>>>(V);
 }
-void launch_verdict(const DevView& V, void* st) { k_verdict<<<V.B, NT, 0, S_(st)>>>(V); }
-void launch_setup_den(const DevView& V, void* st) { k_setup_den<<<V.B, NT, 0, S_(st)>>>(V); }
+void launch_post(const DevView& V, bool mixed, void* st) {
+    if (V.ntiles == 0) return;
+    if (mixed) k_post<float><<<V.ntiles, NT, 0, S_(st)>>>(V);
+    else k_post<double><<<V.ntiles, NT, 0, S_(st)>>>(V);
+}
 
 void launch_gj_step(double* pool, const int64_t* offs, const int32_t* ms, int ndense, int32_t k,
                     int32_t mmax, double* rowbuf, double* colbuf, const int64_t* boff, void* st) {
