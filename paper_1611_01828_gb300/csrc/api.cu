@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -324,17 +326,36 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     h->warm = opt.warm_start == -1 ? (h->mixed ? 1 : 0) : opt.warm_start;
     h->refresh = opt.warm_refresh > 0 ? opt.warm_refresh : 32;
 
-    // ---- host analysis and preparation ----
+    // ---- host analysis and preparation (instances in parallel) ----
     h->prep.resize(B);
-    std::string err;
-    for (int32_t b = 0; b < B; ++b) {
-        int rc = prepare(&P[b], h->prep[b], err);
-        if (rc != HSDE_OK) return fail(rc, "instance " + std::to_string(b) + ": " + err);
-        const int lim = 64;
-        if (cone_bucket_of(h->prep[b].cmax) < 0)
-            return fail(HSDE_ERANGE, "instance " + std::to_string(b) + ": clique of size " +
-                                          std::to_string(h->prep[b].cmax) + " exceeds " +
-                                          std::to_string(lim));
+    {
+        std::vector<int> rcs(B, HSDE_OK);
+        std::vector<std::string> errs(B);
+        std::atomic<int32_t> next{0};
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        const int nth = (int)std::min<unsigned>(hw, (unsigned)B);
+        auto work = [&]() {
+            for (;;) {
+                const int32_t b = next.fetch_add(1);
+                if (b >= B) return;
+                try {
+                    rcs[b] = prepare(&P[b], h->prep[b], errs[b]);
+                } catch (const std::bad_alloc&) {
+                    rcs[b] = HSDE_ENOMEM;
+                    errs[b] = "host allocation failed";
+                }
+            }
+        };
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nth; ++t) pool.emplace_back(work);
+        work();
+        for (auto& t : pool) t.join();
+        for (int32_t b = 0; b < B; ++b) {
+            if (rcs[b] != HSDE_OK) return fail(rcs[b], "instance " + std::to_string(b) + ": " + errs[b]);
+            if (cone_bucket_of(h->prep[b].cmax) < 0)
+                return fail(HSDE_ERANGE, "instance " + std::to_string(b) + ": clique of size " +
+                                              std::to_string(h->prep[b].cmax) + " exceeds 64");
+        }
     }
     // ---- totals and offsets ----
     int64_t Ntot = 0, Ptot = 0, nnzA = 0, Mtot = 0, ncl = 0, ntiles = 0, sinv = 0, scn = 0;

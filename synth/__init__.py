@@ -167,30 +167,57 @@ def block_arrow(l, d, h, m, rng, *, dense_constraints=False, kappa=1e3,
     for mem in cliques:
         r, c = _clique_lower_entries(mem)
         pr.append(r); pc.append(c)
-    pat_r, pat_c, _ = _dedup_sum(np.concatenate(pr), np.concatenate(pc),
-                                 np.zeros(sum(len(x) for x in pr)), n)
-    Ar, Ac, Av = [], [], []
-    for i in range(m):
-        if dense_constraints:
-            r, c = pat_r, pat_c
-        else:
-            j = (i // 2) % l if assign == "pairs" else i % l
-            r, c = _clique_lower_entries(cliques[j])
-        Ar.append(r); Ac.append(c); Av.append(rng.standard_normal(r.shape[0]))
+    if dense_constraints:
+        pat_r, pat_c, _ = _dedup_sum(np.concatenate(pr), np.concatenate(pc),
+                                     np.zeros(sum(len(x) for x in pr)), n)
+        E = pat_r.shape[0]
+        Ar = np.tile(pat_r, m); Ac = np.tile(pat_c, m)
+    else:
+        # every clique has the same number of lower entries E; sort each
+        # clique's list by (col, row) once
+        E = pr[0].shape[0]
+        cr = np.stack(pr); cc = np.stack(pc)
+        order = np.argsort(cc.astype(np.int64) * n + cr, axis=1, kind="stable")
+        cr = np.take_along_axis(cr, order, 1); cc = np.take_along_axis(cc, order, 1)
+        j = (np.arange(m) // 2) % l if assign == "pairs" else np.arange(m) % l
+        Ar = cr[j].reshape(-1); Ac = cc[j].reshape(-1)
+    Av = rng.standard_normal(m * E)
     X0 = _psd_on_cliques(rng, n, cliques, kappa)
     Z0 = _psd_on_cliques(rng, n, cliques, kappa)
     y0 = rng.standard_normal(m)
-    A_ptr, A_row, A_col, A_val, _ = _pack_constraints(Ar, Ac, Av, np.zeros(m), n)
-    b = np.array([_sym_inner(A_row[A_ptr[i]:A_ptr[i + 1]], A_col[A_ptr[i]:A_ptr[i + 1]],
-                             A_val[A_ptr[i]:A_ptr[i + 1]], *X0, n) for i in range(m)])
+    A_ptr = np.arange(m + 1, dtype=np.int64) * E
+    A_row = Ar.astype(np.int32); A_col = Ac.astype(np.int32); A_val = Av
+    b = _apply_A(A_ptr, A_row, A_col, A_val, X0, n)
     # C = sum_i y0_i A_i + Z0
     Cr = np.concatenate([A_row, Z0[0]])
     Cc = np.concatenate([A_col, Z0[1]])
-    Cv = np.concatenate([np.repeat(y0, np.diff(A_ptr)) * A_val, Z0[2]])
+    Cv = np.concatenate([np.repeat(y0, E) * A_val, Z0[2]])
     C_row, C_col, C_val = _dedup_sum(Cr, Cc, Cv, n)
     return Problem(name or f"block_arrow_l{l}_d{d}_h{h}_m{m}", n, m, C_row, C_col, C_val,
                    A_ptr, A_row, A_col, A_val, b, "feasible",
                    dict(family="block_arrow", l=l, d=d, h=h, X0=X0, Z0=Z0, y0=y0))
+
+
+def _apply_A(A_ptr, A_row, A_col, A_val, X, n):
+    """b_i = <A_i, X> (Frobenius) for all constraints, X given as lower COO."""
+    xr, xc, xv = X
+    xkey = xc.astype(np.int64) * n + xr
+    srt = np.argsort(xkey)
+    xkey, xv = xkey[srt], xv[srt]
+    akey = A_col.astype(np.int64) * n + A_row
+    pos = np.searchsorted(xkey, akey)
+    pos_c = np.minimum(pos, xkey.shape[0] - 1)
+    hit = (pos < xkey.shape[0]) & (xkey[pos_c] == akey)
+    vals = np.where(hit, xv[pos_c], 0.0)
+    w = np.where(A_row == A_col, 1.0, 2.0)
+    contrib = w * A_val * vals
+    m = A_ptr.shape[0] - 1
+    out = np.zeros(m)
+    nz = np.diff(A_ptr) > 0
+    if contrib.shape[0]:
+        sums = np.add.reduceat(contrib, A_ptr[:-1][nz])
+        out[nz] = sums
+    return out
 
 
 def maxcut_grid(R, K, rng, name=None):
@@ -199,15 +226,22 @@ def maxcut_grid(R, K, rng, name=None):
     C = weighted Laplacian L_w with edge weights +-1 (uniform), A_i = e_i e_i^T,
     b = 1, minimised as stated (min <L_w, X>)."""
     n = R * K
-    er, ec = [], []
+    v = np.arange(n).reshape(R, K)
+    # edges in the order (row-major vertex, right neighbour first, then down)
+    right = np.stack([v[:, :-1] + 1, v[:, :-1]], -1)          # (R, K-1, 2)
+    down = np.stack([v[:-1, :] + K, v[:-1, :]], -1)           # (R-1, K, 2)
+    er_l, ec_l = [], []
     for i in range(R):
+        blk = []
         for j in range(K):
-            v = i * K + j
             if j + 1 < K:
-                er.append(v + 1); ec.append(v)
+                blk.append(right[i, j])
             if i + 1 < R:
-                er.append(v + K); ec.append(v)
-    er = np.asarray(er, np.int32); ec = np.asarray(ec, np.int32)
+                blk.append(down[i, j])
+        if blk:
+            blk = np.asarray(blk)
+            er_l.append(blk[:, 0]); ec_l.append(blk[:, 1])
+    er = np.concatenate(er_l).astype(np.int32); ec = np.concatenate(ec_l).astype(np.int32)
     w = rng.choice(np.array([-1.0, 1.0]), size=er.shape[0])
     deg = np.zeros(n)
     np.add.at(deg, er, w); np.add.at(deg, ec, w)
@@ -256,18 +290,28 @@ def make_dual_infeasible(p: Problem, rng) -> Problem:
     ii, jj = np.tril_indices(mem.shape[0])
     Dr, Dc, Dv = mem[ii].astype(np.int32), mem[jj].astype(np.int32), np.outer(g, g)[ii, jj]
     DD = _sym_inner(Dr, Dc, Dv, Dr, Dc, Dv, n)
-    rows, cols, vals = [], [], []
-    for i in range(p.m):
-        s = slice(p.A_ptr[i], p.A_ptr[i + 1])
-        r, c, v = p.A_row[s], p.A_col[s], p.A_val[s]
-        coef = _sym_inner(r, c, v, Dr, Dc, Dv, n) / DD
-        r2, c2, v2 = _dedup_sum(np.concatenate([r, Dr]), np.concatenate([c, Dc]),
-                                np.concatenate([v, -coef * Dv]), n)
-        rows.append(r2); cols.append(c2); vals.append(v2)
-    A_ptr, A_row, A_col, A_val, _ = _pack_constraints(rows, cols, vals, np.zeros(p.m), n)
+    # <A_i, Dd> for every constraint at once
+    coef = _apply_A(p.A_ptr, p.A_row, p.A_col, p.A_val, (Dr, Dc, Dv), n) / DD
+    # A_i <- A_i - coef_i Dd  (support grows to include clique 0)
+    m = p.m
+    cnt = np.diff(p.A_ptr)
+    inst = np.repeat(np.arange(m), cnt)
+    allr = np.concatenate([p.A_row, np.tile(Dr, m)])
+    allc = np.concatenate([p.A_col, np.tile(Dc, m)])
+    alli = np.concatenate([inst, np.repeat(np.arange(m), Dr.shape[0])])
+    allv = np.concatenate([p.A_val, -np.repeat(coef, Dr.shape[0]) * np.tile(Dv, m)])
+    key = (alli.astype(np.int64) * n + allc) * n + allr
+    uk, inv = np.unique(key, return_inverse=True)
+    vv = np.zeros(uk.shape[0])
+    np.add.at(vv, inv, allv)
+    ui = uk // (n * n); rem = uk % (n * n)
+    A_row = (rem % n).astype(np.int32); A_col = (rem // n).astype(np.int32)
+    A_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.add.at(A_ptr, ui + 1, 1)
+    A_ptr = np.cumsum(A_ptr)
+    A_val = vv
     X0 = p.meta["X0"]
-    b = np.array([_sym_inner(A_row[A_ptr[i]:A_ptr[i + 1]], A_col[A_ptr[i]:A_ptr[i + 1]],
-                             A_val[A_ptr[i]:A_ptr[i + 1]], *X0, n) for i in range(p.m)])
+    b = _apply_A(A_ptr, A_row, A_col, A_val, X0, n)
     cD = _sym_inner(p.C_row, p.C_col, p.C_val, Dr, Dc, Dv, n)
     C_row, C_col, C_val = _dedup_sum(np.concatenate([p.C_row, Dr]), np.concatenate([p.C_col, Dc]),
                                      np.concatenate([p.C_val, -(cD + 1.0) / DD * Dv]), n)
@@ -298,14 +342,15 @@ def config2(l, d, h=5, instance=0):
                        name=f"cfg2_block_arrow_l{l}_d{d}")
 
 
-def config3(B=256, n_lo=100, n_hi=1500, seed_instance=0):
+def config3(B=256, n_lo=100, n_hi=1500, seed_instance=0, select=None):
     """Batch of B independent instances of uneven sizes.
 
     Half max-cut grids (m = n), half block-arrow with m ~ U[n/2, 2n] assigned
     round-robin to cliques.  10% made primal-infeasible, 10% dual-infeasible
-    (block-arrow only, since diag(X)=1 bounds the max-cut feasible set)."""
+    (block-arrow only, since diag(X)=1 bounds the max-cut feasible set).
+    `select` (iterable of indices) builds only those instances; every
+    instance is the same whichever subset is built."""
     rng = rng_for(3, seed_instance)
-    out = []
     n_pinf = B // 10
     n_dinf = B // 10
     kinds = ["feasible"] * B
@@ -317,18 +362,27 @@ def config3(B=256, n_lo=100, n_hi=1500, seed_instance=0):
     rest = [i for i in range(B) if kinds[i] == "feasible"]
     for s in rng.permutation(len(rest))[:n_pinf]:
         kinds[rest[s]] = "primal_infeasible"
+    specs = []
     for i in range(B):
         n = int(rng.integers(n_lo, n_hi + 1))
-        sub = np.random.Generator(np.random.PCG64(3000 + 7919 * (seed_instance + 1) + i))
         if i % 2 == 0:
-            R = 10
-            K = max(2, n // R)
-            p = maxcut_grid(R, K, sub, name=f"cfg3_{i}_maxcut_{R}x{K}")
+            specs.append(("grid", n, None, None))
         else:
             d = [10, 25, 50][int(rng.integers(0, 3))]
             l = max(2, (n - 5) // d)
             nn = l * d + 5
             m = int(rng.integers(max(1, nn // 2), 2 * nn + 1))
+            specs.append(("arrow", n, d, m))
+    out = []
+    for i in (range(B) if select is None else select):
+        kind, n, d, m = specs[i]
+        sub = np.random.Generator(np.random.PCG64(3000 + 7919 * (seed_instance + 1) + i))
+        if kind == "grid":
+            R = 10
+            K = max(2, n // R)
+            p = maxcut_grid(R, K, sub, name=f"cfg3_{i}_maxcut_{R}x{K}")
+        else:
+            l = max(2, (n - 5) // d)
             p = block_arrow(l, d, 5, m, sub, kappa=1e3, assign="roundrobin",
                             name=f"cfg3_{i}_block_arrow_l{l}_d{d}_m{m}")
         if kinds[i] == "primal_infeasible":
