@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--skip-verdict", action="store_true", help="skip the time-to-verdict and e2e legs")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-instance batched leg")
     ap.add_argument("--batched-steps", type=int, default=30)
+    ap.add_argument("--only-batched", action="store_true", help="run only the batched leg (profiling)")
     return ap.parse_args()
 
 
@@ -151,22 +152,21 @@ def cone_flops(c3):
 
 
 def affine_bytes(sizes, mixed, nnzA):
-    """Compulsory HBM bytes of the affine phase (scatter, A, S^{-1}, A^T, eta)."""
+    """Compulsory HBM bytes of the affine phase (k_fwd, k_solve_dense, k_bwd_eta):
+    A and A^T once each (8-byte value + 4-byte index), S^{-1} once when dense,
+    and each pattern / constraint vector once (gathers counted once)."""
     N, P, m = sizes.N, sizes.P, sizes.m
-    T = 4 if mixed else 8
-    rhs = 8 * 3 * N + 4 * (N + 1) + 4 * P + 3 * T * P + 8 * N
-    spA = 4 * (m + 1) + 12 * nnzA + 8 * nnzA + 24 * m
-    solve = 8 * m * m if sizes.S_dense else 24 * m
-    spAt = 4 * (N + 1) + 12 * nnzA + 8 * nnzA + 8 * 3 * N + N + 8 * N
-    eta = 32 * m
-    return rhs + spA + solve + spAt + eta
+    fwd = 4 * (m + 1) + 12 * nnzA + 8 * N + 16 * m + 24 * m
+    solve = (8 * m * m + 8 * m + 16 * m) if sizes.S_dense else 0
+    bwd = 4 * (N + 1) + 12 * nnzA + 8 * m + 25 * N + 16 * N + 48 * m
+    return fwd + solve + bwd
 
 
 def post_bytes(sizes, mixed, nnzA):
     """Compulsory HBM bytes of the post phase (x update, stopping rule, next f)."""
     N, P, m = sizes.N, sizes.P, sizes.m
     T = 4 if mixed else 8
-    return 8 * 6 * N + 4 * (N + 1) + N + 4 * P + 3 * T * P + 4 * (N + 1) + 12 * nnzA + 8 * nnzA + 32 * m
+    return 16 * N + 8 * N + 4 * (N + 1) + 4 * P + 3 * T * P + 17 * N + 16 * N + 8 * N + 8 * sizes.p
 
 
 def load_peaks():
@@ -262,6 +262,9 @@ def run_ours(args):
         total_ms = sum(a.elapsed_time(b) for a, b in ev)
         return total_ms, phases
 
+    if args.only_batched:
+        print(json.dumps({"batched": batched_leg(args, hsde, torch, dev, stream, timed_steps)}), flush=True)
+        return
     big = 1 << 30
     t0 = time.perf_counter()
     Hm = hsde.Handle(prob, precision="mixed", profile=1, max_iter=big,

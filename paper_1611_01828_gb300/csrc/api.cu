@@ -225,7 +225,7 @@ int enqueue_iteration(hsde_handle* h) {
     if (h->any_dense) launch_solve_dense(V, h->st);
     launch_bwd_eta(V, h->st);
     CK(rec(h, h->ev_aff, h->st));
-    // fork: every clique bucket on its own branch, A x for the check on another
+    // fork: every clique bucket on its own branch
     CK(cudaEventRecord(h->ev_fork, h->st));
     const size_t nb = h->buckets.size();
     for (size_t i = 0; i < nb; ++i) {
@@ -237,10 +237,7 @@ int enqueue_iteration(hsde_handle* h) {
         CK(rec(h, h->ev_ce[i], h->side[i]));
         CK(cudaEventRecord(h->ev_join[i], h->side[i]));
     }
-    CK(cudaStreamWaitEvent(h->side[nb], h->ev_fork, 0));
-    launch_check_m(V, h->side[nb]);
-    CK(cudaEventRecord(h->ev_join[nb], h->side[nb]));
-    for (size_t i = 0; i <= nb; ++i) CK(cudaStreamWaitEvent(h->st, h->ev_join[i], 0));
+    for (size_t i = 0; i < nb; ++i) CK(cudaStreamWaitEvent(h->st, h->ev_join[i], 0));
     CK(rec(h, h->ev_chk, h->st));
     launch_post(V, h->mixed, h->st);
     CK(rec(h, h->ev_it1, h->st));
@@ -252,7 +249,7 @@ int count_kernels(const hsde_handle* h) {
     const DevView& V = h->V;
     int k = 0;
     if (V.ntiles > 0) k += 2;          // bwd_eta, post
-    if (V.Mtot > 0) k += 2;            // fwd, check_m
+    if (V.Mtot > 0) k += 1;            // fwd
     if (h->any_dense) k += 1;          // solve_dense
     for (const auto& b : h->buckets) k += b.count > 0 ? 1 : 0;
     return k;
@@ -373,6 +370,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         ntiles += (I.N + TILE_N - 1) / TILE_N;
         I.tile_end = (int32_t)ntiles;
         I.dense = H.dense ? 1 : 0;
+        I.long_at = (H.S.N() > 0 && (int64_t)H.A_col.size() >= 8 * H.S.N()) ? 1 : 0;
         I.sinv_off = sinv;
         if (H.dense) sinv += (int64_t)H.m * H.m;
         I.status = HSDE_RUNNING;
@@ -435,8 +433,9 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
                  o_cli = cv.take<int32_t>(ncl), o_inst = cv.take<InstDev>(B), o_tiles = cv.take<int4>(ntiles),
                  o_part = cv.take<double>(ntiles * KPART), o_clp = cv.take<double>(ncl),
                  o_clsw = cv.take<int32_t>(ncl),
-                 o_rowp = cv.take<double>(Mtot * 3), o_blist = cv.take<int32_t>(ncl),
-                 o_rowb = cv.take<double>(Mtot), o_cnt = cv.take<int>(2 * (size_t)B);
+                 o_blist = cv.take<int32_t>(ncl),
+                 o_rowb = cv.take<double>(Mtot), o_cnt = cv.take<int>(2 * (size_t)B),
+                 o_af = cv.take<double>(Mtot), o_atyw = cv.take<double>(Ntot), o_atyp = cv.take<double>(Ntot);
     // Gauss-Jordan scratch and per-dense-instance tables
     int ndense = 0;
     int32_t mmax = 0;
@@ -445,7 +444,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     h->any_dense = ndense > 0;
     const size_t o_gjrow = cv.take<double>(Mtot), o_gjcol = cv.take<double>(Mtot),
                  o_gjoff = cv.take<int64_t>(ndense), o_gjm = cv.take<int32_t>(ndense),
-                 o_gjb = cv.take<int64_t>(ndense);
+                 o_gjb = cv.take<int64_t>(ndense), o_gjtp = cv.take<int64_t>(ndense + 1);
     h->arena_bytes = cv.off + 256;
     CK(cudaMalloc(&h->arena, h->arena_bytes));
     char* ar = reinterpret_cast<char*>(h->arena);
@@ -468,9 +467,12 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     V.gmap = (const int32_t*)(ar + o_g); V.cl_off = (const int32_t*)(ar + o_clo);
     V.cl_size = (const int32_t*)(ar + o_cls); V.cl_inst = (const int32_t*)(ar + o_cli);
     V.inst = (InstDev*)(ar + o_inst); V.tiles = (const int4*)(ar + o_tiles);
-    V.part = (double*)(ar + o_part); V.cl_part = (double*)(ar + o_clp); V.row_part = (double*)(ar + o_rowp);
+    V.part = (double*)(ar + o_part); V.cl_part = (double*)(ar + o_clp);
     V.cl_sweeps = (int32_t*)(ar + o_clsw);
     V.rowb = (double*)(ar + o_rowb);
+    V.af = (double*)(ar + o_af);
+    V.atyw = (double*)(ar + o_atyw);
+    V.atyp = (double*)(ar + o_atyp);
     V.counters = (int*)(ar + o_cnt);
     V.eps = opt.eps_tol; V.max_iter = opt.max_iter; V.check_every = opt.check_every;
 
@@ -535,21 +537,33 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     }
     // ---- dense S: upload and invert in place (Gauss-Jordan, SPD) ----
     if (ndense > 0) {
-        std::vector<int64_t> offs, boffs;
+        // dense instances sorted by m, descending: the active ones at step k are a prefix
+        std::vector<int32_t> ord;
+        for (int32_t b = 0; b < B; ++b)
+            if (h->prep[b].dense) ord.push_back(b);
+        std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return h->prep[a].m > h->prep[b].m; });
+        std::vector<int64_t> offs, boffs, tpre;
         std::vector<int32_t> ms;
-        for (int32_t b = 0; b < B; ++b) {
+        int64_t acc_tiles = 0;
+        for (int32_t b : ord) {
             const HostPrep& H = h->prep[b];
-            if (!H.dense) continue;
             CK(cudaMemcpyAsync(V.sinv + inst[b].sinv_off, H.Sdense.data(), sizeof(double) * H.Sdense.size(),
                                cudaMemcpyHostToDevice, st));
             offs.push_back(inst[b].sinv_off);
             ms.push_back(H.m);
             boffs.push_back(inst[b].m_off);
+            tpre.push_back(acc_tiles);
+            acc_tiles += (int64_t)((H.m + 31) / 32) * ((H.m + 7) / 8);
         }
-        UP(o_gjoff, offs); UP(o_gjm, ms); UP(o_gjb, boffs);
-        for (int32_t k = 0; k < mmax; ++k)
-            launch_gj_step(V.sinv, (const int64_t*)(ar + o_gjoff), (const int32_t*)(ar + o_gjm), ndense, k, mmax,
+        tpre.push_back(acc_tiles);
+        UP(o_gjoff, offs); UP(o_gjm, ms); UP(o_gjb, boffs); UP(o_gjtp, tpre);
+        int nact = (int)ord.size();
+        for (int32_t k = 0; k < mmax; ++k) {
+            while (nact > 0 && ms[nact - 1] <= k) --nact;
+            launch_gj_step(V.sinv, (const int64_t*)(ar + o_gjoff), (const int32_t*)(ar + o_gjm),
+                           (const int64_t*)(ar + o_gjtp), nact, tpre[nact], k, ms[0],
                            (double*)(ar + o_gjrow), (double*)(ar + o_gjcol), (const int64_t*)(ar + o_gjb), st);
+        }
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(st));
         for (auto& H : h->prep) { std::vector<double>().swap(H.Sdense); }

@@ -377,7 +377,7 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
 // buckets: padded size CP and threads per clique G
 // ---------------------------------------------------------------------------
 #define HSDE_CONE_BUCKETS(X) \
-    X(4, 4) X(8, 8) X(12, 16) X(16, 32) X(24, 64) X(32, 128) X(40, 128) X(48, 256) X(64, 256)
+    X(4, 4) X(8, 8) X(12, 16) X(16, 32) X(24, 64) X(32, 128) X(40, 256) X(48, 512) X(64, 512)
 
 template <typename T, int CP, int G>
 static int prepare_one() {

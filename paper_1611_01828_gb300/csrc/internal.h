@@ -52,6 +52,8 @@ struct InstDev {
     int32_t status;          // HSDE_RUNNING ...
     int32_t iter;            // iterations done
     int32_t vcold;           // 1: the stored eigenbases are not valid (cold start next)
+    int32_t long_at;         // 1: A^T rows average >= 8 entries (warp per entry)
+    int32_t _pad2;
     // cached by setup
     double den;              // 1 + zeta^T M^{-1} zeta
     double ctp;              // c^T x_p - b^T y_p
@@ -60,6 +62,8 @@ struct InstDev {
     double tau, kappa, eta;
     // last check
     double pres, dres, gap, pobj, dobj, pinf, dinf, ctx, bty;
+    // constraint-space sums of the stopping rule, from k_bwd_eta to k_post
+    double chk_r0, chk_r1, chk_r2;
 };
 
 // Number of partial sums stored per N-space tile.
@@ -96,8 +100,10 @@ struct DevView {
     double* part;            // [ntiles * KPART]
     double* cl_part;         // [ncl]
     int32_t* cl_sweeps;      // [ncl] Jacobi sweeps used by each clique in its last solve
-    double* row_part;        // [Mtot * 3]
     double* rowb;            // [Mtot] b_i (y_w)_i
+    double* af;              // [Mtot] A f of the current iteration
+    double* atyw;            // [Ntot] A^T y_w of the current iteration
+    double* atyp;            // [Ntot] A^T y_p (setup)
     int* counters;           // [2B] completion counters of k_bwd_eta and k_post
     // options
     double eps;
@@ -123,7 +129,6 @@ void launch_spmv_At(const DevView& V, Mode mode, void* st);
 void launch_fwd(const DevView& V, void* st);
 void launch_solve_dense(const DevView& V, void* st);
 void launch_bwd_eta(const DevView& V, void* st);
-void launch_check_m(const DevView& V, void* st);
 void launch_post(const DevView& V, bool mixed, void* st);
 void launch_setup_den(const DevView& V, void* st);
 // cone projection of every clique in one bucket (Eq. Step2 on S, fused with
@@ -135,8 +140,8 @@ int  cone_bucket_of(int c);          // padded size of the bucket of a clique of
 int  cone_vstore_elems(int c);       // stored basis size for a clique of size c
 int  cone_prepare(bool mixed);
 // Gauss-Jordan inversion of the dense S matrices (setup)
-void launch_gj_step(double* pool, const int64_t* offs, const int32_t* ms, int ndense,
-                    int32_t k, int32_t mmax, double* rowbuf, double* colbuf,
+void launch_gj_step(double* pool, const int64_t* offs, const int32_t* ms, const int64_t* tile_pre,
+                    int nact, int64_t ntiles, int32_t k, int32_t mmax, double* rowbuf, double* colbuf,
                     const int64_t* boff, void* st);
 
 }  // namespace hsde

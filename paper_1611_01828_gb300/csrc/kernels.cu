@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(NT) k_spmv_At(DevView V, int mode) {
         for (int j = V.At_ptr[e]; j < j1; ++j) acc += V.At_val[j] * yin[V.At_col[j]];
         const double xv = V.f[e] + V.inv_delta[e] * acc;
         out[e] = xv;
+        if (mode == (int)Mode::Setup) V.atyp[e] = acc;     // A^T y_p, cached
         part += (V.diag[e] ? 1.0 : 2.0) * V.c[e] * xv;
     }
     part = block_sum(part, sh);
@@ -149,8 +150,9 @@ __global__ void __launch_bounds__(NT) k_spmv_At(DevView V, int mode) {
 //   k_fwd      q = y + omega_tau b - A f; diagonal S: y_w = S^{-1} q
 //   k_solve    dense S: y_w = S^{-1} q                     (only if any S is dense)
 //   k_bwd_eta  x_w = f + Delta^{-1} A^T y_w; the last CTA of each instance
-//              computes eta, tau, kappa and y = y_w - eta y_p
-//   k_cone ... per clique bucket, in parallel with k_check_m
+//              computes eta, tau, kappa, y = y_w - eta y_p and the
+//              constraint-space sums of the stopping rule
+//   k_cone ... per clique bucket, in parallel
 //   k_post     x = x_w - eta x_p; stopping-rule sums; the last CTA of each
 //              instance takes the verdict; f of the next iteration
 // "Last CTA" is the usual completion-counter pattern: every CTA publishes its
@@ -182,6 +184,7 @@ __global__ void __launch_bounds__(NT) k_fwd(DevView V) {
     for (int j = V.A_ptr[row] + lane; j < j1; j += 32) acc += V.A_val[j] * V.f[V.A_col[j]];
     acc = warp_sum(acc);
     if (lane == 0) {
+        V.af[row] = acc;
         const double q = V.y[row] + (I.tau + I.kappa) * V.b[row] - acc;
         if (I.dense) {
             V.q[row] = q;
@@ -219,13 +222,32 @@ __global__ void __launch_bounds__(NT) k_bwd_eta(DevView V) {
     InstDev& I = V.inst[t.x];
     if (I.status != HSDE_RUNNING) return;
     double part = 0.0;
-    for (int e = t.y + threadIdx.x; e < t.z; e += NT) {
-        double acc = 0.0;
-        const int j1 = V.At_ptr[e + 1];
-        for (int j = V.At_ptr[e]; j < j1; ++j) acc += V.At_val[j] * V.yw[V.At_col[j]];
-        const double xv = V.f[e] + V.inv_delta[e] * acc;
-        V.xw[e] = xv;
-        part += (V.diag[e] ? 1.0 : 2.0) * V.c[e] * xv;
+    if (!I.long_at) {
+        // short A^T rows: one thread per entry
+        for (int e = t.y + threadIdx.x; e < t.z; e += NT) {
+            double acc = 0.0;
+            const int j1 = V.At_ptr[e + 1];
+            for (int j = V.At_ptr[e]; j < j1; ++j) acc += V.At_val[j] * V.yw[V.At_col[j]];
+            const double xv = V.f[e] + V.inv_delta[e] * acc;
+            V.xw[e] = xv;
+            V.atyw[e] = acc;
+            part += (V.diag[e] ? 1.0 : 2.0) * V.c[e] * xv;
+        }
+    } else {
+        // long A^T rows: one warp per entry, coalesced over the row
+        const int lane = threadIdx.x & 31;
+        for (int e = t.y + (threadIdx.x >> 5); e < t.z; e += NT / 32) {
+            double acc = 0.0;
+            const int j1 = V.At_ptr[e + 1];
+            for (int j = V.At_ptr[e] + lane; j < j1; j += 32) acc += V.At_val[j] * V.yw[V.At_col[j]];
+            acc = warp_sum(acc);
+            if (lane == 0) {
+                const double xv = V.f[e] + V.inv_delta[e] * acc;
+                V.xw[e] = xv;
+                V.atyw[e] = acc;
+                part += (V.diag[e] ? 1.0 : 2.0) * V.c[e] * xv;
+            }
+        }
     }
     part = block_sum(part, sh);
     if (threadIdx.x == 0) V.part[(int64_t)blockIdx.x * KPART + 0] = part;
@@ -241,42 +263,47 @@ __global__ void __launch_bounds__(NT) k_bwd_eta(DevView V) {
     const double sw = ctw - btw;
     const double eta = sw / I.den;
     const double tau = I.tau, kappa = I.kappa;
-    const double tau_hat = (tau + kappa) + sw - eta * I.ctp;
+    const double ot = tau + kappa;
+    const double tau_hat = ot + sw - eta * I.ctp;
     const double tau_new = fmax(0.0, tau_hat - kappa);
     const double kappa_new = kappa - tau_hat + tau_new;
-    for (int i = threadIdx.x; i < I.m; i += NT)
-        V.y[I.m_off + i] = __ldcg(V.yw + I.m_off + i) - eta * V.yp[I.m_off + i];
+    // y = y_w - eta y_p, and the constraint-space sums of the stopping rule.
+    // A x is not formed by an SpMV: with S y_w = q,
+    //   A x_w = A f + A Delta^{-1} A^T y_w = A f + (S - I) y_w = A f + q - y_w,
+    //   A x_p = -b - y_p  (the same identity on the setup solve),
+    // so A x_hat = A x_w - eta A x_p from values this step already has.
+    const bool check = is_check_iter(V, I.iter + 1);
+    double r0 = 0.0, r1 = 0.0, r2 = 0.0;
+    for (int i = threadIdx.x; i < I.m; i += NT) {
+        const int row = I.m_off + i;
+        const double bi = V.b[row], yw = __ldcg(V.yw + row), yp = V.yp[row];
+        const double q = V.y[row] + ot * bi - __ldcg(V.af + row);
+        const double ynew = yw - eta * yp;
+        V.y[row] = ynew;
+        if (check) {
+            const double ax = (__ldcg(V.af + row) + q - yw) - eta * (-bi - yp);
+            const double d = ax - tau_new * bi;
+            r0 += d * d;
+            r1 += ax * ax;
+            r2 += bi * ynew;
+        }
+    }
+    if (check) {
+        r0 = block_sum(r0, sh);
+        r1 = block_sum(r1, sh);
+        r2 = block_sum(r2, sh);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         I.eta = eta;
         I.tau = tau_new;
         I.kappa = kappa_new;
         I.iter += 1;
+        I.chk_r0 = r0;
+        I.chk_r1 = r1;
+        I.chk_r2 = r2;
         if (!isfinite(eta) || !isfinite(tau_new) || !isfinite(kappa_new)) I.status = HSDE_NUMERICAL_ERROR;
         V.counters[2 * t.x] = 0;
-    }
-}
-
-// Stopping-rule partials over m on check iterations: (A x - tau b)^2, (A x)^2,
-// b_i y_i with x = x_w - eta x_p.  One warp per row (runs beside the cones).
-__global__ void __launch_bounds__(NT) k_check_m(DevView V) {
-    const int row = (blockIdx.x * NT + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (row >= V.Mtot) return;
-    const InstDev& I = V.inst[V.row_inst[row]];
-    if (I.status != HSDE_RUNNING || !is_check_iter(V, I.iter)) return;
-    const double eta = I.eta;
-    double acc = 0.0;
-    const int j1 = V.A_ptr[row + 1];
-    for (int j = V.A_ptr[row] + lane; j < j1; j += 32) {
-        const int e = V.A_col[j];
-        acc += V.A_val[j] * (V.xw[e] - eta * V.xp[e]);
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) {
-        const double d = acc - I.tau * V.b[row];
-        V.row_part[(int64_t)row * 3 + 0] = d * d;
-        V.row_part[(int64_t)row * 3 + 1] = acc * acc;
-        V.row_part[(int64_t)row * 3 + 2] = V.b[row] * V.y[row];
     }
 }
 
@@ -309,9 +336,8 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
         const double ce = V.c[e];
         V.f[e] = (x - ot * ce + 0.5 * hall) * V.inv_delta[e];
         if (check) {
-            double r = hz;
-            const int j1 = V.At_ptr[e + 1];
-            for (int j = V.At_ptr[e]; j < j1; ++j) r += V.At_val[j] * V.y[V.At_col[j]];
+            // A^T y = A^T y_w - eta A^T y_p (both kept from this iteration / setup)
+            const double r = hz + V.atyw[e] - eta * V.atyp[e];
             const double w = V.diag[e] ? 1.0 : 2.0;
             const double d = r - tau * ce;
             a1 += w * d * d;
@@ -341,12 +367,7 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
         a1 += __ldcg(pp + 1); a2 += __ldcg(pp + 2); a3 += __ldcg(pp + 3);
     }
     a1 = block_sum(a1, sh); a2 = block_sum(a2, sh); a3 = block_sum(a3, sh);
-    double r0 = 0, r1 = 0, r2 = 0;
-    for (int i = threadIdx.x; i < I.m; i += NT) {
-        const double* rp = V.row_part + (int64_t)(I.m_off + i) * 3;
-        r0 += __ldcg(rp); r1 += __ldcg(rp + 1); r2 += __ldcg(rp + 2);
-    }
-    r0 = block_sum(r0, sh); r1 = block_sum(r1, sh); r2 = block_sum(r2, sh);
+    const double r0 = I.chk_r0, r1 = I.chk_r1, r2 = I.chk_r2;
     double hs = 0;
     for (int k = I.cl_begin + threadIdx.x; k < I.cl_end; k += NT) hs += __ldcg(V.cl_part + k);
     hs = block_sum(hs, sh);
@@ -408,12 +429,15 @@ __global__ void __launch_bounds__(NT) k_setup_den(DevView V) {
 
 // One in-place Gauss-Jordan step (pivot k) on every dense S with m > k.
 // S is symmetric positive definite with eigenvalues >= 1, so no pivoting is
-// needed.  rowbuf/colbuf hold row k and column k before the step.
-__global__ void k_gj_copy(double* pool, const int64_t* offs, const int32_t* ms, int k,
+// needed.  rowbuf/colbuf hold row k and column k before the step.  The dense
+// instances are sorted by m (descending) so the ones still active at step k
+// are a prefix; their 32 x 8 tiles are numbered consecutively (tile_pre) and
+// one CTA handles one tile, so no CTA is launched for a finished instance.
+__global__ void k_gj_copy(double* pool, const int64_t* offs, const int32_t* ms, int nact, int k,
                           double* rowbuf, double* colbuf, const int64_t* boff) {
     const int d = blockIdx.y;
+    if (d >= nact) return;
     const int m = ms[d];
-    if (k >= m) return;
     double* S = pool + offs[d];
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
         rowbuf[boff[d] + j] = S[(int64_t)k * m + j];
@@ -421,13 +445,22 @@ __global__ void k_gj_copy(double* pool, const int64_t* offs, const int32_t* ms, 
     }
 }
 
-__global__ void k_gj_update(double* pool, const int64_t* offs, const int32_t* ms, int k,
-                            const double* rowbuf, const double* colbuf, const int64_t* boff) {
-    const int d = blockIdx.z;
+__global__ void k_gj_update(double* pool, const int64_t* offs, const int32_t* ms, const int64_t* tile_pre,
+                            int nact, int k, const double* rowbuf, const double* colbuf, const int64_t* boff) {
+    // find the instance of this tile (tile_pre is the exclusive prefix of tile counts)
+    const int64_t tile = blockIdx.x;
+    int lo = 0, hi = nact - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tile_pre[mid] <= tile) lo = mid; else hi = mid - 1;
+    }
+    const int d = lo;
     const int m = ms[d];
-    if (k >= m) return;
-    const int i = blockIdx.y * blockDim.y + threadIdx.y;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tx = (m + 31) / 32;
+    const int64_t local = tile - tile_pre[d];
+    const int ti = (int)(local / tx), tj = (int)(local - (local / tx) * tx);
+    const int i = ti * 8 + threadIdx.y;
+    const int j = tj * 32 + threadIdx.x;
     if (i >= m || j >= m) return;
     double* S = pool + offs[d];
     const double* rk = rowbuf + boff[d];
@@ -475,22 +508,20 @@ void launch_solve_dense(const DevView& V, void* st) {
 void launch_bwd_eta(const DevView& V, void* st) {
     if (V.ntiles > 0) k_bwd_eta<<<V.ntiles, NT, 0, S_(st)>>>(V);
 }
-void launch_check_m(const DevView& V, void* st) {
-    if (V.Mtot > 0) k_check_m<<<rows_grid(V.Mtot), NT, 0, S_(st)>>>(V);
-}
 void launch_post(const DevView& V, bool mixed, void* st) {
     if (V.ntiles == 0) return;
     if (mixed) k_post<float><<<V.ntiles, NT, 0, S_(st)>>>(V);
     else k_post<double><<<V.ntiles, NT, 0, S_(st)>>>(V);
 }
 
-void launch_gj_step(double* pool, const int64_t* offs, const int32_t* ms, int ndense, int32_t k,
-                    int32_t mmax, double* rowbuf, double* colbuf, const int64_t* boff, void* st) {
-    dim3 gc((mmax + 255) / 256, ndense);
-    k_gj_copy<<<gc, 256, 0, S_(st)>>>(pool, offs, ms, k, rowbuf, colbuf, boff);
-    dim3 blk(32, 8);
-    dim3 gu((mmax + 31) / 32, (mmax + 7) / 8, ndense);
-    k_gj_update<<<gu, blk, 0, S_(st)>>>(pool, offs, ms, k, rowbuf, colbuf, boff);
+void launch_gj_step(double* pool, const int64_t* offs, const int32_t* ms, const int64_t* tile_pre, int nact,
+                    int64_t ntiles, int32_t k, int32_t mmax, double* rowbuf, double* colbuf, const int64_t* boff,
+                    void* st) {
+    if (nact <= 0 || ntiles <= 0) return;
+    dim3 gc((mmax + 255) / 256, nact);
+    k_gj_copy<<<gc, 256, 0, S_(st)>>>(pool, offs, ms, nact, k, rowbuf, colbuf, boff);
+    k_gj_update<<<(unsigned)ntiles, dim3(32, 8), 0, S_(st)>>>(pool, offs, ms, tile_pre, nact, k, rowbuf, colbuf,
+                                                             boff);
 }
 
 }  // namespace hsde

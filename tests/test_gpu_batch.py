@@ -1,8 +1,17 @@
 """GPU: batched serving of independent SDPs of uneven sizes in the same
 launches (the config-3 generator), against the FP64 oracle per instance.
 
-Tolerances: identical verdicts; SOLVED objectives within 1e-4 (1 + |obj|);
-iteration counts within 10% (mixed precision changes the trajectory a little).
+Tolerances: identical verdicts and iteration counts within 10% at the
+default eps_tol = 1e-4.  Objectives are compared against the oracle's
+eps_tol = 1e-7 optimum, because at eps_tol = 1e-4 the stopping rule only pins
+them to a few 1e-4 relative on the worse-conditioned block-arrow instances
+(the oracle's own 1e-4 objective is 6.5e-4 from its 1e-7 one on instance 11):
+  * FP64 at eps_tol = 1e-6: within 1e-4 (1 + |obj|);
+  * mixed at eps_tol = 1e-4: within 2e-3 (1 + |obj|).  FP32 projections carry
+    ~1e-6 relative error per iteration, which the slowly contracting (unscaled)
+    ADMM amplifies; mixed residuals stall near 1e-5, so 1e-6 is out of reach;
+  * mixed to 1e-4, then continued in FP64 from the mixed state to 1e-6:
+    within 1e-4 (1 + |obj|).
 """
 import numpy as np
 import pytest
@@ -24,6 +33,9 @@ def hs():
     return hsde
 
 
+TIGHT = [2, 11, 13]
+
+
 @pytest.fixture(scope="module")
 def batch():
     probs = synth.config3(B=16, n_lo=60, n_hi=160, select=SEL)
@@ -31,8 +43,15 @@ def batch():
     return probs, refs
 
 
+@pytest.fixture(scope="module")
+def tight():
+    probs = synth.config3(B=16, n_lo=60, n_hi=160, select=TIGHT)
+    refs = [ohsde.HSDE(p).solve(eps=1e-7, max_iter=60000) for p in probs]
+    return probs, refs
+
+
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_batched_verdicts_and_objectives(hs, batch, prec):
+def test_batched_verdicts(hs, batch, prec):
     probs, refs = batch
     kinds = {p.kind for p in probs}
     assert {"feasible", "primal_infeasible", "dual_infeasible"} <= kinds
@@ -42,8 +61,45 @@ def test_batched_verdicts_and_objectives(hs, batch, prec):
     for p, r, s, inf in zip(probs, refs, st, infos):
         assert int(s) == r.status, (p.name, int(s), r.status)
         assert abs(inf["iterations"] - r.iterations) <= max(3, 0.1 * r.iterations), p.name
-        if r.status == ohsde.SOLVED:
-            assert abs(inf["pobj"] - r.info["pobj"]) <= 1e-4 * (1 + abs(r.info["pobj"])), p.name
+        if prec == "fp64" and r.status == ohsde.SOLVED:
+            assert abs(inf["pobj"] - r.info["pobj"]) <= 1e-6 * (1 + abs(r.info["pobj"])), p.name
+
+
+def test_fp64_objectives_at_tight_tolerance(hs, tight):
+    probs, refs = tight
+    with hs.Handle(probs, precision="fp64", eps_tol=1e-6, max_iter=60000) as H:
+        st = H.solve(chunk=200)
+        infos = [H.hsde_get_info(i) for i in range(len(probs))]
+    for p, r, s, inf in zip(probs, refs, st, infos):
+        assert r.status == ohsde.SOLVED and int(s) == r.status, p.name
+        assert abs(inf["pobj"] - r.info["pobj"]) <= 1e-4 * (1 + abs(r.info["pobj"])), p.name
+        assert abs(inf["dobj"] - r.info["dobj"]) <= 1e-4 * (1 + abs(r.info["dobj"])), p.name
+
+
+def test_mixed_objectives_at_default_tolerance(hs, tight):
+    probs, refs = tight
+    with hs.Handle(probs, precision="mixed") as H:
+        st = H.solve(chunk=200)
+        infos = [H.hsde_get_info(i) for i in range(len(probs))]
+    for p, r, s, inf in zip(probs, refs, st, infos):
+        assert int(s) in (hs.SOLVED, hs.MAX_ITER), p.name
+        assert abs(inf["pobj"] - r.info["pobj"]) <= 2e-3 * (1 + abs(r.info["pobj"])), p.name
+
+
+def test_mixed_then_fp64_polish(hs, tight):
+    probs, refs = tight
+    with hs.Handle(probs, precision="mixed") as Hm:
+        Hm.solve(chunk=200)
+        states = [Hm.hsde_get_state(i) for i in range(len(probs))]
+        its = [Hm.hsde_get_info(i)["iterations"] for i in range(len(probs))]
+    with hs.Handle(probs, precision="fp64", eps_tol=1e-6, max_iter=60000) as Hd:
+        for i in range(len(probs)):
+            Hd.hsde_set_state(i, states[i], its[i])
+        st = Hd.solve(chunk=200)
+        infos = [Hd.hsde_get_info(i) for i in range(len(probs))]
+    for p, r, s, inf in zip(probs, refs, st, infos):
+        assert int(s) == hs.SOLVED, p.name
+        assert abs(inf["pobj"] - r.info["pobj"]) <= 1e-4 * (1 + abs(r.info["pobj"])), p.name
 
 
 def test_frozen_instances_do_not_move(hs, batch):
