@@ -1,0 +1,73 @@
+"""Pins of the oracle's reverse-mode gradient of f(C, b) = c^T x_K / tau_K
+after K unrolled ADMM iterations: central finite differences of the oracle's
+own forward (step 1e-6, FP64) on random directions, a finite-difference check
+of the Daleckii-Krein product alone, and the literal sparse Q against the
+dense one."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import adjoint, dense, hsde
+
+
+def _perturbed(p, dC_lower_vals, db, t):
+    q = synth.Problem(**{**p.__dict__})
+    q.C_val = p.C_val + t * dC_lower_vals
+    q.b = p.b + t * db
+    return q
+
+
+def _C_on_pattern(p, st):
+    """Give C an explicit entry on every pattern position (zeros allowed) so
+    that perturbations can touch all of them."""
+    pos = {(r, c): e for e, (r, c) in enumerate(zip(p.C_row.tolist(), p.C_col.tolist()))}
+    vals = np.zeros(st.N)
+    for e, (r, c) in enumerate(zip(st.pat_row.tolist(), st.pat_col.tolist())):
+        if (r, c) in pos:
+            vals[e] = p.C_val[pos[(r, c)]]
+    q = synth.Problem(**{**p.__dict__})
+    q.C_row, q.C_col, q.C_val = st.pat_row.copy(), st.pat_col.copy(), vals
+    return q
+
+
+def test_dk_vjp_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    for c in (2, 4, 7):
+        A = rng.standard_normal((c, c)); A = A + A.T
+        G = rng.standard_normal((c, c)); G = G + G.T
+        D = rng.standard_normal((c, c)); D = D + D.T
+        h = 1e-6
+        fd = (np.sum(G * hsde.project_psd(A + h * D)) - np.sum(G * hsde.project_psd(A - h * D))) / (2 * h)
+        assert abs(fd - np.sum(adjoint.dk_vjp(A, G) * D)) <= 1e-6 * (1 + abs(fd))
+
+
+def test_sparse_Q_equals_dense_Q():
+    hs = hsde.HSDE(synth.config0())
+    assert np.array_equal(adjoint.sparse_Q(hs).toarray(), dense.build_Q(hs))
+
+
+@pytest.mark.parametrize("case", ["grid", "arrow"])
+def test_unrolled_gradient_matches_central_differences(case):
+    rng = np.random.default_rng(3)
+    if case == "grid":
+        p0 = synth.maxcut_grid(3, 5, np.random.default_rng(1))
+        K = 40
+    else:
+        p0 = synth.block_arrow(3, 3, 2, 5, np.random.default_rng(2), kappa=30.0, assign="roundrobin")
+        K = 30
+    st = hsde.HSDE(p0).V.st
+    p = _C_on_pattern(p0, st)
+    hs = hsde.HSDE(p)
+    f, cbar, bbar = adjoint.gradient(hs, K)
+    assert f == pytest.approx(adjoint.objective(hs, K), rel=1e-12)
+    G = adjoint.grad_C_lower(hs, cbar)
+    w = np.where(st.pat_row == st.pat_col, 1.0, 2.0)
+    for _ in range(4):
+        dC = rng.standard_normal(st.N)
+        db = rng.standard_normal(p.m)
+        h = 1e-6
+        fp = adjoint.objective(hsde.HSDE(_perturbed(p, dC, db, h)), K)
+        fm = adjoint.objective(hsde.HSDE(_perturbed(p, dC, db, -h)), K)
+        fd = (fp - fm) / (2 * h)
+        an = float(np.sum(w * G * dC) + bbar @ db)
+        assert abs(fd - an) <= 1e-5 * (1 + abs(fd)), (fd, an)
