@@ -269,6 +269,34 @@ HSDE_API int  hsde_spd_inverse(double* S, int32_t m, void* cuda_stream);
  * HSDE_ECUDA (no current device, symbol lookup or launch failure). */
 HSDE_API int  hsde_spd_inverse_noalloc(double* S, int32_t m, void* cuda_stream);
 
+/* Replace the data c = C (N pattern values, lower CSC order) and b (m values)
+ * of instance i, keeping the pattern, the constraint matrices and the cached
+ * factor S (which does not depend on c or b); M^{-1} zeta and
+ * 1 + zeta^T M^{-1} zeta (Eq. MatrixInverseResult) are recomputed.  The
+ * iterate is left as it is.  Errors: HSDE_EINVAL (null or non-finite). */
+HSDE_API int  hsde_set_data(hsde_handle* h, int32_t i, const double* c, const double* b);
+
+/* Unrolled differentiation (single-instance handles).  hsde_unrolled_forward
+ * runs exactly K iterations of Eqs. Step1-Step3 from the standard start
+ * u0 = (0,0,0,0,1), nu0 = (0,0,0,0,1), with the stopping rule and the
+ * eigensolver warm start disabled, keeping the iterate every ckpt iterations,
+ * and returns x_K (N), y_K (m), tau_K and kappa_K.
+ * hsde_unrolled_backward then returns the gradient of
+ *     L = sum_e xbar_e x_K,e + ybar^T y_K + taubar tau_K + kappabar kappa_K
+ * with respect to the stored lower values of C (gC, N values; an entry off
+ * the diagonal stands for both (i,j) and (j,i)) and b (gb, m values), through
+ * every iteration: the psd projections by the Daleckii-Krein formula (1/2 at
+ * coinciding zero eigenvalues), the tau step, and the affine step by the
+ * adjoint solve (I+Q)^{-T} = (I-Q)^{-1} with the same cached factor.  Each
+ * checkpoint segment is recomputed once to record its eigendecompositions.
+ * Not in the paper.  Afterwards the handle's iterate is undefined (use
+ * hsde_set_state).  Errors: HSDE_EINVAL (B != 1, K or ckpt < 1),
+ * HSDE_ESTATE (backward without forward), HSDE_ENOMEM, HSDE_ECUDA. */
+HSDE_API int  hsde_unrolled_forward(hsde_handle* h, int32_t K, int32_t ckpt, double* x, double* y,
+                                    double* tau, double* kappa);
+HSDE_API int  hsde_unrolled_backward(hsde_handle* h, const double* xbar, const double* ybar,
+                                     double taubar, double kappabar, double* gC, double* gb);
+
 /* Free all device and host memory of the handle.  NULL-safe. */
 HSDE_API void hsde_destroy(hsde_handle* h);
 

@@ -176,6 +176,29 @@ struct hsde_symbolic {
     Symbolic S;
 };
 
+// Buffers of the reverse sweep through unrolled iterations (allocated on the
+// first hsde_unrolled_forward, outside the iteration hot path).
+struct UnrollWS {
+    void* mem = nullptr;
+    size_t bytes = 0;
+    int K = 0, ckpt = 0, nseg = 0;
+    size_t cp_stride = 0;
+    char* cp = nullptr;
+    int64_t tv_total = 0;
+    void* tape_v = nullptr;
+    double *tape_scal = nullptr, *tape_x = nullptr, *tape_y = nullptr;
+    double *xbar = nullptr, *ybar = nullptr, *adj_scal = nullptr, *wtau = nullptr, *kpart = nullptr;
+    void *sbar = nullptr, *zbar = nullptr, *vbar = nullptr, *aw_s = nullptr, *aw_v = nullptr;
+    double *f2 = nullptr, *q2 = nullptr, *yw2 = nullptr, *xw2 = nullptr, *part2 = nullptr, *eta2 = nullptr;
+    double *otau = nullptr, *ox = nullptr, *oy = nullptr;
+    void *os = nullptr, *ov = nullptr;
+    double *xp_neg = nullptr, *yp_neg = nullptr, *den_neg = nullptr, *ctp_neg = nullptr;
+    double *gc = nullptr, *gb = nullptr;
+    int64_t* tv_off = nullptr;
+    bool neg_ready = false;
+    bool forward_done = false;
+};
+
 struct hsde_handle {
     int32_t B = 0;
     hsde_options opt{};
@@ -209,6 +232,7 @@ struct hsde_handle {
     int64_t launched = 0;      // iterations enqueued since setup
     bool any_dense = false;
     bool need_rhs = true;      // f must be formed before the next iteration (after setup / set_state)
+    UnrollWS uw;
 };
 
 namespace {
@@ -218,8 +242,14 @@ cudaError_t rec(hsde_handle* h, cudaEvent_t ev, cudaStream_t s) {
     return h->capturing ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal) : cudaEventRecord(ev, s);
 }
 
-int enqueue_iteration(hsde_handle* h) {
-    const DevView& V = h->V;
+int enqueue_iteration_v(hsde_handle* h, const DevView& V, int warm, bool events);
+
+int enqueue_iteration(hsde_handle* h) { return enqueue_iteration_v(h, h->V, h->warm, true); }
+
+int enqueue_iteration_v(hsde_handle* h, const DevView& V, int warm, bool events) {
+    const bool prof = h->profile;
+    if (!events) h->profile = false;
+    struct Restore { hsde_handle* h; bool p; ~Restore() { h->profile = p; } } restore{h, prof};
     CK(rec(h, h->ev_it0, h->st));
     launch_fwd(V, h->st);
     if (h->any_dense) launch_solve_dense(V, h->st);
@@ -231,7 +261,7 @@ int enqueue_iteration(hsde_handle* h) {
     for (size_t i = 0; i < nb; ++i) {
         CK(cudaStreamWaitEvent(h->side[i], h->ev_fork, 0));
         CK(rec(h, h->ev_cs[i], h->side[i]));
-        int rc = launch_cone(V, h->buckets[i], h->mixed, h->max_sweeps, h->jtol, h->warm, h->refresh,
+        int rc = launch_cone(V, h->buckets[i], h->mixed, h->max_sweeps, h->jtol, warm, h->refresh,
                              h->side[i]);
         if (rc != HSDE_OK) return fail(rc, "cone launch failed");
         CK(rec(h, h->ev_ce[i], h->side[i]));
@@ -273,6 +303,7 @@ void free_handle(hsde_handle* h) {
     for (auto& e : h->ev_cs) if (e) cudaEventDestroy(e);
     for (auto& e : h->ev_ce) if (e) cudaEventDestroy(e);
     if (h->arena) cudaFree(h->arena);
+    if (h->uw.mem) cudaFree(h->uw.mem);
     if (h->host_inst) cudaFreeHost(h->host_inst);
     if (h->own_stream && h->st) cudaStreamDestroy(h->st);
     delete h;
@@ -604,7 +635,8 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         }
         CK(cudaStreamSynchronize(st));
     }
-    if (cone_prepare(h->mixed) != HSDE_OK) return fail(HSDE_ECUDA, "cudaFuncSetAttribute failed");
+    if (cone_prepare(h->mixed) != HSDE_OK || rev_prepare(h->mixed) != HSDE_OK)
+        return fail(HSDE_ECUDA, "cudaFuncSetAttribute failed");
 
     // ---- capture one iteration into a graph ----
     h->kernels_per_iter = count_kernels(h);
@@ -988,6 +1020,273 @@ int hsde_get_profile(hsde_handle* h, hsde_profile* out) {
     for (int32_t v : sw) { tot += v; mx = std::max(mx, v); }
     out->sweeps_mean = sw.empty() ? 0.0 : (double)tot / (double)sw.size();
     out->sweeps_max = mx;
+    return HSDE_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Allocate (or grow) the reverse-mode workspace for K iterations with a
+// checkpoint every ckpt iterations.
+int ensure_unroll_ws(hsde_handle* h, int K, int ckpt) {
+    UnrollWS& w = h->uw;
+    const DevView& V = h->V;
+    const size_t T = h->mixed ? sizeof(float) : sizeof(double);
+    const int nseg = (K + ckpt - 1) / ckpt;
+    const int64_t N = V.Ntot, P = V.Ptot, M = V.Mtot, B = V.B;
+    // per-clique tape offsets (CP*CP + CP elements each)
+    std::vector<int64_t> tvo;
+    int64_t tv = 0;
+    for (const auto& H : h->prep)
+        for (int32_t k = 0; k < H.S.p(); ++k) {
+            const int cp = cone_bucket_of(H.S.clique_ptr[k + 1] - H.S.clique_ptr[k]);
+            tvo.push_back(tv);
+            tv += (int64_t)cp * cp + cp;
+        }
+    Carver cv;
+    const size_t cp_stride = ((N * 8 + 3 * P * T + M * 8 + sizeof(InstDev) * B) + 255) / 256 * 256;
+    const size_t o_cp = cv.take<char>(cp_stride * (size_t)nseg);
+    const size_t o_tv = cv.take<char>((size_t)tv * T * ckpt), o_ts = cv.take<double>(2 * B * (size_t)ckpt),
+                 o_tx = cv.take<double>(N * (size_t)ckpt), o_ty = cv.take<double>(M * (size_t)ckpt);
+    const size_t o_xb = cv.take<double>(N), o_yb = cv.take<double>(M), o_as = cv.take<double>(2 * B),
+                 o_wt = cv.take<double>(B), o_kp = cv.take<double>(B);
+    const size_t o_sb = cv.take<char>(P * T), o_zb = cv.take<char>(P * T), o_vb = cv.take<char>(P * T),
+                 o_aws = cv.take<char>(P * T), o_awv = cv.take<char>(P * T);
+    const size_t o_f2 = cv.take<double>(N), o_q2 = cv.take<double>(M), o_yw2 = cv.take<double>(M),
+                 o_xw2 = cv.take<double>(N), o_p2 = cv.take<double>(V.ntiles), o_e2 = cv.take<double>(B),
+                 o_ot = cv.take<double>(B), o_ox = cv.take<double>(N), o_oy = cv.take<double>(M);
+    const size_t o_os = cv.take<char>(P * T), o_ov = cv.take<char>(P * T);
+    const size_t o_xpn = cv.take<double>(N), o_ypn = cv.take<double>(M), o_dn = cv.take<double>(B),
+                 o_cn = cv.take<double>(B), o_gc = cv.take<double>(N), o_gb = cv.take<double>(M),
+                 o_tvo = cv.take<int64_t>(tvo.size());
+    const size_t bytes = cv.off + 256;
+    if (bytes > w.bytes) {
+        if (w.mem) CK(cudaFree(w.mem));
+        w.mem = nullptr;
+        w.bytes = 0;
+        CK(cudaMalloc(&w.mem, bytes));
+        w.bytes = bytes;
+        w.neg_ready = false;
+    }
+    char* m = reinterpret_cast<char*>(w.mem);
+    w.K = K; w.ckpt = ckpt; w.nseg = nseg; w.cp_stride = cp_stride; w.tv_total = tv;
+    w.cp = m + o_cp; w.tape_v = m + o_tv; w.tape_scal = (double*)(m + o_ts);
+    w.tape_x = (double*)(m + o_tx); w.tape_y = (double*)(m + o_ty);
+    w.xbar = (double*)(m + o_xb); w.ybar = (double*)(m + o_yb); w.adj_scal = (double*)(m + o_as);
+    w.wtau = (double*)(m + o_wt); w.kpart = (double*)(m + o_kp);
+    w.sbar = m + o_sb; w.zbar = m + o_zb; w.vbar = m + o_vb; w.aw_s = m + o_aws; w.aw_v = m + o_awv;
+    w.f2 = (double*)(m + o_f2); w.q2 = (double*)(m + o_q2); w.yw2 = (double*)(m + o_yw2);
+    w.xw2 = (double*)(m + o_xw2); w.part2 = (double*)(m + o_p2); w.eta2 = (double*)(m + o_e2);
+    w.otau = (double*)(m + o_ot); w.ox = (double*)(m + o_ox); w.oy = (double*)(m + o_oy);
+    w.os = m + o_os; w.ov = m + o_ov;
+    w.xp_neg = (double*)(m + o_xpn); w.yp_neg = (double*)(m + o_ypn);
+    w.den_neg = (double*)(m + o_dn); w.ctp_neg = (double*)(m + o_cn);
+    w.gc = (double*)(m + o_gc); w.gb = (double*)(m + o_gb);
+    w.tv_off = (int64_t*)(m + o_tvo);
+    if (!tvo.empty())
+        CK(cudaMemcpyAsync(w.tv_off, tvo.data(), sizeof(int64_t) * tvo.size(), cudaMemcpyHostToDevice, h->st));
+    return HSDE_OK;
+}
+
+// M^{-1} zeta' for the adjoint solve, zeta' = (c, 0, b, 0) (Q with b negated).
+int ensure_neg_zeta(hsde_handle* h) {
+    UnrollWS& w = h->uw;
+    if (w.neg_ready) return HSDE_OK;
+    ApplyArgs A{};
+    A.wx = h->V.c; A.ws = nullptr; A.wv = nullptr; A.wy = h->V.b; A.wy_sign = 1.0; A.wtau = nullptr; A.sb = -1.0;
+    A.den = nullptr; A.f = w.f2; A.q = w.q2; A.yw = w.yp_neg; A.xw = w.xp_neg; A.part = w.part2;
+    A.den_out = w.den_neg; A.ctp_out = w.ctp_neg;
+    launch_apply(h->V, A, h->mixed, true, h->st);
+    CK(cudaGetLastError());
+    w.neg_ready = true;
+    return HSDE_OK;
+}
+
+// The view used while unrolling: no stopping, no warm start, optional tape.
+DevView unroll_view(const hsde_handle* h) {
+    DevView V = h->V;
+    V.eps = -1.0;
+    V.max_iter = 0x7fffffff;
+    V.vstore = nullptr;
+    V.tv_off = h->uw.tv_off;
+    V.tape_v = nullptr;
+    V.tape_scal = nullptr;
+    return V;
+}
+
+int reset_standard_start(hsde_handle* h) {
+    const DevView& V = h->V;
+    const size_t T = h->mixed ? sizeof(float) : sizeof(double);
+    CK(cudaMemsetAsync(V.x, 0, sizeof(double) * V.Ntot, h->st));
+    CK(cudaMemsetAsync(V.s, 0, T * V.Ptot, h->st));
+    CK(cudaMemsetAsync(V.z, 0, T * V.Ptot, h->st));
+    CK(cudaMemsetAsync(V.v, 0, T * V.Ptot, h->st));
+    if (V.Mtot) CK(cudaMemsetAsync(V.y, 0, sizeof(double) * V.Mtot, h->st));
+    int rc = sync_inst(h);
+    if (rc != HSDE_OK) return rc;
+    for (int32_t b = 0; b < h->B; ++b) {
+        InstDev& I = h->host_inst[b];
+        I.tau = 1.0; I.kappa = 1.0; I.eta = 0.0; I.iter = 0; I.status = HSDE_RUNNING; I.vcold = 1;
+    }
+    CK(cudaMemcpyAsync(V.inst, h->host_inst, sizeof(InstDev) * h->B, cudaMemcpyHostToDevice, h->st));
+    h->need_rhs = true;
+    return HSDE_OK;
+}
+
+int copy_state(hsde_handle* h, char* dst, bool save) {
+    const DevView& V = h->V;
+    const size_t T = h->mixed ? sizeof(float) : sizeof(double);
+    struct Part { void* dev; size_t n; } parts[] = {
+        {V.x, sizeof(double) * V.Ntot}, {V.s, T * V.Ptot}, {V.z, T * V.Ptot}, {V.v, T * V.Ptot},
+        {V.y, sizeof(double) * V.Mtot}, {V.inst, sizeof(InstDev) * V.B}};
+    size_t off = 0;
+    for (auto& p : parts) {
+        if (p.n) {
+            if (save) CK(cudaMemcpyAsync(dst + off, p.dev, p.n, cudaMemcpyDeviceToDevice, h->st));
+            else CK(cudaMemcpyAsync(p.dev, dst + off, p.n, cudaMemcpyDeviceToDevice, h->st));
+        }
+        off += p.n;
+    }
+    return HSDE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hsde_set_data(hsde_handle* h, int32_t i, const double* c, const double* b) {
+    int rc = check_handle(h, i);
+    if (rc != HSDE_OK) return rc;
+    if (!c || (!b && h->prep[i].m > 0)) return fail(HSDE_EINVAL, "null data");
+    CK(cudaSetDevice(h->device));
+    HostPrep& H = h->prep[i];
+    const int64_t N = H.S.N();
+    for (int64_t e = 0; e < N; ++e)
+        if (!std::isfinite(c[e])) return fail(HSDE_EINVAL, "non-finite c");
+    for (int32_t j = 0; j < H.m; ++j)
+        if (!std::isfinite(b[j])) return fail(HSDE_EINVAL, "non-finite b");
+    H.cvec.assign(c, c + N);
+    H.b.assign(b, b + H.m);
+    CK(cudaMemcpyAsync(const_cast<double*>(h->V.c) + h->x_off[i], c, sizeof(double) * N, cudaMemcpyHostToDevice,
+                       h->st));
+    if (H.m)
+        CK(cudaMemcpyAsync(const_cast<double*>(h->V.b) + h->m_off[i], b, sizeof(double) * H.m,
+                           cudaMemcpyHostToDevice, h->st));
+    // S does not depend on (c, b); M^{-1} zeta and 1 + zeta^T M^{-1} zeta do
+    launch_rhs(h->V, h->mixed, Mode::Setup, h->st);
+    launch_spmv_A(h->V, Mode::Setup, h->st);
+    launch_solve(h->V, Mode::Setup, h->st);
+    launch_spmv_At(h->V, Mode::Setup, h->st);
+    launch_setup_den(h->V, h->st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->st));
+    h->uw.neg_ready = false;
+    h->uw.forward_done = false;
+    h->need_rhs = true;
+    return HSDE_OK;
+}
+
+int hsde_unrolled_forward(hsde_handle* h, int32_t K, int32_t ckpt, double* x, double* y, double* tau,
+                          double* kappa) {
+    if (!h) return fail(HSDE_EINVAL, "null handle");
+    if (h->B != 1) return fail(HSDE_EINVAL, "unrolled differentiation needs a single-instance handle");
+    if (K < 1 || ckpt < 1) return fail(HSDE_EINVAL, "K and ckpt must be positive");
+    CK(cudaSetDevice(h->device));
+    int rc;
+    if ((rc = ensure_unroll_ws(h, K, ckpt)) != HSDE_OK) return rc;
+    if ((rc = ensure_neg_zeta(h)) != HSDE_OK) return rc;
+    if ((rc = reset_standard_start(h)) != HSDE_OK) return rc;
+    UnrollWS& w = h->uw;
+    const DevView Vu = unroll_view(h);
+    launch_rhs(Vu, h->mixed, Mode::Iter, h->st);
+    h->need_rhs = false;
+    for (int32_t k = 0; k < K; ++k) {
+        if (k % ckpt == 0 && (rc = copy_state(h, w.cp + (size_t)(k / ckpt) * w.cp_stride, true)) != HSDE_OK)
+            return rc;
+        if ((rc = enqueue_iteration_v(h, Vu, 0, false)) != HSDE_OK) return rc;
+    }
+    if ((rc = sync_inst(h)) != HSDE_OK) return rc;
+    const InstDev& I = h->host_inst[0];
+    if (x) CK(cudaMemcpy(x, h->V.x, sizeof(double) * h->V.Ntot, cudaMemcpyDeviceToHost));
+    if (y && h->V.Mtot) CK(cudaMemcpy(y, h->V.y, sizeof(double) * h->V.Mtot, cudaMemcpyDeviceToHost));
+    if (tau) *tau = I.tau;
+    if (kappa) *kappa = I.kappa;
+    w.forward_done = true;
+    return HSDE_OK;
+}
+
+int hsde_unrolled_backward(hsde_handle* h, const double* xbar, const double* ybar, double taubar, double kappabar,
+                           double* gC, double* gb) {
+    if (!h) return fail(HSDE_EINVAL, "null handle");
+    UnrollWS& w = h->uw;
+    if (!w.forward_done) return fail(HSDE_ESTATE, "hsde_unrolled_forward must run first");
+    CK(cudaSetDevice(h->device));
+    const DevView& V = h->V;
+    const size_t T = h->mixed ? sizeof(float) : sizeof(double);
+    cudaStream_t st = h->st;
+    // seeds
+    if (xbar) CK(cudaMemcpyAsync(w.xbar, xbar, sizeof(double) * V.Ntot, cudaMemcpyHostToDevice, st));
+    else CK(cudaMemsetAsync(w.xbar, 0, sizeof(double) * V.Ntot, st));
+    if (V.Mtot) {
+        if (ybar) CK(cudaMemcpyAsync(w.ybar, ybar, sizeof(double) * V.Mtot, cudaMemcpyHostToDevice, st));
+        else CK(cudaMemsetAsync(w.ybar, 0, sizeof(double) * V.Mtot, st));
+    }
+    const double sc[2] = {taubar, kappabar};
+    CK(cudaMemcpyAsync(w.adj_scal, sc, sizeof(sc), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(w.sbar, 0, T * V.Ptot, st));
+    CK(cudaMemsetAsync(w.zbar, 0, T * V.Ptot, st));
+    CK(cudaMemsetAsync(w.vbar, 0, T * V.Ptot, st));
+    CK(cudaMemsetAsync(w.gc, 0, sizeof(double) * V.Ntot, st));
+    if (V.Mtot) CK(cudaMemsetAsync(w.gb, 0, sizeof(double) * V.Mtot, st));
+    RevArgs R{};
+    R.tv_off = w.tv_off; R.tape_scal = w.tape_scal; R.tape_x = w.tape_x; R.tape_y = w.tape_y;
+    R.xbar = w.xbar; R.ybar = w.ybar; R.sbar = w.sbar; R.zbar = w.zbar; R.vbar = w.vbar;
+    R.adj_scal = w.adj_scal; R.wtau = w.wtau; R.kpart = w.kpart; R.aw_s = w.aw_s; R.aw_v = w.aw_v;
+    R.otau = w.otau; R.ox = w.ox; R.oy = w.oy; R.os = w.os; R.ov = w.ov; R.gc = w.gc; R.gb = w.gb;
+    launch_rev_seed(V, R, st);
+    ApplyArgs A{};
+    A.wx = w.xbar; A.ws = w.aw_s; A.wv = w.aw_v; A.wy = w.ybar; A.wy_sign = -1.0; A.wtau = w.wtau; A.sb = -1.0;
+    A.xp = w.xp_neg; A.yp = w.yp_neg; A.den = w.den_neg; A.ctp = w.ctp_neg;
+    A.f = w.f2; A.q = w.q2; A.yw = w.yw2; A.xw = w.xw2; A.part = w.part2; A.eta = w.eta2;
+    A.ox = w.ox; A.os = w.os; A.ov = w.ov; A.oy = w.oy; A.otau = w.otau;
+    const DevView Vu = unroll_view(h);
+    const size_t tvT = (size_t)w.tv_total * T;
+    int rc;
+    for (int seg = w.nseg - 1; seg >= 0; --seg) {
+        const int k0 = seg * w.ckpt;
+        const int len = std::min(w.ckpt, w.K - k0);
+        if ((rc = copy_state(h, w.cp + (size_t)seg * w.cp_stride, false)) != HSDE_OK) return rc;
+        launch_rhs(Vu, h->mixed, Mode::Iter, st);
+        for (int j = 0; j < len; ++j) {
+            DevView Vt = Vu;
+            Vt.tape_v = reinterpret_cast<char*>(w.tape_v) + (size_t)j * tvT;
+            Vt.tape_scal = w.tape_scal + (size_t)j * 2 * V.B;
+            if ((rc = enqueue_iteration_v(h, Vt, 0, false)) != HSDE_OK) return rc;
+            CK(cudaMemcpyAsync(w.tape_x + (size_t)j * V.Ntot, V.x, sizeof(double) * V.Ntot,
+                               cudaMemcpyDeviceToDevice, st));
+            if (V.Mtot)
+                CK(cudaMemcpyAsync(w.tape_y + (size_t)j * V.Mtot, V.y, sizeof(double) * V.Mtot,
+                                   cudaMemcpyDeviceToDevice, st));
+        }
+        for (int j = len - 1; j >= 0; --j) {
+            R.tape_v = reinterpret_cast<char*>(w.tape_v) + (size_t)j * tvT;
+            launch_rev_scal_pre(R, j, V.B, st);
+            for (const auto& bk : h->buckets) {
+                rc = launch_rev_clique(Vu, R, bk, h->mixed, st);
+                if (rc != HSDE_OK) return fail(rc, "reverse clique launch failed");
+            }
+            launch_apply(Vu, A, h->mixed, false, st);
+            launch_rev_update(Vu, R, j, h->mixed, st);
+            launch_rev_scal_post(R, V.B, st);
+        }
+    }
+    launch_rev_finish(V, R, st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    if (gC) CK(cudaMemcpy(gC, w.gc, sizeof(double) * V.Ntot, cudaMemcpyDeviceToHost));
+    if (gb && V.Mtot) CK(cudaMemcpy(gb, w.gb, sizeof(double) * V.Mtot, cudaMemcpyDeviceToHost));
+    h->need_rhs = true;
     return HSDE_OK;
 }
 

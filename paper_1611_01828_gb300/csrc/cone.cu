@@ -337,6 +337,15 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
             T* t2 = Vc; Vc = Vn; Vn = t2;
         }
     }
+    if (V.tape_v) {
+        // reverse-mode tape: eigenvectors (original index x slot) and raw eigenvalues
+        T* tv = reinterpret_cast<T*>(V.tape_v) + V.tv_off[k];
+        for (int idx = lane; idx < CP * CP; idx += G) {
+            const int i = idx / CP, j = idx - (idx / CP) * CP;
+            tv[idx] = Vc[i * LD + j];
+        }
+        for (int i = lane; i < CP; i += G) tv[CP * CP + i] = A[i * LD + i];
+    }
     for (int i = lane; i < CP; i += G) lam[i] = fmax(A[i * LD + i], T(0));
     if (Vst != nullptr && warm) {
         for (int idx = lane; idx < CP * CP; idx += G) {

@@ -102,12 +102,39 @@ struct DevView {
     int32_t* cl_sweeps;      // [ncl] Jacobi sweeps used by each clique in its last solve
     double* rowb;            // [Mtot] b_i (y_w)_i
     double* af;              // [Mtot] A f of the current iteration
+    // reverse-mode tape of one iteration (null when not recording)
+    void* tape_v;            // per clique: CP x CP eigenvectors, then CP eigenvalues
+    const int64_t* tv_off;   // [ncl] offset of each clique's tape block (elements)
+    double* tape_scal;       // [2B] tau_hat and tau_hat - kappa
     double* atyw;            // [Ntot] A^T y_w of the current iteration
     double* atyp;            // [Ntot] A^T y_p (setup)
     int* counters;           // [2B] completion counters of k_bwd_eta and k_post
     // options
     double eps;
     int32_t max_iter, check_every;
+};
+
+// Arguments of one affine apply u_hat = (I + Q(c, sb*b))^{-1} omega.
+struct ApplyArgs {
+    const double* wx; const void* ws; const void* wv; const double* wy; double wy_sign;
+    const double* wtau;      // [B] omega_tau (null: 0)
+    double sb;               // sign of b in Q
+    const double* xp; const double* yp; const double* den; const double* ctp;   // M^{-1} zeta for sb
+    double* f; double* q; double* yw; double* xw; double* part; double* eta;    // scratch
+    double* ox; void* os; void* ov; double* oy; double* otau;                    // u_hat
+    double* den_out; double* ctp_out;    // setup mode (den == null)
+};
+
+// Reverse-mode buffers.
+struct RevArgs {
+    void* tape_v; const int64_t* tv_off; double* tape_scal; double* tape_x; double* tape_y;
+    double* xbar; double* ybar; void* sbar; void* zbar; void* vbar;
+    double* adj_scal;        // [2B] (tau_bar, kappa_bar)
+    double* wtau;            // [B]
+    double* kpart;           // [B]
+    void* aw_s; void* aw_v;
+    const double* otau; const double* ox; const double* oy; const void* os; const void* ov;
+    double* gc; double* gb;
 };
 
 // Bucket of cliques handled by one eigensolver variant.
@@ -139,6 +166,15 @@ int  cone_smem_bytes(int cmax, bool mixed);
 int  cone_bucket_of(int c);          // padded size of the bucket of a clique of size c, -1 if none
 int  cone_vstore_elems(int c);       // stored basis size for a clique of size c
 int  cone_prepare(bool mixed);
+// reverse mode (unrolled.cu)
+void launch_apply(const DevView& V, const ApplyArgs& A, bool mixed, bool setup_only, void* st);
+int  rev_prepare(bool mixed);
+int  launch_rev_clique(const DevView& V, const RevArgs& R, const Bucket& bk, bool mixed, void* st);
+void launch_rev_scal_pre(const RevArgs& R, int slot, int B, void* st);
+void launch_rev_scal_post(const RevArgs& R, int B, void* st);
+void launch_rev_update(const DevView& V, const RevArgs& R, int slot, bool mixed, void* st);
+void launch_rev_seed(const DevView& V, const RevArgs& R, void* st);
+void launch_rev_finish(const DevView& V, const RevArgs& R, void* st);
 // Gauss-Jordan inversion of the dense S matrices (setup)
 void launch_gj_step(double* pool, const int64_t* offs, const int32_t* ms, const int64_t* tile_pre,
                     int nact, int64_t ntiles, int32_t k, int32_t mmax, double* rowbuf, double* colbuf,

@@ -295,6 +295,10 @@ __global__ void __launch_bounds__(NT) k_bwd_eta(DevView V) {
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        if (V.tape_scal) {
+            V.tape_scal[2 * t.x] = tau_hat;
+            V.tape_scal[2 * t.x + 1] = tau_hat - kappa;
+        }
         I.eta = eta;
         I.tau = tau_new;
         I.kappa = kappa_new;

@@ -87,6 +87,9 @@ _SIGS = {
     "hsde_get_profile": (C.c_int, [C.c_void_p, C.POINTER(hsde_profile)]),
     "hsde_destroy": (None, [C.c_void_p]),
     "hsde_spd_inverse": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "hsde_set_data": (C.c_int, [C.c_void_p, C.c_int32, _f64p, _f64p]),
+    "hsde_unrolled_forward": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, _f64p, _f64p, _f64p, _f64p]),
+    "hsde_unrolled_backward": (C.c_int, [C.c_void_p, _f64p, _f64p, C.c_double, C.c_double, _f64p, _f64p]),
     "hsde_spd_inverse_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
 }
 
@@ -266,6 +269,29 @@ class Handle:
                   for i in range(pr.nphases)}
         return dict(kernels_per_iteration=pr.kernels_per_iteration, phases=phases,
                     sweeps_mean=pr.sweeps_mean, sweeps_max=pr.sweeps_max)
+
+    def hsde_set_data(self, i: int, c: np.ndarray, b: np.ndarray):
+        cc = np.ascontiguousarray(c, np.float64)
+        bb = np.ascontiguousarray(b, np.float64)
+        _ck(lib.hsde_set_data(self.h, i, _ptr(cc, C.c_double), _ptr(bb, C.c_double)), "hsde_set_data")
+
+    def hsde_unrolled_forward(self, K: int, ckpt: int = 20):
+        sz = self.sizes[0]
+        x, y = np.zeros(sz.N), np.zeros(sz.m)
+        tau, kappa = C.c_double(), C.c_double()
+        _ck(lib.hsde_unrolled_forward(self.h, int(K), int(ckpt), _ptr(x, C.c_double), _ptr(y, C.c_double),
+                                      C.byref(tau), C.byref(kappa)), "hsde_unrolled_forward")
+        return x, y, tau.value, kappa.value
+
+    def hsde_unrolled_backward(self, xbar, ybar, taubar: float, kappabar: float):
+        sz = self.sizes[0]
+        xb = np.ascontiguousarray(xbar, np.float64)
+        yb = np.ascontiguousarray(ybar, np.float64)
+        gC, gb = np.zeros(sz.N), np.zeros(sz.m)
+        _ck(lib.hsde_unrolled_backward(self.h, _ptr(xb, C.c_double), _ptr(yb, C.c_double), float(taubar),
+                                       float(kappabar), _ptr(gC, C.c_double), _ptr(gb, C.c_double)),
+            "hsde_unrolled_backward")
+        return gC, gb
 
     # ---- convenience: run to a verdict in chunks ----
     def solve(self, chunk: int = 20):

@@ -1,0 +1,112 @@
+"""GPU: gradient of f(C, b) = c^T x_K / (tau_K + kappa_K) after K unrolled
+ADMM iterations through the library's reverse sweep.
+
+* FP64 against the oracle's reverse mode (itself pinned by central
+  differences): relative 1e-6.
+* The max-cut n = 1000 workload (open 10 x 100 grid), K = 200, checkpoint
+  every 20: central differences of the GPU forward (step 1e-6, FP64) on 20
+  random directions in (C, b): relative 1e-5 of the directional derivative
+  (plus 1e-7 absolute).
+* Mixed precision (FP32 projections) against FP64 on the same instance:
+  relative 2e-2 of the gradient norm.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import adjoint, hsde as ohsde
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1611_01828_gb300 import hsde, unrolled
+    return torch, hsde, unrolled
+
+
+def _on_pattern(p, st):
+    """Give C an explicit (possibly zero) entry on every pattern position."""
+    pos = {(r, c): e for e, (r, c) in enumerate(zip(p.C_row.tolist(), p.C_col.tolist()))}
+    vals = np.zeros(st.N)
+    for e, (r, c) in enumerate(zip(st.pat_row.tolist(), st.pat_col.tolist())):
+        if (r, c) in pos:
+            vals[e] = p.C_val[pos[(r, c)]]
+    q = synth.Problem(**{**p.__dict__})
+    q.C_row, q.C_col, q.C_val = st.pat_row.copy(), st.pat_col.copy(), vals
+    return q
+
+
+def _grad(torch, hsde, unrolled, H, c, b, K, ckpt):
+    ct = torch.tensor(c, dtype=torch.float64, requires_grad=True)
+    bt = torch.tensor(b, dtype=torch.float64, requires_grad=True)
+    f = unrolled.unrolled_objective(ct, bt, H, K, ckpt)
+    f.backward()
+    return float(f), ct.grad.numpy().copy(), bt.grad.numpy().copy()
+
+
+@pytest.mark.parametrize("case", ["grid", "arrow", "cfg0"])
+def test_fp64_gradient_matches_oracle(env, case):
+    torch, hsde, unrolled = env
+    if case == "grid":
+        p0, K = synth.maxcut_grid(3, 5, np.random.default_rng(1)), 40
+    elif case == "arrow":
+        p0, K = synth.block_arrow(3, 3, 2, 5, np.random.default_rng(2), kappa=30.0, assign="roundrobin"), 30
+    else:
+        p0, K = synth.config0(), 25
+    st = ohsde.HSDE(p0).V.st
+    p = _on_pattern(p0, st)
+    ref = ohsde.HSDE(p)
+    f_r, cbar, bbar = adjoint.gradient(ref, K)
+    w = np.where(st.pat_row == st.pat_col, 1.0, 2.0)
+    gC_ref = w * adjoint.grad_C_lower(ref, cbar)
+    with hsde.Handle(p, precision="fp64") as H:
+        f, gC, gb = _grad(torch, hsde, unrolled, H, p.C_val, p.b, K, 7)
+    assert f == pytest.approx(f_r, rel=1e-9)
+    assert np.linalg.norm(gC - gC_ref) <= 1e-6 * np.linalg.norm(gC_ref)
+    assert np.linalg.norm(gb - bbar) <= 1e-6 * max(1e-12, np.linalg.norm(bbar))
+
+
+@pytest.fixture(scope="module")
+def cfg4(env):
+    torch, hsde, unrolled = env
+    p = synth.config4()
+    H = hsde.Handle(p, precision="fp64")
+    c0 = unrolled.pattern_values(H, p.C_row, p.C_col, p.C_val)
+    yield p, H, c0
+    H.close()
+
+
+def test_config4_gradient_central_differences(env, cfg4):
+    torch, hsde, unrolled = env
+    p, H, c0 = cfg4
+    K, ckpt = 200, 20
+    f0, gC, gb = _grad(torch, hsde, unrolled, H, c0, p.b, K, ckpt)
+    w = torch.as_tensor(unrolled.pattern_weights(H))
+    rng = np.random.default_rng(44)
+
+    def fval(c, b):
+        with torch.no_grad():
+            return float(unrolled.unrolled_objective(torch.tensor(c), torch.tensor(b), H, K, ckpt, weights=w))
+
+    h = 1e-6
+    for _ in range(20):
+        dC = rng.standard_normal(c0.shape[0])
+        db = rng.standard_normal(p.m)
+        fd = (fval(c0 + h * dC, p.b + h * db) - fval(c0 - h * dC, p.b - h * db)) / (2 * h)
+        an = float(gC @ dC + gb @ db)
+        assert abs(fd - an) <= 1e-5 * abs(fd) + 1e-7, (fd, an)
+
+
+def test_config4_mixed_gradient_close_to_fp64(env, cfg4):
+    torch, hsde, unrolled = env
+    p, H, c0 = cfg4
+    K, ckpt = 200, 20
+    _, gC64, gb64 = _grad(torch, hsde, unrolled, H, c0, p.b, K, ckpt)
+    with hsde.Handle(p, precision="mixed") as Hm:
+        _, gC32, gb32 = _grad(torch, hsde, unrolled, Hm, c0, p.b, K, ckpt)
+    g64 = np.concatenate([gC64, gb64]); g32 = np.concatenate([gC32, gb32])
+    assert np.linalg.norm(g32 - g64) <= 2e-2 * np.linalg.norm(g64)
