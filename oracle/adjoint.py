@@ -25,7 +25,9 @@ on the embedding of Section 3.2 (Eq. HomogeneousEmbedding):
   product.  At an eigenvalue exactly 0 the projection is not differentiable;
   1/2 is the value a central difference sees (by Moreau, Pi(tM) - Pi(-tM) =
   tM), and exactly-zero eigenvalues do occur in the first iteration from the
-  standard start.  This derivative is not in the paper; it is textbook matrix
+  standard start.  Eigenvalues below 1e-10 of the block's largest one are
+  taken as exactly zero, so that rounding in the eigensolver does not pick
+  the derivative.  This derivative is not in the paper; it is textbook matrix
   analysis.
 * Eq. Step3, nu = nu - u_hat + u: linear.
 
@@ -41,7 +43,12 @@ import scipy.sparse.linalg as spla
 from . import dense, hsde
 
 
+ZERO_REL = 1e-10   # eigenvalues below this fraction of the block's largest are taken as 0
+
+
 def _dk_gamma(lam):
+    scale = np.abs(lam).max() if lam.size else 0.0
+    lam = np.where(np.abs(lam) <= ZERO_REL * scale, 0.0, lam)
     lp = np.maximum(lam, 0.0)
     dl = lam[:, None] - lam[None, :]
     dp = lp[:, None] - lp[None, :]

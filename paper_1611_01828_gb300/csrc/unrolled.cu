@@ -5,7 +5,8 @@
 //   symmetric gradient G,  a_bar = V (Gamma o (V^T G V)) V^T  with
 //   Gamma_ij = (max(l_i,0) - max(l_j,0)) / (l_i - l_j) for l_i != l_j and
 //   1, 1/2, 0 for l_i == l_j > 0, = 0, < 0 (1/2 is what a central difference
-//   sees at an exactly-zero eigenvalue).  V and l come from the forward
+//   sees at an exactly-zero eigenvalue; eigenvalues below 1e-10 (FP64) or
+//   1e-5 (FP32) of the block's largest are taken as zero).  V and l come from the forward
 //   Jacobi solve of the same iteration (the tape).
 // * k_ap_*: u_hat = (I + Q(c, sb*b))^{-1} omega for any omega, by the same
 //   eliminations as the iteration (Sections 4.2-4.3) with the sign of b as a
@@ -238,6 +239,17 @@ k_rev_clique(DevView V, RevArgs R, const int32_t* __restrict__ list, int nlist) 
     }
     for (int i = lane; i < CP; i += G) lam[i] = tv[CP * CP + i];
     rsync<G>(gid);
+    // eigenvalues below a fraction of the block's largest count as exactly 0
+    // (1e-10 in FP64, 1e-5 in FP32), so rounding does not pick the derivative
+    {
+        T mx = 0;
+        for (int i = 0; i < CP; ++i) mx = fmax(mx, fabs(lam[i]));
+        const T thr = mx * (sizeof(T) == 8 ? T(1e-10) : T(1e-5));
+        rsync<G>(gid);
+        for (int i = lane; i < CP; i += G)
+            if (fabs(lam[i]) <= thr) lam[i] = T(0);
+        rsync<G>(gid);
+    }
     for (int idx = lane; idx < c * c; idx += G) {
         const int bcol = idx / c, arow = idx - bcol * c;
         if (arow < bcol) continue;
