@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-instance batched leg")
     ap.add_argument("--batched-steps", type=int, default=30)
     ap.add_argument("--only-batched", action="store_true", help="run only the batched leg (profiling)")
+    ap.add_argument("--batched-instances", type=int, default=0,
+                    help="0: all 256; else the first k instances (smaller profiling case)")
     return ap.parse_args()
 
 
@@ -410,7 +412,8 @@ def batched_leg(args, hsde, torch, dev, stream, timed_steps):
     import synth
     rank = int(os.environ.get("RANK", "0"))
     t0 = time.perf_counter()
-    probs = synth.config3(seed_instance=rank)
+    sel = range(args.batched_instances) if args.batched_instances > 0 else None
+    probs = synth.config3(seed_instance=rank, select=sel)
     gen_s = time.perf_counter() - t0
     B = len(probs)
     big = 1 << 30
@@ -457,7 +460,7 @@ def batched_leg(args, hsde, torch, dev, stream, timed_steps):
     expect = {"feasible": ("solved", "max_iter"), "primal_infeasible": ("primal_infeasible",),
               "dual_infeasible": ("dual_infeasible",)}
     agree = sum(1 for p, nm in zip(probs, names) if nm in expect[p.kind])
-    return {"workload": "batch256_grid_and_block_arrow_n100-1500", "instances": B,
+    return {"workload": f"batch{B}_grid_and_block_arrow_n100-1500", "instances": B,
             "value": value, "unit": "instance-iterations/s", "ms_per_step": ms / K, "steps": K,
             "fp64_plain": {"value": v64, "ms_per_step": ms64 / K64, "steps": K64},
             "mixed_over_fp64": value / v64,
