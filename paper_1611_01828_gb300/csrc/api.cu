@@ -401,7 +401,6 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         ntiles += (I.N + TILE_N - 1) / TILE_N;
         I.tile_end = (int32_t)ntiles;
         I.dense = H.dense ? 1 : 0;
-        I.long_at = 0;   // thread per entry measured faster on the batched workload
         I.sinv_off = sinv;
         if (H.dense) sinv += (int64_t)H.m * H.m;
         I.status = HSDE_RUNNING;

@@ -52,8 +52,6 @@ struct InstDev {
     int32_t status;          // HSDE_RUNNING ...
     int32_t iter;            // iterations done
     int32_t vcold;           // 1: the stored eigenbases are not valid (cold start next)
-    int32_t long_at;         // 1: A^T rows average >= 8 entries (warp per entry)
-    int32_t _pad2;
     // cached by setup
     double den;              // 1 + zeta^T M^{-1} zeta
     double ctp;              // c^T x_p - b^T y_p

@@ -27,6 +27,7 @@
 namespace hsde {
 
 static constexpr int NT = 256;   // threads per CTA for N-space tiles and m rows
+static_assert(TILE_N == NT, "one pattern entry per thread in the N-space kernels");
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -222,33 +223,47 @@ __global__ void __launch_bounds__(NT) k_bwd_eta(DevView V) {
     InstDev& I = V.inst[t.x];
     if (I.status != HSDE_RUNNING) return;
     double part = 0.0;
-    if (!I.long_at) {
-        // short A^T rows: one thread per entry
-        for (int e = t.y + threadIdx.x; e < t.z; e += NT) {
-            double acc = 0.0;
-            const int j1 = V.At_ptr[e + 1];
-            for (int j = V.At_ptr[e]; j < j1; ++j) acc += V.At_val[j] * V.yw[V.At_col[j]];
-            const double xv = V.f[e] + V.inv_delta[e] * acc;
-            V.xw[e] = xv;
-            V.atyw[e] = acc;
-            part += (V.diag[e] ? 1.0 : 2.0) * V.c[e] * xv;
+    // Rows of A^T up to LONG_AT entries: one thread per entry.  Longer rows
+    // (e.g. arrow-corner entries shared by every constraint) are queued and
+    // reduced by the whole CTA with coalesced strides; the owning thread then
+    // adds the entry's c^T x_w term in its usual place (fixed order).
+    constexpr int LONG_AT = 64;
+    __shared__ int long_list[NT];
+    __shared__ int n_long;
+    if (threadIdx.x == 0) n_long = 0;
+    __syncthreads();
+    bool mine_long = false;
+    int my_e = -1;
+    for (int e = t.y + threadIdx.x; e < t.z; e += NT) {
+        const int j0 = V.At_ptr[e], j1 = V.At_ptr[e + 1];
+        if (j1 - j0 > LONG_AT) {
+            long_list[atomicAdd(&n_long, 1)] = e;
+            mine_long = true;
+            my_e = e;
+            continue;
         }
-    } else {
-        // long A^T rows: one warp per entry, coalesced over the row
-        const int lane = threadIdx.x & 31;
-        for (int e = t.y + (threadIdx.x >> 5); e < t.z; e += NT / 32) {
-            double acc = 0.0;
-            const int j1 = V.At_ptr[e + 1];
-            for (int j = V.At_ptr[e] + lane; j < j1; j += 32) acc += V.At_val[j] * V.yw[V.At_col[j]];
-            acc = warp_sum(acc);
-            if (lane == 0) {
-                const double xv = V.f[e] + V.inv_delta[e] * acc;
-                V.xw[e] = xv;
-                V.atyw[e] = acc;
-                part += (V.diag[e] ? 1.0 : 2.0) * V.c[e] * xv;
-            }
+        double acc = 0.0;
+        for (int j = j0; j < j1; ++j) acc += V.At_val[j] * V.yw[V.At_col[j]];
+        const double xv = V.f[e] + V.inv_delta[e] * acc;
+        V.xw[e] = xv;
+        V.atyw[e] = acc;
+        part += (V.diag[e] ? 1.0 : 2.0) * V.c[e] * xv;
+    }
+    __syncthreads();
+    const int nl = n_long;
+    for (int q = 0; q < nl; ++q) {
+        const int e = long_list[q];
+        double acc = 0.0;
+        const int j1 = V.At_ptr[e + 1];
+        for (int j = V.At_ptr[e] + threadIdx.x; j < j1; j += NT) acc += V.At_val[j] * V.yw[V.At_col[j]];
+        acc = block_sum(acc, sh);
+        if (threadIdx.x == 0) {
+            V.xw[e] = V.f[e] + V.inv_delta[e] * acc;
+            V.atyw[e] = acc;
         }
     }
+    __syncthreads();
+    if (mine_long) part += (V.diag[my_e] ? 1.0 : 2.0) * V.c[my_e] * V.xw[my_e];
     part = block_sum(part, sh);
     if (threadIdx.x == 0) V.part[(int64_t)blockIdx.x * KPART + 0] = part;
     if (!last_cta(V.counters + 2 * t.x, I.tile_end - I.tile_begin, &flag)) return;
