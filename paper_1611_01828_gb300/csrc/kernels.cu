@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(NT) k_bwd_eta(DevView V) {
     // (e.g. arrow-corner entries shared by every constraint) are queued and
     // reduced by the whole CTA with coalesced strides; the owning thread then
     // adds the entry's c^T x_w term in its usual place (fixed order).
-    constexpr int LONG_AT = 64;
+    constexpr int LONG_AT = 512;
     __shared__ int long_list[NT];
     __shared__ int n_long;
     if (threadIdx.x == 0) n_long = 0;
