@@ -327,6 +327,33 @@ int upload(void* dst, const std::vector<T>& v, cudaStream_t st) {
     return HSDE_OK;
 }
 
+// A^T tiles of one instance for k_bwd_eta: runs of whole rows (pattern
+// entries) with at most TILE_N rows and AT_TILE_NNZ nonzeros, so that every
+// CTA gets about the same number of nonzeros whatever the row lengths.  Each
+// row of a tile is reduced by a group of lanes, the power of two (1 ... 32)
+// nearest above the tile's mean row length; a row longer than AT_TILE_NNZ is
+// a tile alone, reduced by the whole CTA (lanes = TILE_N).
+void append_at_tiles(const HostPrep& H, int32_t b, int64_t xo, std::vector<int4>& out) {
+    const int64_t N = H.S.N();
+    int64_t e0 = 0, nnz = 0;
+    auto close = [&](int64_t e1) {
+        const int64_t rows = e1 - e0;
+        int lanes = 1;
+        if (rows == 1 && nnz > AT_TILE_NNZ) lanes = TILE_N;
+        else
+            while (lanes < 32 && lanes * rows < nnz) lanes *= 2;
+        out.push_back(make_int4(b, (int)(xo + e0), (int)(xo + e1), lanes));
+        e0 = e1;
+        nnz = 0;
+    };
+    for (int64_t e = 0; e < N; ++e) {
+        const int64_t len = H.At_ptr[e + 1] - H.At_ptr[e];
+        if (e > e0 && (e - e0 >= TILE_N || nnz + len > AT_TILE_NNZ)) close(e);
+        nnz += len;
+    }
+    if (N > e0) close(N);
+}
+
 int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_handle** out) {
     const double t0 = now_ms();
     if (!out) return fail(HSDE_EINVAL, "out is null");
@@ -389,6 +416,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     int64_t Ntot = 0, Ptot = 0, nnzA = 0, Mtot = 0, ncl = 0, ntiles = 0, sinv = 0, scn = 0;
     h->x_off.resize(B); h->p_off.resize(B); h->m_off.resize(B);
     std::vector<InstDev> inst(B);
+    std::vector<int4> hat;   // A^T tiles
     for (int32_t b = 0; b < B; ++b) {
         const HostPrep& H = h->prep[b];
         InstDev& I = inst[b];
@@ -400,6 +428,9 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         I.tile_begin = (int32_t)ntiles;
         ntiles += (I.N + TILE_N - 1) / TILE_N;
         I.tile_end = (int32_t)ntiles;
+        I.at_begin = (int32_t)hat.size();
+        append_at_tiles(H, b, Ntot, hat);
+        I.at_end = (int32_t)hat.size();
         I.dense = H.dense ? 1 : 0;
         I.sinv_off = sinv;
         if (H.dense) sinv += (int64_t)H.m * H.m;
@@ -462,6 +493,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     const size_t o_g = cv.take<int32_t>(Ptot), o_clo = cv.take<int32_t>(ncl), o_cls = cv.take<int32_t>(ncl),
                  o_cli = cv.take<int32_t>(ncl), o_inst = cv.take<InstDev>(B), o_tiles = cv.take<int4>(ntiles),
                  o_part = cv.take<double>(ntiles * KPART), o_clp = cv.take<double>(ncl),
+                 o_att = cv.take<int4>(hat.size()), o_atpart = cv.take<double>(hat.size()),
                  o_clsw = cv.take<int32_t>(ncl),
                  o_blist = cv.take<int32_t>(ncl),
                  o_rowb = cv.take<double>(Mtot), o_cnt = cv.take<int>(2 * (size_t)B),
@@ -480,6 +512,8 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     char* ar = reinterpret_cast<char*>(h->arena);
     DevView& V = h->V;
     V.B = B; V.Ntot = Ntot; V.Ptot = Ptot; V.Mtot = (int32_t)Mtot; V.ntiles = (int32_t)ntiles;
+    V.nat = (int32_t)hat.size();
+    V.at_tiles = (const int4*)(ar + o_att); V.at_part = (double*)(ar + o_atpart);
     V.ncl = (int32_t)ncl;
     V.x = (double*)(ar + o_x); V.c = (const double*)(ar + o_c); V.inv_delta = (const double*)(ar + o_id);
     V.xp = (double*)(ar + o_xp); V.f = (double*)(ar + o_f); V.xw = (double*)(ar + o_xw);
@@ -563,6 +597,8 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         std::vector<InstDev> iv(inst);
         CK(cudaMemcpyAsync(ar + o_inst, iv.data(), sizeof(InstDev) * B, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(ar + o_tiles, htiles.data(), sizeof(int4) * htiles.size(), cudaMemcpyHostToDevice, st));
+        if (!hat.empty())
+            CK(cudaMemcpyAsync(ar + o_att, hat.data(), sizeof(int4) * hat.size(), cudaMemcpyHostToDevice, st));
         CK(cudaStreamSynchronize(st));
     }
     // ---- dense S: upload and invert in place (Gauss-Jordan, SPD) ----

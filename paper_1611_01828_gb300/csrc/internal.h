@@ -48,6 +48,7 @@ struct InstDev {
     int32_t m_off, m;        // constraints
     int32_t cl_begin, cl_end;      // cliques
     int32_t tile_begin, tile_end;  // N-space tiles
+    int32_t at_begin, at_end;      // A^T tiles (nonzero-balanced, k_bwd_eta)
     int32_t dense;           // S stored dense (1) or diagonal (0)
     int32_t status;          // HSDE_RUNNING ...
     int32_t iter;            // iterations done
@@ -68,12 +69,14 @@ struct InstDev {
 constexpr int KPART = 4;
 // Entries per N-space tile (one CTA of 256 threads each).
 constexpr int TILE_N = 256;
+// Nonzeros of A^T per A^T tile (whole rows; a longer row is a tile alone).
+constexpr int AT_TILE_NNZ = 4096;
 
 // Device view of the whole batch (plain pointers into one arena).
 struct DevView {
     int32_t B;
     int64_t Ntot, Ptot;
-    int32_t Mtot, ntiles, ncl;
+    int32_t Mtot, ntiles, ncl, nat;
     // N space
     double* x; const double* c; const double* inv_delta; double* xp;
     double* f; double* xw;
@@ -96,6 +99,8 @@ struct DevView {
     InstDev* inst;
     const int4* tiles;       // (inst, begin, end, 0)
     double* part;            // [ntiles * KPART]
+    const int4* at_tiles;    // (inst, begin, end, lanes per row; NT: whole CTA on one row)
+    double* at_part;         // [nat] c^T x_w partial of each A^T tile
     double* cl_part;         // [ncl]
     int32_t* cl_sweeps;      // [ncl] Jacobi sweeps used by each clique in its last solve
     double* rowb;            // [Mtot] b_i (y_w)_i

@@ -219,58 +219,52 @@ __global__ void __launch_bounds__(NT) k_solve_dense(DevView V) {
 __global__ void __launch_bounds__(NT) k_bwd_eta(DevView V) {
     __shared__ double sh[32];
     __shared__ int flag;
-    const int4 t = V.tiles[blockIdx.x];
+    const int4 t = V.at_tiles[blockIdx.x];   // (inst, first entry, end, lanes per row)
     InstDev& I = V.inst[t.x];
     if (I.status != HSDE_RUNNING) return;
     double part = 0.0;
-    // Rows of A^T up to LONG_AT entries: one thread per entry.  Longer rows
-    // (e.g. arrow-corner entries shared by every constraint) are queued and
-    // reduced by the whole CTA with coalesced strides; the owning thread then
-    // adds the entry's c^T x_w term in its usual place (fixed order).
-    constexpr int LONG_AT = 512;
-    __shared__ int long_list[NT];
-    __shared__ int n_long;
-    if (threadIdx.x == 0) n_long = 0;
-    __syncthreads();
-    bool mine_long = false;
-    int my_e = -1;
-    for (int e = t.y + threadIdx.x; e < t.z; e += NT) {
-        const int j0 = V.At_ptr[e], j1 = V.At_ptr[e + 1];
-        if (j1 - j0 > LONG_AT) {
-            long_list[atomicAdd(&n_long, 1)] = e;
-            mine_long = true;
-            my_e = e;
-            continue;
-        }
-        double acc = 0.0;
-        for (int j = j0; j < j1; ++j) acc += V.At_val[j] * V.yw[V.At_col[j]];
-        const double xv = V.f[e] + V.inv_delta[e] * acc;
-        V.xw[e] = xv;
-        V.atyw[e] = acc;
-        part += (V.diag[e] ? 1.0 : 2.0) * V.c[e] * xv;
-    }
-    __syncthreads();
-    const int nl = n_long;
-    for (int q = 0; q < nl; ++q) {
-        const int e = long_list[q];
+    const int G = t.w;
+    if (G >= NT) {
+        // one long row of A^T: the whole CTA, coalesced strides
+        const int e = t.y;
         double acc = 0.0;
         const int j1 = V.At_ptr[e + 1];
         for (int j = V.At_ptr[e] + threadIdx.x; j < j1; j += NT) acc += V.At_val[j] * V.yw[V.At_col[j]];
         acc = block_sum(acc, sh);
         if (threadIdx.x == 0) {
-            V.xw[e] = V.f[e] + V.inv_delta[e] * acc;
+            const double xv = V.f[e] + V.inv_delta[e] * acc;
+            V.xw[e] = xv;
             V.atyw[e] = acc;
+            part = (V.diag[e] ? 1.0 : 2.0) * V.c[e] * xv;
+        }
+    } else {
+        // groups of G lanes (a power of two <= 32, aligned in the warp), one
+        // row per group at a time; the loop bound is uniform over the CTA so
+        // every lane of a warp reaches each shuffle.
+        const int grp = threadIdx.x / G, lane = threadIdx.x & (G - 1), ngrp = NT / G;
+        for (int base = t.y; base < t.z; base += ngrp) {
+            const int e = base + grp;
+            const bool valid = e < t.z;
+            double acc = 0.0;
+            if (valid) {
+                const int j1 = V.At_ptr[e + 1];
+                for (int j = V.At_ptr[e] + lane; j < j1; j += G) acc += V.At_val[j] * V.yw[V.At_col[j]];
+            }
+            for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (valid && lane == 0) {
+                const double xv = V.f[e] + V.inv_delta[e] * acc;
+                V.xw[e] = xv;
+                V.atyw[e] = acc;
+                part += (V.diag[e] ? 1.0 : 2.0) * V.c[e] * xv;
+            }
         }
     }
-    __syncthreads();
-    if (mine_long) part += (V.diag[my_e] ? 1.0 : 2.0) * V.c[my_e] * V.xw[my_e];
     part = block_sum(part, sh);
-    if (threadIdx.x == 0) V.part[(int64_t)blockIdx.x * KPART + 0] = part;
-    if (!last_cta(V.counters + 2 * t.x, I.tile_end - I.tile_begin, &flag)) return;
+    if (threadIdx.x == 0) V.at_part[blockIdx.x] = part;
+    if (!last_cta(V.counters + 2 * t.x, I.at_end - I.at_begin, &flag)) return;
     // ---- last CTA of this instance ----
     double ctw = 0.0;
-    for (int tt = I.tile_begin + threadIdx.x; tt < I.tile_end; tt += NT)
-        ctw += __ldcg(V.part + (int64_t)tt * KPART);
+    for (int tt = I.at_begin + threadIdx.x; tt < I.at_end; tt += NT) ctw += __ldcg(V.at_part + tt);
     ctw = block_sum(ctw, sh);
     double btw = 0.0;
     for (int i = threadIdx.x; i < I.m; i += NT) btw += __ldcg(V.rowb + I.m_off + i);
@@ -525,7 +519,7 @@ void launch_solve_dense(const DevView& V, void* st) {
     if (V.Mtot > 0) k_solve_dense<<<rows_grid(V.Mtot), NT, 0, S_(st)>>>(V);
 }
 void launch_bwd_eta(const DevView& V, void* st) {
-    if (V.ntiles > 0) k_bwd_eta<<<V.ntiles, NT, 0, S_(st)>>>(V);
+    if (V.nat > 0) k_bwd_eta<<<V.nat, NT, 0, S_(st)>>>(V);
 }
 void launch_post(const DevView& V, bool mixed, void* st) {
     if (V.ntiles == 0) return;
