@@ -19,8 +19,12 @@
 // block J_r^T X J_c is written straight to the slots those indices occupy in
 // the next round (ping-pong buffers), following the circle tournament
 // (slot 0 fixed, the others advance one place), so every index pair meets
-// once per sweep.  V keeps original indices on its rows and slots on its
-// columns, so no permutation has to be tracked: s = V max(diag A, 0) V^T.
+// once per sweep.  Only the lower triangle of A is kept: the blocks with
+// row pair >= column pair are rotated, and each result goes to its lower
+// position in the next round's slots.  V is stored slot-major (row = slot,
+// column = original index), so a rotation mixes two rows and every access
+// is a coalesced 2-vector; no permutation has to be tracked:
+// s = V max(diag A, 0) V^T with V(i, slot) = Vs[slot][i].
 // Warm start: V of the previous iteration (per clique, FP32/FP64 as the
 // clique arrays) seeds the next solve through A <- V^T A V, with a cold start
 // every `refresh` iterations to bound the loss of orthogonality.
@@ -41,14 +45,19 @@ struct ConeCfg {
     static constexpr int G = G_;
     static constexpr int K = CP / 2;
     static constexpr int LD = CP + 2;                 // even row stride: 2-vector loads stay aligned
-    static constexpr int NTH = (G >= 128) ? G : 128;  // threads per CTA
+    static constexpr int NTH = (G > 32) ? G : 128;    // threads per CTA
     static constexpr int GPB = NTH / G;               // groups (cliques) per CTA
-    static constexpr int NBLK = K * K;
+    static constexpr int NBLK = K * (K + 1) / 2;      // lower 2x2 blocks (row pair >= column pair)
     static constexpr int BPL = (NBLK + G - 1) / G;    // 2x2 blocks per thread per round
-    static constexpr int NVP = CP * K;
-    static constexpr int VPL = (NVP + G - 1) / G;     // V pairs per thread per round
-    // per group: A0, A1, V0, V1 (CP x LD), rot (cs,sn) K, tan K, lambda CP, red 32
-    static constexpr size_t t_elems = 4 * CP * LD + 2 * K + K + CP + 32;
+    static constexpr int NVP = K * K;                 // V items: slot pair x column pair
+    static constexpr int VPL = (NVP + G - 1) / G;     // V items per thread per round
+    static_assert(G <= 32 ? (32 % G == 0) : (G % 32 == 0), "group: a power of two <= 32 or whole warps");
+    static_assert(BPL <= 32 && VPL <= 32, "per-thread masks are 32 bits");
+    // per group: A0, A1, V0, V1 (CP x LD), rot (cs,sn) K, tan K, lambda CP, red
+    // (one double per warp of the group, whatever T is: 64 elements)
+    static constexpr size_t t_elems = 4 * CP * LD + 2 * K + K + CP + 64;
+    static_assert((G + 31) / 32 * sizeof(double) <= 64 * sizeof(T), "red holds one double per warp");
+    static_assert((4 * CP * LD + 3 * K + CP) % 2 == 0, "red is 8-byte aligned");
     static constexpr size_t group_bytes = (t_elems * sizeof(T) + 15) / 16 * 16;
     static constexpr size_t smem = GPB * group_bytes;
 };
@@ -142,10 +151,15 @@ __device__ __forceinline__ void rotation(double app, double aqq, double apq, dou
 // Offsets (in elements of one CP x LD buffer) a thread uses in every round.
 // The thread-to-block assignment does not change between rounds, so the
 // tournament map is evaluated once per solve, not once per round.
+template <int LD>
+__device__ __forceinline__ int lower_pos(int r, int c) {
+    return r >= c ? r * LD + c : c * LD + r;
+}
+
 template <typename Cfg>
 struct RoundPlan {
-    int a_src[Cfg::BPL];       // top-left of the 2x2 block (rows 2kr, 2kr+1; cols 2kc, 2kc+1)
-    int a_dst[Cfg::BPL][4];    // (r0,c0) (r0,c1) (r1,c0) (r1,c1) in the next round's slots
+    int a_src[Cfg::BPL];       // top-left of the 2x2 block (rows 2kr, 2kr+1; cols 2kc, 2kc+1), kr >= kc
+    int a_dst[Cfg::BPL][4];    // lower positions of (r0,c0) (r0,c1) (r1,c0) (r1,c1) in the next slots
     int rot_r[Cfg::BPL], rot_c[Cfg::BPL];
     int v_src[Cfg::VPL], v_dst0[Cfg::VPL], v_dst1[Cfg::VPL], v_rot[Cfg::VPL];
     unsigned diag_mask, a_valid, v_valid;
@@ -158,14 +172,16 @@ struct RoundPlan {
             int b = lane + i * G;
             if (b < Cfg::NBLK) a_valid |= 1u << i;
             else b = 0;
-            const int kr = b / K, kc = b - (b / K) * K;
+            int kr = 0;
+            while ((kr + 1) * (kr + 2) / 2 <= b) ++kr;
+            const int kc = b - kr * (kr + 1) / 2;
             const int r0 = sigma<CP>(2 * kr), r1 = sigma<CP>(2 * kr + 1);
             const int c0 = sigma<CP>(2 * kc), c1 = sigma<CP>(2 * kc + 1);
             a_src[i] = (2 * kr) * LD + 2 * kc;
-            a_dst[i][0] = r0 * LD + c0;
-            a_dst[i][1] = r0 * LD + c1;
-            a_dst[i][2] = r1 * LD + c0;
-            a_dst[i][3] = r1 * LD + c1;
+            a_dst[i][0] = lower_pos<LD>(r0, c0);
+            a_dst[i][1] = lower_pos<LD>(r0, c1);
+            a_dst[i][2] = lower_pos<LD>(r1, c0);
+            a_dst[i][3] = lower_pos<LD>(r1, c1);
             rot_r[i] = 2 * kr;
             rot_c[i] = 2 * kc;
             if (kr == kc) diag_mask |= 1u << i;
@@ -175,11 +191,11 @@ struct RoundPlan {
             int b = lane + i * G;
             if (b < Cfg::NVP) v_valid |= 1u << i;
             else b = 0;
-            const int row = b / K, kc = b - (b / K) * K;
-            v_src[i] = row * LD + 2 * kc;
-            v_dst0[i] = row * LD + sigma<CP>(2 * kc);
-            v_dst1[i] = row * LD + sigma<CP>(2 * kc + 1);
-            v_rot[i] = 2 * kc;
+            const int kp = b / K, col = 2 * (b - (b / K) * K);
+            v_src[i] = (2 * kp) * LD + col;
+            v_dst0[i] = sigma<CP>(2 * kp) * LD + col;
+            v_dst1[i] = sigma<CP>(2 * kp + 1) * LD + col;
+            v_rot[i] = 2 * kp;
         }
     }
 };
@@ -190,13 +206,13 @@ __device__ __forceinline__ void jacobi_round(const RoundPlan<Cfg>& pl, const T* 
                                              T* __restrict__ rot, T* __restrict__ tan_, int lane, int gid) {
     constexpr int K = Cfg::K, LD = Cfg::LD, G = Cfg::G;
     using V2 = typename Vec2<T>::type;
-    // rotation of every slot pair (2k, 2k+1)
+    // rotation of every slot pair (2k, 2k+1), from the lower triangle
     if (lane < K) {
         const int k = lane;
-        const V2 top = *reinterpret_cast<const V2*>(A + (2 * k) * LD + 2 * k);
-        const T aqq = A[(2 * k + 1) * LD + 2 * k + 1];
+        const T app = A[(2 * k) * LD + 2 * k];
+        const V2 qrow = *reinterpret_cast<const V2*>(A + (2 * k + 1) * LD + 2 * k);   // (a_qp, a_qq)
         T cs, sn, t;
-        rotation(top.x, aqq, top.y, cs, sn, t);
+        rotation(app, qrow.y, qrow.x, cs, sn, t);
         V2 cssn;
         cssn.x = cs;
         cssn.y = sn;
@@ -210,12 +226,12 @@ __device__ __forceinline__ void jacobi_round(const RoundPlan<Cfg>& pl, const T* 
         const V2 top = *reinterpret_cast<const V2*>(A + pl.a_src[i]);
         const V2 bot = *reinterpret_cast<const V2*>(A + pl.a_src[i] + LD);
         if (pl.diag_mask & (1u << i)) {
+            // top.y lies above the diagonal (not kept); a_pq = bot.x
             const T t = tan_[pl.rot_r[i] >> 1];
-            const T off = (t == T(0)) ? top.y : T(0);
-            An[pl.a_dst[i][0]] = top.x - t * top.y;
-            An[pl.a_dst[i][1]] = off;
-            An[pl.a_dst[i][2]] = off;
-            An[pl.a_dst[i][3]] = bot.y + t * top.y;
+            const T apq = bot.x;
+            An[pl.a_dst[i][0]] = top.x - t * apq;
+            An[pl.a_dst[i][1]] = (t == T(0)) ? apq : T(0);
+            An[pl.a_dst[i][3]] = bot.y + t * apq;
         } else {
             const V2 rr = *reinterpret_cast<const V2*>(rot + pl.rot_r[i]);
             const V2 rc = *reinterpret_cast<const V2*>(rot + pl.rot_c[i]);
@@ -232,10 +248,16 @@ __device__ __forceinline__ void jacobi_round(const RoundPlan<Cfg>& pl, const T* 
 #pragma unroll
     for (int i = 0; i < Cfg::VPL; ++i) {
         if ((Cfg::NVP % G != 0) && !(pl.v_valid & (1u << i))) continue;
-        const V2 vv = *reinterpret_cast<const V2*>(Vc + pl.v_src[i]);
         const V2 rc = *reinterpret_cast<const V2*>(rot + pl.v_rot[i]);
-        Vn[pl.v_dst0[i]] = rc.x * vv.x - rc.y * vv.y;
-        Vn[pl.v_dst1[i]] = rc.y * vv.x + rc.x * vv.y;
+        const V2 v0 = *reinterpret_cast<const V2*>(Vc + pl.v_src[i]);
+        const V2 v1 = *reinterpret_cast<const V2*>(Vc + pl.v_src[i] + LD);
+        V2 n0, n1;
+        n0.x = rc.x * v0.x - rc.y * v1.x;
+        n0.y = rc.x * v0.y - rc.y * v1.y;
+        n1.x = rc.y * v0.x + rc.x * v1.x;
+        n1.y = rc.y * v0.y + rc.x * v1.y;
+        *reinterpret_cast<V2*>(Vn + pl.v_dst0[i]) = n0;
+        *reinterpret_cast<V2*>(Vn + pl.v_dst1[i]) = n1;
     }
     gsync<G>(gid);
 }
@@ -271,7 +293,7 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
     T* Vst = V.vstore ? reinterpret_cast<T*>(V.vstore) + V.vs_off[k] : nullptr;
     const bool use_warm = warm && Vst != nullptr && !I.vcold && refresh > 1 && (I.iter % refresh) != 1;
 
-    // zero A0 (padding included); V0 = I or the stored basis
+    // zero A0 (padding included); V0 = I or the stored basis (both slot-major)
     for (int idx = lane; idx < CP * CP; idx += G) {
         const int i = idx / CP, j = idx - (idx / CP) * CP;
         A0[i * LD + j] = T(0);
@@ -295,23 +317,23 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
     T* Vc = V0;
     T* Vn = V1;
     if (use_warm) {
-        // An = A Vc, then A = Vc^T An  (A symmetric); result kept symmetric
+        // An = V^T A (slot x original; A symmetric, full), then the lower
+        // triangle of A = An V
         for (int idx = lane; idx < CP * CP; idx += G) {
-            const int i = idx / CP, j = idx - (idx / CP) * CP;
+            const int sl = idx / CP, i = idx - (idx / CP) * CP;
             T acc = 0;
 #pragma unroll 8
-            for (int q = 0; q < CP; ++q) acc += A[i * LD + q] * Vc[q * LD + j];
-            An[i * LD + j] = acc;
+            for (int q = 0; q < CP; ++q) acc += Vc[sl * LD + q] * A[q * LD + i];
+            An[sl * LD + i] = acc;
         }
         gsync<G>(gid);
         for (int idx = lane; idx < CP * CP; idx += G) {
-            const int i = idx / CP, j = idx - (idx / CP) * CP;
-            if (i < j) continue;
+            const int tl = idx / CP, sl = idx - (idx / CP) * CP;
+            if (sl < tl) continue;
             T acc = 0;
 #pragma unroll 8
-            for (int q = 0; q < CP; ++q) acc += Vc[q * LD + i] * An[q * LD + j];
-            A[i * LD + j] = acc;
-            A[j * LD + i] = acc;
+            for (int q = 0; q < CP; ++q) acc += An[sl * LD + q] * Vc[tl * LD + q];
+            A[sl * LD + tl] = acc;
         }
         gsync<G>(gid);
     }
@@ -321,15 +343,16 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
     int sweeps_done = 0;
     for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
         sweeps_done = sweep;
-        T offd = 0, tot = 0;
+        T offd = 0, dg = 0;
         for (int idx = lane; idx < CP * CP; idx += G) {
             const int i = idx / CP, j = idx - (idx / CP) * CP;
+            if (i < j) continue;
             const T a = A[i * LD + j];
-            tot += a * a;
-            if (i != j) offd += a * a;
+            if (i == j) dg += a * a;
+            else offd += T(2) * a * a;
         }
         offd = gsum<G>(offd, red, gid);
-        tot = gsum<G>(tot, red, gid);
+        const T tot = gsum<G>(dg, red, gid) + offd;
         if (offd <= tol2 * tot || sweep == max_sweeps) break;
         for (int r = 0; r < CP - 1; ++r) {
             jacobi_round<Cfg>(plan, A, An, Vc, Vn, rot, tan_, lane, gid);
@@ -342,7 +365,7 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
         T* tv = reinterpret_cast<T*>(V.tape_v) + V.tv_off[k];
         for (int idx = lane; idx < CP * CP; idx += G) {
             const int i = idx / CP, j = idx - (idx / CP) * CP;
-            tv[idx] = Vc[i * LD + j];
+            tv[idx] = Vc[j * LD + i];   // (original index i, slot j)
         }
         for (int i = lane; i < CP; i += G) tv[CP * CP + i] = A[i * LD + i];
     }
@@ -361,7 +384,7 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
         if (arow < bcol) continue;
         T acc = 0;
 #pragma unroll 8
-        for (int q = 0; q < CP; ++q) acc += Vc[arow * LD + q] * lam[q] * Vc[bcol * LD + q];
+        for (int q = 0; q < CP; ++q) acc += Vc[q * LD + arow] * lam[q] * Vc[q * LD + bcol];
         const int64_t j = off + (int64_t)bcol * c - (bcol * (bcol - 1)) / 2 + (arow - bcol);
         const int gi = V.gmap[j];
         const double gx = V.xw[gi] - eta * V.xp[gi];
@@ -386,7 +409,7 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
 // buckets: padded size CP and threads per clique G
 // ---------------------------------------------------------------------------
 #define HSDE_CONE_BUCKETS(X) \
-    X(4, 4) X(8, 8) X(12, 16) X(16, 32) X(24, 64) X(32, 128) X(40, 256) X(48, 512) X(64, 512)
+    X(4, 4) X(8, 8) X(12, 16) X(16, 32) X(24, 96) X(32, 160) X(40, 224) X(48, 320) X(64, 544)
 
 template <typename T, int CP, int G>
 static int prepare_one() {
