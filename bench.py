@@ -36,6 +36,18 @@ UNIT = "iterations/s"
 WORKLOAD = "maxcut_grid20x100_n2000_m2000"
 
 
+
+def sweep_stats(phases):
+    """Mean Jacobi sweeps per clique, and per cone bucket the mean (over the
+    timed steps) of the most sweeps any clique of the bucket took."""
+    out = {}
+    sw = phases.get("_sweeps_mean")
+    if sw and sw[2]:
+        out["mean_per_clique"] = round(sw[0] / sw[2], 3)
+    out["bucket_max"] = {k: round(a[3] / a[2], 2) for k, a in phases.items()
+                         if k.startswith("cone_") and a[2]}
+    return out
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -257,9 +269,13 @@ def run_ours(args):
             if profile:
                 pr = H.hsde_get_profile()
                 for k, (ms, units) in pr["phases"].items():
-                    a = phases.setdefault(k, [0.0, units, 0])
+                    a = phases.setdefault(k, [0.0, units, 0, 0])
                     a[0] += ms
                     a[2] += 1
+                    a[3] += pr["phase_sweeps_max"].get(k, 0)
+                sw = phases.setdefault("_sweeps_mean", [0.0, 0, 0, 0])
+                sw[0] += pr["sweeps_mean"]
+                sw[2] += 1
         barrier()
         total_ms = sum(a.elapsed_time(b) for a, b in ev)
         return total_ms, phases
@@ -340,7 +356,7 @@ def run_ours(args):
 
     # roofline of the dominant phase
     peaks = load_peaks()
-    avg = {k: (a[0] / a[2], a[1]) for k, a in phases.items() if k != "iteration" and a[2]}
+    avg = {k: (a[0] / a[2], a[1]) for k, a in phases.items() if k not in ("iteration", "_sweeps_mean") and a[2]}
     dom = max(avg, key=lambda k: avg[k][0])
     dom_ms, dom_units = avg[dom]
     if dom.startswith("cone_"):
@@ -393,6 +409,7 @@ def run_ours(args):
         "time_to_verdict": {"mixed": ttv_mixed, "fp64": ttv_fp64, "eps_tol": 1e-4, "max_iter": 2000},
         "setup_ms": setup_mixed_ms,
         "phase_us": phase_avg,
+        "jacobi_sweeps": sweep_stats(phases),
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": world * Ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": L * 8, "d2h_bytes_per_step": L * 8,
@@ -426,7 +443,7 @@ def batched_leg(args, hsde, torch, dev, stream, timed_steps):
     sizes = list(H.sizes)
     H.close()
     value = B * K / (ms / 1e3)
-    avg = {k: (a[0] / a[2], a[1]) for k, a in phases.items() if k != "iteration" and a[2]}
+    avg = {k: (a[0] / a[2], a[1]) for k, a in phases.items() if k not in ("iteration", "_sweeps_mean") and a[2]}
     dom = max(avg, key=lambda k: avg[k][0])
     dom_ms, dom_units = avg[dom]
     peaks = load_peaks() or {}
@@ -466,6 +483,7 @@ def batched_leg(args, hsde, torch, dev, stream, timed_steps):
             "mixed_over_fp64": value / v64,
             "setup_s": setup_s, "generate_s": gen_s, "kernels_per_iteration": kern,
             "phase_us": {k: round(v[0] * 1e3, 1) for k, v in avg.items()},
+            "jacobi_sweeps": sweep_stats(phases),
             "roofline": roof,
             "time_to_all_verdicts_s": ttv, "max_iterations": max(iters),
             "verdicts": {k: names.count(k) for k in sorted(set(names))},

@@ -144,6 +144,10 @@ typedef struct hsde_profile {
     double  sweeps_mean;  /* Jacobi sweeps per clique in the last iteration      */
     int32_t sweeps_max;
     int32_t _pad;
+    int32_t phase_sweeps_max[HSDE_MAX_PHASES];  /* cone phases: most sweeps any
+                                                   clique of the bucket took
+                                                   (it sets the phase's time); 0
+                                                   for the other phases       */
 } hsde_profile;
 
 typedef struct hsde_handle hsde_handle;

@@ -228,6 +228,7 @@ struct hsde_handle {
     cudaEvent_t ev_it0 = nullptr, ev_aff = nullptr, ev_chk = nullptr, ev_it1 = nullptr;
     cudaEvent_t ev_cs[10] = {}, ev_ce[10] = {};
     std::vector<int64_t> bucket_c3;
+    std::vector<std::vector<int32_t>> bucket_ids;   // host copy of each bucket's clique list
     int kernels_per_iter = 0;
     int64_t launched = 0;      // iterations enqueued since setup
     bool any_dense = false;
@@ -255,10 +256,17 @@ int enqueue_iteration_v(hsde_handle* h, const DevView& V, int warm, bool events)
     if (h->any_dense) launch_solve_dense(V, h->st);
     launch_bwd_eta(V, h->st);
     CK(rec(h, h->ev_aff, h->st));
-    // fork: every clique bucket on its own branch
+    // fork: every clique bucket on its own branch; buckets whose CTAs each
+    // take a whole SM go first, largest cliques first (their CTAs are placed
+    // while SMs are still empty), then the others, smallest first
     CK(cudaEventRecord(h->ev_fork, h->st));
     const size_t nb = h->buckets.size();
-    for (size_t i = 0; i < nb; ++i) {
+    std::vector<size_t> order;
+    for (size_t i = nb; i-- > 0;)
+        if (cone_bucket_alone(h->buckets[i], h->mixed)) order.push_back(i);
+    for (size_t i = 0; i < nb; ++i)
+        if (!cone_bucket_alone(h->buckets[i], h->mixed)) order.push_back(i);
+    for (size_t i : order) {
         CK(cudaStreamWaitEvent(h->side[i], h->ev_fork, 0));
         CK(rec(h, h->ev_cs[i], h->side[i]));
         int rc = launch_cone(V, h->buckets[i], h->mixed, h->max_sweeps, h->jtol, warm, h->refresh,
@@ -666,6 +674,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
                                cudaMemcpyHostToDevice, st));
             h->buckets.push_back(Bucket{caps[t], (int32_t)lists[t].size(), dl + used});
             h->bucket_c3.push_back(c3[t]);
+            h->bucket_ids.push_back(lists[t]);
             used += lists[t].size();
         }
         CK(cudaStreamSynchronize(st));
@@ -1055,6 +1064,12 @@ int hsde_get_profile(hsde_handle* h, hsde_profile* out) {
     for (int32_t v : sw) { tot += v; mx = std::max(mx, v); }
     out->sweeps_mean = sw.empty() ? 0.0 : (double)tot / (double)sw.size();
     out->sweeps_max = mx;
+    // cone phases follow "affine" in bucket order
+    for (size_t i = 0; i < h->buckets.size() && 1 + i < (size_t)HSDE_MAX_PHASES; ++i) {
+        int32_t bm = 0;
+        for (int32_t k : h->bucket_ids[i]) bm = std::max(bm, sw[k]);
+        out->phase_sweeps_max[1 + i] = bm;
+    }
     return HSDE_OK;
 }
 

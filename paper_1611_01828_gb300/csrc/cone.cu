@@ -33,6 +33,7 @@
 // (sub-warp shuffles for G < 32, named barriers for G > 32).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "internal.h"
@@ -54,8 +55,9 @@ struct ConeCfg {
     static_assert(G <= 32 ? (32 % G == 0) : (G % 32 == 0), "group: a power of two <= 32 or whole warps");
     static_assert(BPL <= 32 && VPL <= 32, "per-thread masks are 32 bits");
     // per group: A0, A1, V0, V1 (CP x LD), rot (cs,sn) K, tan K, lambda CP, red
-    // (one double per warp of the group, whatever T is: 64 elements)
-    static constexpr size_t t_elems = 4 * CP * LD + 2 * K + K + CP + 64;
+    // (one double per warp of the group, whatever T is: 64 elements), and
+    // the list of slots with a positive eigenvalue (CP + 1 ints)
+    static constexpr size_t t_elems = 4 * CP * LD + 2 * K + K + CP + 64 + (CP + 2);   // + positive-slot list
     static_assert((G + 31) / 32 * sizeof(double) <= 64 * sizeof(T), "red holds one double per warp");
     static_assert((4 * CP * LD + 3 * K + CP) % 2 == 0, "red is 8-byte aligned");
     static constexpr size_t group_bytes = (t_elems * sizeof(T) + 15) / 16 * 16;
@@ -262,11 +264,28 @@ __device__ __forceinline__ void jacobi_round(const RoundPlan<Cfg>& pl, const T* 
     gsync<G>(gid);
 }
 
+// Column of entry e in a packed lower column-major c x c block (column b
+// starts at b c - b (b - 1) / 2).
+__device__ __forceinline__ int packed_column(int e, int c) {
+    const float cc = 2.f * c + 1.f;
+    int b = (int)((cc - sqrtf(fmaxf(cc * cc - 8.f * e, 0.f))) * 0.5f);
+    b = max(0, min(b, c - 1));
+    while (b > 0 && b * c - b * (b - 1) / 2 > e) --b;
+    while (b + 1 < c && (b + 1) * c - (b + 1) * b / 2 <= e) ++b;
+    return b;
+}
+
 template <typename T, int CP, int G>
-__global__ void __launch_bounds__(ConeCfg<T, CP, G>::NTH)
+__global__ void __launch_bounds__(ConeCfg<T, CP, G>::NTH, ConeCfg<T, CP, G>::GPB > 1 ? 8 : 1)
 k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T tol2, int warm, int refresh) {
     using Cfg = ConeCfg<T, CP, G>;
-    constexpr int LD = Cfg::LD;
+    using V2 = typename Vec2<T>::type;
+    constexpr int LD = Cfg::LD, K = Cfg::K;
+    constexpr int EPT = (CP * (CP + 1) / 2 + G - 1) / G;   // lower entries per thread
+    // One clique per CTA: the gathered values stay in registers until the
+    // rebuild.  Groups of <= 32 lanes (many cliques per CTA) re-read them
+    // instead, keeping registers, and so resident CTAs, as they were.
+    constexpr bool STASH = G > 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int gid = threadIdx.x / G, lane = threadIdx.x % G;
     const int li = blockIdx.x * Cfg::GPB + gid;
@@ -280,14 +299,16 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
     T* V0 = A1 + CP * LD;
     T* V1 = V0 + CP * LD;
     T* rot = V1 + CP * LD;
-    T* tan_ = rot + 2 * Cfg::K;
-    T* lam = tan_ + Cfg::K;
+    T* tan_ = rot + 2 * K;
+    T* lam = tan_ + K;
     T* red = lam + CP;
+    int* pos = reinterpret_cast<int*>(red + 64);   // positive eigenvalues (slots), count at [CP]
 
     T* s = reinterpret_cast<T*>(V.s);
     T* z = reinterpret_cast<T*>(V.z);
     T* v = reinterpret_cast<T*>(V.v);
     const int c = V.cl_size[k];
+    const int nlow = c * (c + 1) / 2;
     const int64_t off = V.cl_off[k];
     const double eta = I.eta;
     T* Vst = V.vstore ? reinterpret_cast<T*>(V.vstore) + V.vs_off[k] : nullptr;
@@ -299,47 +320,110 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
         A0[i * LD + j] = T(0);
         V0[i * LD + j] = use_warm ? Vst[idx] : ((i == j) ? T(1) : T(0));
     }
-    gsync<G>(gid);
-    // gather + rank-one correction: a = s_hat - z  (lower entries, mirrored)
-    for (int idx = lane; idx < c * c; idx += G) {
-        const int bcol = idx / c, arow = idx - bcol * c;
-        if (arow < bcol) continue;
-        const int64_t j = off + (int64_t)bcol * c - (bcol * (bcol - 1)) / 2 + (arow - bcol);
-        const int gi = V.gmap[j];
-        const double gx = V.xw[gi] - eta * V.xp[gi];
-        const double av = 0.5 * ((double)s[j] - (double)z[j] - (double)v[j] + gx);
-        A0[arow * LD + bcol] = (T)av;
-        A0[bcol * LD + arow] = (T)av;
+    // Gather + rank-one correction, a = s_hat - z, over the lower entries
+    // (packed order e = j - off).  With STASH each thread keeps its entries'
+    // a, H_k xh and v_hat in registers until the rebuild writes s, z, v.
+    int apos[STASH ? EPT : 1];   // arow * LD + bcol; -1: no entry
+    unsigned diag_bits = 0u;
+    double avs[STASH ? EPT : 1], gxs[STASH ? EPT : 1];
+    T vns[STASH ? EPT : 1];
+    if constexpr (STASH) {
+        int gi[EPT];
+        T so[EPT], zo[EPT], vo[EPT];
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            const int e = lane + q * G;
+            apos[q] = -1;
+            if (e < nlow) {
+                const int b = packed_column(e, c);
+                const int arow = b + (e - (b * c - b * (b - 1) / 2));
+                apos[q] = arow * LD + b;
+                if (arow == b) diag_bits |= 1u << q;
+                gi[q] = V.gmap[off + e];
+                so[q] = s[off + e];
+                zo[q] = z[off + e];
+                vo[q] = v[off + e];
+            }
+        }
+        gsync<G>(gid);   // A0 zeroed
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            if (apos[q] < 0) continue;
+            const double gx = V.xw[gi[q]] - eta * V.xp[gi[q]];
+            const double so_ = so[q], zo_ = zo[q], vo_ = vo[q];
+            const double av = 0.5 * (so_ - zo_ - vo_ + gx);
+            gxs[q] = gx;
+            avs[q] = av;
+            vns[q] = (T)(0.5 * (so_ + zo_ + vo_ - gx));
+            const int arow = apos[q] / LD, b = apos[q] - (apos[q] / LD) * LD;
+            A0[apos[q]] = (T)av;
+            A0[b * LD + arow] = (T)av;
+        }
+    } else {
+        gsync<G>(gid);   // A0 zeroed
+        for (int e = lane; e < nlow; e += G) {
+            const int b = packed_column(e, c);
+            const int arow = b + (e - (b * c - b * (b - 1) / 2));
+            const int gi = V.gmap[off + e];
+            const double gx = V.xw[gi] - eta * V.xp[gi];
+            const double av = 0.5 * ((double)s[off + e] - (double)z[off + e] - (double)v[off + e] + gx);
+            A0[arow * LD + b] = (T)av;
+            A0[b * LD + arow] = (T)av;
+        }
     }
     gsync<G>(gid);
     T* A = A0;
     T* An = A1;
     T* Vc = V0;
     T* Vn = V1;
+    RoundPlan<Cfg> plan;
+    plan.build(lane);
+    const int cq = (c + 1) & ~1;   // A and its products vanish beyond c
     if (use_warm) {
-        // An = V^T A (slot x original; A symmetric, full), then the lower
-        // triangle of A = An V
-        for (int idx = lane; idx < CP * CP; idx += G) {
-            const int sl = idx / CP, i = idx - (idx / CP) * CP;
-            T acc = 0;
-#pragma unroll 8
-            for (int q = 0; q < CP; ++q) acc += Vc[sl * LD + q] * A[q * LD + i];
-            An[sl * LD + i] = acc;
+        // An = V^T A (slot x original; A symmetric and full), 2 x 2 tiles
+        for (int tix = lane; tix < K * K; tix += G) {
+            const int ts = tix / K, ti = tix - (tix / K) * K;
+            T a00 = 0, a01 = 0, a10 = 0, a11 = 0;
+            for (int q = 0; q < cq; q += 2) {
+                const V2 v0 = *reinterpret_cast<const V2*>(Vc + (2 * ts) * LD + q);
+                const V2 v1 = *reinterpret_cast<const V2*>(Vc + (2 * ts + 1) * LD + q);
+                const V2 x0 = *reinterpret_cast<const V2*>(A + (2 * ti) * LD + q);
+                const V2 x1 = *reinterpret_cast<const V2*>(A + (2 * ti + 1) * LD + q);
+                a00 += v0.x * x0.x + v0.y * x0.y;
+                a01 += v0.x * x1.x + v0.y * x1.y;
+                a10 += v1.x * x0.x + v1.y * x0.y;
+                a11 += v1.x * x1.x + v1.y * x1.y;
+            }
+            V2 r0, r1;
+            r0.x = a00; r0.y = a01; r1.x = a10; r1.y = a11;
+            *reinterpret_cast<V2*>(An + (2 * ts) * LD + 2 * ti) = r0;
+            *reinterpret_cast<V2*>(An + (2 * ts + 1) * LD + 2 * ti) = r1;
         }
         gsync<G>(gid);
-        for (int idx = lane; idx < CP * CP; idx += G) {
-            const int tl = idx / CP, sl = idx - (idx / CP) * CP;
-            if (sl < tl) continue;
-            T acc = 0;
-#pragma unroll 8
-            for (int q = 0; q < CP; ++q) acc += An[sl * LD + q] * Vc[tl * LD + q];
-            A[sl * LD + tl] = acc;
+        // lower triangle of A = An V, 2 x 2 tiles (the round plan's blocks)
+#pragma unroll
+        for (int i = 0; i < Cfg::BPL; ++i) {
+            if ((Cfg::NBLK % G != 0) && !(plan.a_valid & (1u << i))) continue;
+            const int r = plan.rot_r[i], cl = plan.rot_c[i];
+            T a00 = 0, a01 = 0, a10 = 0, a11 = 0;
+            for (int q = 0; q < cq; q += 2) {
+                const V2 x0 = *reinterpret_cast<const V2*>(An + r * LD + q);
+                const V2 x1 = *reinterpret_cast<const V2*>(An + (r + 1) * LD + q);
+                const V2 v0 = *reinterpret_cast<const V2*>(Vc + cl * LD + q);
+                const V2 v1 = *reinterpret_cast<const V2*>(Vc + (cl + 1) * LD + q);
+                a00 += x0.x * v0.x + x0.y * v0.y;
+                a01 += x0.x * v1.x + x0.y * v1.y;
+                a10 += x1.x * v0.x + x1.y * v0.y;
+                a11 += x1.x * v1.x + x1.y * v1.y;
+            }
+            A[r * LD + cl] = a00;
+            A[(r + 1) * LD + cl] = a10;
+            A[(r + 1) * LD + cl + 1] = a11;
+            if (r != cl) A[r * LD + cl + 1] = a01;
         }
         gsync<G>(gid);
     }
 
-    RoundPlan<Cfg> plan;
-    plan.build(lane);
     int sweeps_done = 0;
     for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
         sweeps_done = sweep;
@@ -376,27 +460,90 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
             Vst[idx] = Vc[i * LD + j];
         }
     }
+    // slots with a positive eigenvalue, in slot order (one warp, or the group)
+    if constexpr (G >= 32) {
+        if (lane < 32) {
+            int base = 0;
+            for (int c0 = 0; c0 < CP; c0 += 32) {
+                const int i = c0 + lane;
+                const bool pp = i < CP && A[i * LD + i] > T(0);
+                const unsigned m = __ballot_sync(0xffffffffu, pp);
+                if (pp) pos[base + __popc(m & ((1u << lane) - 1u))] = i;
+                base += __popc(m);
+            }
+            if (lane == 0) pos[CP] = base;
+        }
+    } else {
+        const unsigned gm = gmask<G>();
+        const int sh = (threadIdx.x & 31) & ~(G - 1);
+        int base = 0;
+        for (int c0 = 0; c0 < CP; c0 += G) {
+            const int i = c0 + lane;
+            const bool pp = i < CP && A[i * LD + i] > T(0);
+            const unsigned m = (__ballot_sync(gm, pp) & gm) >> sh;
+            if (pp) pos[base + __popc(m & ((1u << lane) - 1u))] = i;
+            base += __popc(m);
+        }
+        if (lane == 0) pos[CP] = base;
+    }
+    gsync<G>(gid);
+
+    // s = V max(Lambda, 0) V^T on the lower triangle (2 x 2 tiles, positive
+    // eigenvalues only), into the free buffer An
+    const int npos = pos[CP];
+#pragma unroll
+    for (int i = 0; i < Cfg::BPL; ++i) {
+        if ((Cfg::NBLK % G != 0) && !(plan.a_valid & (1u << i))) continue;
+        const int r = plan.rot_r[i], cl = plan.rot_c[i];
+        if (cl >= c) continue;
+        T a00 = 0, a01 = 0, a10 = 0, a11 = 0;
+        for (int t = 0; t < npos; ++t) {
+            const int q = pos[t];
+            const T w = lam[q];
+            const V2 x = *reinterpret_cast<const V2*>(Vc + q * LD + r);
+            const V2 y = *reinterpret_cast<const V2*>(Vc + q * LD + cl);
+            const T wx0 = w * x.x, wx1 = w * x.y;
+            a00 += wx0 * y.x;
+            a01 += wx0 * y.y;
+            a10 += wx1 * y.x;
+            a11 += wx1 * y.y;
+        }
+        An[r * LD + cl] = a00;
+        An[(r + 1) * LD + cl] = a10;
+        An[(r + 1) * LD + cl + 1] = a11;
+        if (r != cl) An[r * LD + cl + 1] = a01;
+    }
     gsync<G>(gid);
 
     double res = 0.0;
-    for (int idx = lane; idx < c * c; idx += G) {
-        const int bcol = idx / c, arow = idx - bcol * c;
-        if (arow < bcol) continue;
-        T acc = 0;
-#pragma unroll 8
-        for (int q = 0; q < CP; ++q) acc += Vc[q * LD + arow] * lam[q] * Vc[q * LD + bcol];
-        const int64_t j = off + (int64_t)bcol * c - (bcol * (bcol - 1)) / 2 + (arow - bcol);
-        const int gi = V.gmap[j];
-        const double gx = V.xw[gi] - eta * V.xp[gi];
-        const double so = s[j], zo = z[j], vo = v[j];
-        const double av = 0.5 * (so - zo - vo + gx);
-        const double vn = 0.5 * (so + zo + vo - gx);
-        const double sn = (double)acc;
-        s[j] = (T)sn;
-        z[j] = (T)(sn - av);
-        v[j] = (T)vn;
-        const double d = gx - sn;
-        res += (arow == bcol ? 1.0 : 2.0) * d * d;
+    if constexpr (STASH) {
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            if (apos[q] < 0) continue;
+            const int64_t j = off + lane + q * G;
+            const double sn = (double)An[apos[q]];
+            s[j] = (T)sn;
+            z[j] = (T)(sn - avs[q]);
+            v[j] = vns[q];
+            const double d = gxs[q] - sn;
+            res += ((diag_bits >> q) & 1u ? 1.0 : 2.0) * d * d;
+        }
+    } else {
+        for (int e = lane; e < nlow; e += G) {
+            const int b = packed_column(e, c);
+            const int arow = b + (e - (b * c - b * (b - 1) / 2));
+            const int64_t j = off + e;
+            const double sn = (double)An[arow * LD + b];
+            const int gi = V.gmap[j];
+            const double gx = V.xw[gi] - eta * V.xp[gi];
+            const double so_ = s[j], zo_ = z[j], vo_ = v[j];
+            const double av = 0.5 * (so_ - zo_ - vo_ + gx);
+            s[j] = (T)sn;
+            z[j] = (T)(sn - av);
+            v[j] = (T)(0.5 * (so_ + zo_ + vo_ - gx));
+            const double d = gx - sn;
+            res += (arow == b ? 1.0 : 2.0) * d * d;
+        }
     }
     res = gsum<G>(res, reinterpret_cast<double*>(red), gid);
     if (lane == 0) {
@@ -411,15 +558,31 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
 #define HSDE_CONE_BUCKETS(X) \
     X(4, 4) X(8, 8) X(12, 16) X(16, 32) X(24, 96) X(32, 160) X(40, 224) X(48, 320) X(64, 544)
 
+// Device limits read by cone_prepare: opt-in shared memory per CTA, SMs.
+static int g_smem_optin = 0;
+static int g_num_sms = 0;
+
 template <typename T, int CP, int G>
 static int prepare_one() {
     using Cfg = ConeCfg<T, CP, G>;
-    if (Cfg::smem > 48 * 1024) {
-        if (cudaFuncSetAttribute(k_cone<T, CP, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)Cfg::smem) != cudaSuccess)
+    // one clique per CTA: allowed the whole opt-in shared memory, which a
+    // launch asks for when the bucket has few cliques (a CTA alone on its SM)
+    const int want = Cfg::GPB == 1 ? std::max<int>(g_smem_optin, (int)Cfg::smem) : (int)Cfg::smem;
+    if (want > 48 * 1024) {
+        if (cudaFuncSetAttribute(k_cone<T, CP, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, want) != cudaSuccess)
             return HSDE_ECUDA;
     }
     return HSDE_OK;
+}
+
+// A bucket of few large cliques sets the latency of the whole cone phase:
+// each of its CTAs takes a whole SM (no small-clique CTA shares its
+// shared-memory bandwidth or issue slots).
+template <typename T, int CP, int G>
+static bool alone_one(const Bucket& bk) {
+    using Cfg = ConeCfg<T, CP, G>;
+    const int grid = (bk.count + Cfg::GPB - 1) / Cfg::GPB;
+    return Cfg::GPB == 1 && CP >= 32 && 3 * grid <= g_num_sms && g_smem_optin >= (int)Cfg::smem;
 }
 
 template <typename T, int CP, int G>
@@ -427,8 +590,8 @@ static void launch_one(const DevView& V, const Bucket& bk, int max_sweeps, doubl
                        cudaStream_t st) {
     using Cfg = ConeCfg<T, CP, G>;
     const int grid = (bk.count + Cfg::GPB - 1) / Cfg::GPB;
-    k_cone<T, CP, G><<<grid, Cfg::NTH, Cfg::smem, st>>>(V, bk.list, bk.count, max_sweeps, (T)(tol * tol), warm,
-                                                        refresh);
+    const size_t smem = alone_one<T, CP, G>(bk) ? (size_t)g_smem_optin : Cfg::smem;
+    k_cone<T, CP, G><<<grid, Cfg::NTH, smem, st>>>(V, bk.list, bk.count, max_sweeps, (T)(tol * tol), warm, refresh);
 }
 
 int cone_bucket_of(int c) {
@@ -444,6 +607,11 @@ int cone_vstore_elems(int c) {
 }
 
 int cone_prepare(bool mixed) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return HSDE_ECUDA;
     int rc = HSDE_OK;
 #define X(cp, g) rc |= mixed ? prepare_one<float, cp, g>() : prepare_one<double, cp, g>();
     HSDE_CONE_BUCKETS(X)
@@ -457,6 +625,14 @@ int cone_smem_bytes(int cmax, bool mixed) {
     HSDE_CONE_BUCKETS(X)
 #undef X
     return -1;
+}
+
+bool cone_bucket_alone(const Bucket& bk, bool mixed) {
+#define X(cp, g) \
+    if (bk.cmax == cp) return mixed ? alone_one<float, cp, g>(bk) : alone_one<double, cp, g>(bk);
+    HSDE_CONE_BUCKETS(X)
+#undef X
+    return false;
 }
 
 int launch_cone(const DevView& V, const Bucket& bk, bool mixed, int max_sweeps, double tol, int warm, int refresh,

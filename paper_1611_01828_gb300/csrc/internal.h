@@ -168,6 +168,7 @@ int  launch_cone(const DevView& V, const Bucket& bk, bool mixed, int max_sweeps,
 int  cone_smem_bytes(int cmax, bool mixed);
 int  cone_bucket_of(int c);          // padded size of the bucket of a clique of size c, -1 if none
 int  cone_vstore_elems(int c);       // stored basis size for a clique of size c
+bool cone_bucket_alone(const Bucket& bk, bool mixed);   // its CTAs each take a whole SM (launched first)
 int  cone_prepare(bool mixed);
 // reverse mode (unrolled.cu)
 void launch_apply(const DevView& V, const ApplyArgs& A, bool mixed, bool setup_only, void* st);

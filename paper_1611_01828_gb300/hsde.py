@@ -60,7 +60,8 @@ class hsde_profile(C.Structure):
     _fields_ = [("kernels_per_iteration", C.c_int32), ("nphases", C.c_int32),
                 ("phase_ms", C.c_double * MAX_PHASES), ("phase_name", (C.c_char * 24) * MAX_PHASES),
                 ("phase_units", C.c_int64 * MAX_PHASES), ("sweeps_mean", C.c_double),
-                ("sweeps_max", C.c_int32), ("_pad", C.c_int32)]
+                ("sweeps_max", C.c_int32), ("_pad", C.c_int32),
+                ("phase_sweeps_max", C.c_int32 * MAX_PHASES)]
 
 
 # Every function declared in include/hsde.h: name -> (restype, argtypes)
@@ -267,8 +268,10 @@ class Handle:
         _ck(lib.hsde_get_profile(self.h, C.byref(pr)), "hsde_get_profile")
         phases = {pr.phase_name[i].value.decode(): (pr.phase_ms[i], int(pr.phase_units[i]))
                   for i in range(pr.nphases)}
+        phase_sweeps = {pr.phase_name[i].value.decode(): int(pr.phase_sweeps_max[i])
+                        for i in range(pr.nphases) if pr.phase_name[i].value.startswith(b"cone_")}
         return dict(kernels_per_iteration=pr.kernels_per_iteration, phases=phases,
-                    sweeps_mean=pr.sweeps_mean, sweeps_max=pr.sweeps_max)
+                    sweeps_mean=pr.sweeps_mean, sweeps_max=pr.sweeps_max, phase_sweeps_max=phase_sweeps)
 
     def hsde_set_data(self, i: int, c: np.ndarray, b: np.ndarray):
         cc = np.ascontiguousarray(c, np.float64)
