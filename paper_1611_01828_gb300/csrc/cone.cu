@@ -125,15 +125,19 @@ __device__ __forceinline__ int sigma(int j) {
 // Jacobi rotation (c, s, t = s/c) that zeroes a_pq of the 2x2 block
 // [[a_pp, a_pq], [a_pq, a_qq]] (Golub & Van Loan, symmetric Schur 2x2):
 // theta = (a_qq - a_pp) / (2 a_pq), t = sign(theta) / (|theta| + sqrt(1 + theta^2)).
-// FP32 uses the fast reciprocal / reciprocal-square-root instructions: the
-// rotation is applied exactly as the computed (c, s) pair, so their ~2 ulp
-// error only perturbs the angle, not the orthogonality of the update.
+// FP32 uses the approximate divide, reciprocal and reciprocal square root
+// instructions for t: the update applies c = 1/sqrt(1 + t^2) and s = t c as
+// computed, so their error only perturbs the angle (a_pq is zeroed to
+// ~1e-7 relative, which the update drops), not the orthogonality of the
+// rotation.  For |theta| > 1e18, sqrt(1 + theta^2) = |theta| in FP32.
 __device__ __forceinline__ void rotation(float app, float aqq, float apq, float& cs, float& sn, float& t) {
     cs = 1.f; sn = 0.f; t = 0.f;
     if (apq != 0.f) {
         const float theta = __fdividef(aqq - app, 2.f * apq);
-        const float r = __fsqrt_rn(fmaf(theta, theta, 1.f));
-        t = __frcp_rn(fabsf(theta) + r);
+        const float at = fabsf(theta);
+        const float q = fmaf(theta, theta, 1.f);
+        const float r = at < 1e18f ? q * rsqrtf(q) : at;
+        t = __fdividef(1.f, at + r);
         if (theta < 0.f) t = -t;
         cs = rsqrtf(fmaf(t, t, 1.f));
         sn = t * cs;

@@ -61,12 +61,13 @@ struct InstDev {
     double tau, kappa, eta;
     // last check
     double pres, dres, gap, pobj, dobj, pinf, dinf, ctx, bty;
-    // constraint-space sums of the stopping rule, from k_bwd_eta to k_post
-    double chk_r0, chk_r1, chk_r2;
+    // omega_tau = tau + kappa of the current iteration (before the update),
+    // from k_bwd_eta to k_post
+    double ot_prev;
 };
 
 // Number of partial sums stored per N-space tile.
-constexpr int KPART = 4;
+constexpr int KPART = 8;
 // Entries per N-space tile (one CTA of 256 threads each).
 constexpr int TILE_N = 256;
 // Nonzeros of A^T per A^T tile (whole rows; a longer row is a tile alone).
