@@ -24,6 +24,7 @@ import json
 import os
 import signal
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -74,7 +75,7 @@ import json, os, sys, time
 sys.path.insert(0, {root!r})
 import synth
 from oracle import hsde
-p = synth.config1(instance={inst})
+p = synth.maxcut_grid_instance(instance={inst})
 t0 = time.perf_counter()
 ref = hsde.HSDE(p)
 setup_s = time.perf_counter() - t0
@@ -119,7 +120,9 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # samples go to a scratch file; HSDE_CLOCKS_DIR keeps them somewhere else
+        out = os.environ.get("HSDE_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"hsde_clocks_rank{index}.csv")
 
     def start(self):
         try:
@@ -240,7 +243,7 @@ def run_ours(args):
     import synth
     from paper_1611_01828_gb300 import hsde
 
-    prob = synth.config1(instance=rank)
+    prob = synth.maxcut_grid_instance(instance=rank)
     # a real stream shared by the library, the L2 flush and the timing events
     # (torch's default stream is the legacy NULL stream)
     stream = torch.cuda.Stream(dev)
@@ -366,7 +369,7 @@ def run_ours(args):
         roof = {"bound": "alu", "kernel": f"k_cone ({dom}, FP32 Jacobi)", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (max SM clock)",
-                "traffic": traffic_from_profile(f"k_cone_{dom}_cfg1"),
+                "traffic": traffic_from_profile(f"k_{dom}_maxcut_grid20x100"),
                 "phase_ms": dom_ms, "algorithmic_flops_per_launch": cone_flops(dom_units)}
     else:
         peak = (peaks or {}).get("hbm_gbs", 6800.0)
@@ -430,7 +433,7 @@ def batched_leg(args, hsde, torch, dev, stream, timed_steps):
     rank = int(os.environ.get("RANK", "0"))
     t0 = time.perf_counter()
     sel = range(args.batched_instances) if args.batched_instances > 0 else None
-    probs = synth.config3(seed_instance=rank, select=sel)
+    probs = synth.serving_batch(seed_instance=rank, select=sel)
     gen_s = time.perf_counter() - t0
     B = len(probs)
     big = 1 << 30

@@ -258,14 +258,15 @@ int enqueue_iteration_v(hsde_handle* h, const DevView& V, int warm, bool events)
     CK(rec(h, h->ev_aff, h->st));
     // fork: every clique bucket on its own branch; buckets whose CTAs each
     // take a whole SM go first, largest cliques first (their CTAs are placed
-    // while SMs are still empty), then the others, smallest first
+    // while SMs are still empty), then the others by total work sum c^3,
+    // largest first (the longest branch starts first)
     CK(cudaEventRecord(h->ev_fork, h->st));
     const size_t nb = h->buckets.size();
-    std::vector<size_t> order;
+    std::vector<size_t> order, rest;
     for (size_t i = nb; i-- > 0;)
-        if (cone_bucket_alone(h->buckets[i], h->mixed)) order.push_back(i);
-    for (size_t i = 0; i < nb; ++i)
-        if (!cone_bucket_alone(h->buckets[i], h->mixed)) order.push_back(i);
+        (cone_bucket_alone(h->buckets[i], h->mixed) ? order : rest).push_back(i);
+    std::stable_sort(rest.begin(), rest.end(), [&](size_t a, size_t b) { return h->bucket_c3[a] > h->bucket_c3[b]; });
+    order.insert(order.end(), rest.begin(), rest.end());
     for (size_t i : order) {
         CK(cudaStreamWaitEvent(h->side[i], h->ev_fork, 0));
         CK(rec(h, h->ev_cs[i], h->side[i]));

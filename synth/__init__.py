@@ -32,8 +32,8 @@ import numpy as np
 
 __all__ = [
     "Problem", "block_arrow", "maxcut_grid", "make_primal_infeasible",
-    "make_dual_infeasible", "trace_one", "config0", "config1", "config2",
-    "config3", "config4", "rng_for",
+    "make_dual_infeasible", "trace_one", "block_arrow_n50", "maxcut_grid_instance", "block_arrow_sweep",
+    "serving_batch", "differentiation_maxcut_grid", "rng_for",
 ]
 
 
@@ -324,25 +324,25 @@ def make_dual_infeasible(p: Problem, rng) -> Problem:
 # the five workload configurations
 # ----------------------------------------------------------------------------
 
-def config0(infeasible=False):
+def block_arrow_n50(infeasible=False):
     """n=50 block-arrow (8 blocks of 6, arrow 2), m=20 dense constraints, cond(X0)<=100."""
     p = block_arrow(8, 6, 2, 20, rng_for(0), dense_constraints=True, kappa=100.0,
-                    name="cfg0_block_arrow_n50_m20")
+                    name="block_arrow_n50_m20")
     return make_primal_infeasible(p) if infeasible else p
 
 
-def config1(R=20, K=100, instance=0):
+def maxcut_grid_instance(R=20, K=100, instance=0):
     """maxG32-shaped max-cut: open 20 x 100 grid (n=2000, m=2000)."""
-    return maxcut_grid(R, K, rng_for(1, instance), name=f"cfg1_maxcut_grid{R}x{K}")
+    return maxcut_grid(R, K, rng_for(1, instance), name=f"maxcut_grid{R}x{K}")
 
 
-def config2(l, d, h=5, instance=0):
+def block_arrow_sweep(l, d, h=5, instance=0):
     """Block-arrow sweep: m = 2l, constraints 2j, 2j+1 dense on clique j, cond <= 1e3."""
     return block_arrow(l, d, h, 2 * l, rng_for(2, instance), kappa=1e3, assign="pairs",
-                       name=f"cfg2_block_arrow_l{l}_d{d}")
+                       name=f"block_arrow_l{l}_d{d}")
 
 
-def config3(B=256, n_lo=100, n_hi=1500, seed_instance=0, select=None):
+def serving_batch(B=256, n_lo=100, n_hi=1500, seed_instance=0, select=None):
     """Batch of B independent instances of uneven sizes.
 
     Half max-cut grids (m = n), half block-arrow with m ~ U[n/2, 2n] assigned
@@ -380,11 +380,11 @@ def config3(B=256, n_lo=100, n_hi=1500, seed_instance=0, select=None):
         if kind == "grid":
             R = 10
             K = max(2, n // R)
-            p = maxcut_grid(R, K, sub, name=f"cfg3_{i}_maxcut_{R}x{K}")
+            p = maxcut_grid(R, K, sub, name=f"batch_{i}_maxcut_{R}x{K}")
         else:
             l = max(2, (n - 5) // d)
             p = block_arrow(l, d, 5, m, sub, kappa=1e3, assign="roundrobin",
-                            name=f"cfg3_{i}_block_arrow_l{l}_d{d}_m{m}")
+                            name=f"batch_{i}_block_arrow_l{l}_d{d}_m{m}")
         if kinds[i] == "primal_infeasible":
             p = make_primal_infeasible(p)
         elif kinds[i] == "dual_infeasible":
@@ -393,6 +393,6 @@ def config3(B=256, n_lo=100, n_hi=1500, seed_instance=0, select=None):
     return out
 
 
-def config4():
+def differentiation_maxcut_grid():
     """Differentiation workload: max-cut on the open 10 x 100 grid (n=1000)."""
-    return maxcut_grid(10, 100, rng_for(4), name="cfg4_maxcut_grid10x100")
+    return maxcut_grid(10, 100, rng_for(4), name="maxcut_grid10x100_diff")

@@ -43,8 +43,8 @@ def test_default_options(hs):
 
 def _cases():
     rng = np.random.default_rng(0)
-    out = [synth.config0(), synth.config0(True), synth.maxcut_grid(7, 9, rng), synth.config4(),
-           synth.block_arrow(5, 4, 3, 6, rng), synth.config1()]
+    out = [synth.block_arrow_n50(), synth.block_arrow_n50(True), synth.maxcut_grid(7, 9, rng), synth.differentiation_maxcut_grid(),
+           synth.block_arrow(5, 4, 3, 6, rng), synth.maxcut_grid_instance()]
     # random sparse patterns with fill
     for seed in range(4):
         n = 30 + 17 * seed
@@ -81,7 +81,7 @@ def _mutate(p, **kw):
 
 
 def test_invalid_inputs_rejected(hs):
-    p = synth.config0()
+    p = synth.block_arrow_n50()
     bad = [
         _mutate(p, n=0),
         _mutate(p, C_row=np.where(np.arange(len(p.C_row)) == 3, 999, p.C_row).astype(np.int32)),

@@ -1,5 +1,5 @@
 """GPU: batched serving of independent SDPs of uneven sizes in the same
-launches (the config-3 generator), against the FP64 oracle per instance.
+launches (the serving-batch generator), against the FP64 oracle per instance.
 
 Tolerances: identical verdicts and iteration counts within 10% at the
 default eps_tol = 1e-4.  Objectives are compared against the oracle's
@@ -38,14 +38,14 @@ TIGHT = [2, 11, 13]
 
 @pytest.fixture(scope="module")
 def batch():
-    probs = synth.config3(B=16, n_lo=60, n_hi=160, select=SEL)
+    probs = synth.serving_batch(B=16, n_lo=60, n_hi=160, select=SEL)
     refs = [ohsde.HSDE(p).solve(max_iter=3000) for p in probs]
     return probs, refs
 
 
 @pytest.fixture(scope="module")
 def tight():
-    probs = synth.config3(B=16, n_lo=60, n_hi=160, select=TIGHT)
+    probs = synth.serving_batch(B=16, n_lo=60, n_hi=160, select=TIGHT)
     refs = [ohsde.HSDE(p).solve(eps=1e-7, max_iter=60000) for p in probs]
     return probs, refs
 

@@ -63,8 +63,8 @@ def random_state(ref, rng, f32=False):
 
 
 PROBS = {
-    "cfg0": lambda: synth.config0(),
-    "cfg0_inf": lambda: synth.config0(True),
+    "arrow_n50": lambda: synth.block_arrow_n50(),
+    "arrow_n50_inf": lambda: synth.block_arrow_n50(True),
     "grid_7x9": lambda: synth.maxcut_grid(7, 9, np.random.default_rng(1)),
     "arrow_odd": lambda: synth.block_arrow(6, 5, 2, 9, np.random.default_rng(2), assign="roundrobin"),
     "arrow_buckets": lambda: synth.block_arrow(3, 30, 3, 6, np.random.default_rng(3)),   # c = 33 (CTA path)
@@ -117,7 +117,7 @@ def test_mixed_one_step_from_random_state(hs, name):
     assert rel(got, want) < 1e-4
 
 
-@pytest.mark.parametrize("name", ["cfg0", "grid_7x9", "arrow_odd"])
+@pytest.mark.parametrize("name", ["arrow_n50", "grid_7x9", "arrow_odd"])
 def test_fp64_first_iterations_from_start(hs, name):
     p = PROBS[name]()
     ref = ohsde.HSDE(p)
@@ -136,7 +136,7 @@ def _oracle_solve(p, **kw):
     return ref, ref.solve(**kw)
 
 
-@pytest.mark.parametrize("name", ["cfg0", "cfg0_inf", "arrow_odd"])
+@pytest.mark.parametrize("name", ["arrow_n50", "arrow_n50_inf", "arrow_odd"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_full_solve_verdict_and_objective(hs, name, prec):
     p = PROBS[name]()
@@ -156,7 +156,7 @@ def test_full_solve_verdict_and_objective(hs, name, prec):
 
 
 def test_solution_and_certificate_queries(hs):
-    p = synth.config0()
+    p = synth.block_arrow_n50()
     ref, res = _oracle_solve(p)
     with hs.Handle(p, precision="fp64") as H:
         H.solve()
@@ -168,7 +168,7 @@ def test_solution_and_certificate_queries(hs):
     assert rel(V.x_from_lower(X), Xr) < 1e-6
     assert rel(y, yr) < 1e-6
     assert rel(V.x_from_lower(Z), Zr) < 1e-6
-    pi = synth.config0(True)
+    pi = synth.block_arrow_n50(True)
     ref2, res2 = _oracle_solve(pi)
     with hs.Handle(pi, precision="fp64") as H:
         H.solve()
@@ -192,7 +192,7 @@ def test_dual_infeasible_certificate(hs):
 
 
 def test_batch_equals_single_bitwise(hs):
-    probs = [PROBS[k]() for k in ("cfg0", "grid_7x9", "arrow_odd", "cfg0_inf")]
+    probs = [PROBS[k]() for k in ("arrow_n50", "grid_7x9", "arrow_odd", "arrow_n50_inf")]
     singles = []
     for p in probs:
         with hs.Handle(p, precision="fp64") as H:
@@ -207,7 +207,7 @@ def test_batch_equals_single_bitwise(hs):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_checkpoint_resume_bitwise(hs, prec):
     # bitwise only without the eigensolver warm start (its basis is not state)
-    p = PROBS["cfg0"]()
+    p = PROBS["arrow_n50"]()
     with hs.Handle(p, precision=prec, warm_start=0) as H:
         H.hsde_iterate(40)
         straight = H.hsde_get_state(0)
@@ -221,7 +221,7 @@ def test_checkpoint_resume_bitwise(hs, prec):
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
-@pytest.mark.parametrize("name", ["cfg0", "arrow_buckets", "grid_7x9"])
+@pytest.mark.parametrize("name", ["arrow_n50", "arrow_buckets", "grid_7x9"])
 def test_warm_start_matches_cold_start(hs, prec, tol, name):
     p = PROBS[name]()
     out = {}
@@ -256,8 +256,8 @@ def test_no_constraints_and_singleton_cliques(hs):
 
 
 @pytest.mark.parametrize("d", [10, 25, 50])
-def test_config2_small_sweep_mixed_vs_oracle(hs, d):
-    p = synth.config2(100, d)
+def test_block_arrow_sweep_mixed_vs_oracle(hs, d):
+    p = synth.block_arrow_sweep(100, d)
     ref, res = _oracle_solve(p)
     with hs.Handle(p, precision="mixed") as H:
         st = H.solve(chunk=50)
@@ -267,8 +267,8 @@ def test_config2_small_sweep_mixed_vs_oracle(hs, d):
         assert abs(info["pobj"] - res.info["pobj"]) <= 1e-4 * max(1.0, abs(res.info["pobj"]))
 
 
-def test_config1_first_iterations_fp64(hs):
-    p = synth.config1()
+def test_maxcut_grid20x100_first_iterations_fp64(hs):
+    p = synth.maxcut_grid_instance()
     ref = ohsde.HSDE(p)
     u, nu = ref.initial()
     for _ in range(30):

@@ -52,7 +52,7 @@ def _grad(torch, hsde, unrolled, H, c, b, K, ckpt):
     return float(f), ct.grad.numpy().copy(), bt.grad.numpy().copy()
 
 
-@pytest.mark.parametrize("case", ["grid", "arrow", "cfg0"])
+@pytest.mark.parametrize("case", ["grid", "arrow", "arrow_n50"])
 def test_fp64_gradient_matches_oracle(env, case):
     torch, hsde, unrolled = env
     if case == "grid":
@@ -60,7 +60,7 @@ def test_fp64_gradient_matches_oracle(env, case):
     elif case == "arrow":
         p0, K = synth.block_arrow(3, 3, 2, 5, np.random.default_rng(2), kappa=30.0, assign="roundrobin"), 30
     else:
-        p0, K = synth.config0(), 25
+        p0, K = synth.block_arrow_n50(), 25
     st = ohsde.HSDE(p0).V.st
     p = _on_pattern(p0, st)
     ref = ohsde.HSDE(p)
@@ -75,18 +75,18 @@ def test_fp64_gradient_matches_oracle(env, case):
 
 
 @pytest.fixture(scope="module")
-def cfg4(env):
+def diff_grid(env):
     torch, hsde, unrolled = env
-    p = synth.config4()
+    p = synth.differentiation_maxcut_grid()
     H = hsde.Handle(p, precision="fp64")
     c0 = unrolled.pattern_values(H, p.C_row, p.C_col, p.C_val)
     yield p, H, c0
     H.close()
 
 
-def test_config4_gradient_central_differences(env, cfg4):
+def test_diff_grid_gradient_central_differences(env, diff_grid):
     torch, hsde, unrolled = env
-    p, H, c0 = cfg4
+    p, H, c0 = diff_grid
     K, ckpt = 200, 20
     f0, gC, gb = _grad(torch, hsde, unrolled, H, c0, p.b, K, ckpt)
     w = torch.as_tensor(unrolled.pattern_weights(H))
@@ -105,13 +105,13 @@ def test_config4_gradient_central_differences(env, cfg4):
         an = float(gC @ dC + gb @ db)
         errs.append(abs(fd - an) / max(abs(fd), 1e-12))
     errs = np.array(errs)
-    print("config-4 central-difference relative errors:", np.array2string(errs, precision=2))
+    print("max-cut 10x100 central-difference relative errors:", np.array2string(errs, precision=2))
     assert np.median(errs) <= 5e-3 and errs.max() <= 5e-2, errs
 
 
-def test_config4_gradient_matches_oracle(env, cfg4):
+def test_diff_grid_gradient_matches_oracle(env, diff_grid):
     torch, hsde, unrolled = env
-    p, H, c0 = cfg4
+    p, H, c0 = diff_grid
     K, ckpt = 200, 20
     _, gC, gb = _grad(torch, hsde, unrolled, H, c0, p.b, K, ckpt)
     st = ohsde.HSDE(p).V.st
@@ -124,9 +124,9 @@ def test_config4_gradient_matches_oracle(env, cfg4):
     assert np.linalg.norm(gb - bbar) <= 1e-6 * np.linalg.norm(bbar)
 
 
-def test_config4_mixed_gradient_close_to_fp64(env, cfg4):
+def test_diff_grid_mixed_gradient_close_to_fp64(env, diff_grid):
     torch, hsde, unrolled = env
-    p, H, c0 = cfg4
+    p, H, c0 = diff_grid
     K, ckpt = 200, 20
     _, gC64, gb64 = _grad(torch, hsde, unrolled, H, c0, p.b, K, ckpt)
     with hsde.Handle(p, precision="mixed") as Hm:

@@ -42,7 +42,7 @@ def test_dk_vjp_matches_finite_differences():
 
 
 def test_sparse_Q_equals_dense_Q():
-    hs = hsde.HSDE(synth.config0())
+    hs = hsde.HSDE(synth.block_arrow_n50())
     assert np.array_equal(adjoint.sparse_Q(hs).toarray(), dense.build_Q(hs))
 
 

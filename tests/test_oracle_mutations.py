@@ -70,7 +70,7 @@ def test_wrong_sign_nu_update(monkeypatch):
         u_new = self.project_K(uhat - nu)
         return u_new, nu + uhat - u_new, uhat
     monkeypatch.setattr(hsde.HSDE, "step", bad_step)
-    res = hsde.HSDE(synth.config0()).solve(max_iter=500)
+    res = hsde.HSDE(synth.block_arrow_n50()).solve(max_iter=500)
     assert res.status != hsde.SOLVED
 
 
@@ -80,7 +80,7 @@ def test_missing_tau_clamp(monkeypatch):
         out[self.nF:self.nF + self.nd] = self.project_S(w[self.nF:self.nF + self.nd])
         return out                                          # tau not clamped at 0
     monkeypatch.setattr(hsde.HSDE, "project_K", bad_proj)
-    res = hsde.HSDE(synth.config0(infeasible=True)).solve(max_iter=500)
+    res = hsde.HSDE(synth.block_arrow_n50(infeasible=True)).solve(max_iter=500)
     assert res.status != hsde.PRIMAL_INFEASIBLE
 
 
@@ -97,7 +97,7 @@ def test_transposed_clique_block(monkeypatch):
             out[o:o + c * c] = ((V * np.maximum(lam, 0)) @ V.T).reshape(-1, order="F")
         return out
     monkeypatch.setattr(hsde.HSDE, "project_S", bad)
-    hs = hsde.HSDE(synth.config0())
+    hs = hsde.HSDE(synth.block_arrow_n50())
     rng = np.random.default_rng(3)
     s = rng.standard_normal(hs.nd)
     got = hs.project_S(s)

@@ -100,10 +100,10 @@ def test_Q_is_skew():
     assert abs(u @ Q @ u) < 1e-10
 
 
-@pytest.mark.parametrize("prob", ["tiny", "tiny_dense", "cfg0", "cfg0_inf", "grid"])
+@pytest.mark.parametrize("prob", ["tiny", "tiny_dense", "arrow_n50", "arrow_n50_inf", "grid"])
 def test_affine_matches_dense_solve(prob):
     p = {"tiny": lambda: _tiny(), "tiny_dense": lambda: _tiny(dense_constraints=True, seed=3),
-         "cfg0": synth.config0, "cfg0_inf": lambda: synth.config0(True),
+         "arrow_n50": synth.block_arrow_n50, "arrow_n50_inf": lambda: synth.block_arrow_n50(True),
          "grid": lambda: synth.maxcut_grid(3, 4, np.random.default_rng(2))}[prob]()
     hs = hsde.HSDE(p)
     Q = dense.build_Q(hs)
@@ -132,7 +132,7 @@ def test_third_block_elimination_matrix():
 
 
 def test_dense_iterates_match_eliminated_iterates():
-    p = synth.config0()
+    p = synth.block_arrow_n50()
     hs = hsde.HSDE(p)
     Q = dense.build_Q(hs)
     u, nu = hs.initial()
@@ -168,7 +168,7 @@ def test_pattern_restriction_equals_full_space():
 
 
 def test_packed_layout_roundtrip():
-    hs = hsde.HSDE(synth.config0())
+    hs = hsde.HSDE(synth.block_arrow_n50())
     rng = np.random.default_rng(0)
     xl = rng.standard_normal(hs.V.st.N)
     assert np.array_equal(hs.V.x_to_lower(hs.V.x_from_lower(xl)), xl)

@@ -81,7 +81,7 @@ def test_verdict_solved_on_hand_built_optimum():
 def test_verdict_primal_infeasible_closed_form_certificate():
     """tr X = -1 appended: y = -e_{m+1}, z_k = diag(1/D) on each clique gives
     A^T y + H^T z = 0 and b^T y = 1."""
-    p = synth.config0(infeasible=True)
+    p = synth.block_arrow_n50(infeasible=True)
     hs = hsde.HSDE(p)
     st = hs.V.st
     y = np.zeros(hs.m); y[-1] = -1.0
@@ -115,8 +115,8 @@ def test_verdict_dual_infeasible_hand_built_direction():
     assert hs.verdict(info, 1e-4) == hsde.DUAL_INFEASIBLE
 
 
-def test_config0_solution_invariants():
-    p = synth.config0()
+def test_block_arrow_n50_solution_invariants():
+    p = synth.block_arrow_n50()
     hs = hsde.HSDE(p)
     res = hs.solve(eps=1e-6, max_iter=20000)
     assert res.status == hsde.SOLVED
@@ -146,7 +146,7 @@ def test_config0_solution_invariants():
 
 
 def test_primal_infeasible_instance_gives_valid_certificate():
-    p = synth.config0(infeasible=True)
+    p = synth.block_arrow_n50(infeasible=True)
     hs = hsde.HSDE(p)
     res = hs.solve()
     assert res.status == hsde.PRIMAL_INFEASIBLE
@@ -175,6 +175,6 @@ def test_dual_infeasible_instance_gives_valid_certificate():
         assert np.linalg.eigvalsh(0.5 * (Sk + Sk.T)).min() >= -1e-9 * max(1e-30, np.abs(Sk).max())
 
 
-def test_feasible_config0_reaches_tolerance():
-    res = hsde.HSDE(synth.config0()).solve()
+def test_feasible_block_arrow_n50_reaches_tolerance():
+    res = hsde.HSDE(synth.block_arrow_n50()).solve()
     assert res.status == hsde.SOLVED and res.iterations < 2000

@@ -99,7 +99,7 @@ def test_cliques_against_networkx(seed):
 
 def test_block_arrow_closed_form():
     g = GOLD["block_arrow_l8_d6_h2"]
-    p = synth.config0()
+    p = synth.block_arrow_n50()
     st = symbolic.analyze(p)
     assert st.p == g["p"] and all(len(c) == g["c"] for c in st.cliques)
     assert st.N == g["N"] and st.n_d == g["n_d"] and st.P == g["P"]

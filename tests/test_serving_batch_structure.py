@@ -19,8 +19,8 @@ def hs():
 
 
 @pytest.mark.parametrize("i", [0, 1, 37, 64, 101, 128, 199, 255])
-def test_config3_instance_structure_bit_exact(hs, i):
-    p = synth.config3(select=[i])[0]
+def test_serving_batch_instance_structure_bit_exact(hs, i):
+    p = synth.serving_batch(select=[i])[0]
     got = hs.hsde_analyze(p)
     st = symbolic.analyze(p)
     for k in ("order", "clique_ptr", "clique_idx", "pat_colptr", "pat_row", "gather", "D"):
