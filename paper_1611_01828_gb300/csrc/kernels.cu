@@ -51,6 +51,34 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return r;
 }
 
+// NV block sums at once (one set of barriers); each value is summed in the
+// same order as block_sum.  sh holds NV * NT / 32 doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum_n(double (&v)[NV], double* sh) {
+    constexpr int W = NT / 32;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
+    __syncthreads();
+    if (l == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) sh[i * W + w] = v[i];
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double t = (l < W) ? sh[i * W + l] : 0.0;
+            t = warp_sum(t);
+            if (l == 0) sh[i * W] = t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = sh[i * W];
+    __syncthreads();
+}
+
 __device__ __forceinline__ bool is_check_iter(const DevView& V, int iter) {
     return (iter % V.check_every) == 0 || iter >= V.max_iter;
 }
@@ -263,13 +291,11 @@ __global__ void __launch_bounds__(NT) k_bwd_eta(DevView V) {
     if (threadIdx.x == 0) V.at_part[blockIdx.x] = part;
     if (!last_cta(V.counters + 2 * t.x, I.at_end - I.at_begin, &flag)) return;
     // ---- last CTA of this instance ----
-    double ctw = 0.0;
-    for (int tt = I.at_begin + threadIdx.x; tt < I.at_end; tt += NT) ctw += __ldcg(V.at_part + tt);
-    ctw = block_sum(ctw, sh);
-    double btw = 0.0;
-    for (int i = threadIdx.x; i < I.m; i += NT) btw += __ldcg(V.rowb + I.m_off + i);
-    btw = block_sum(btw, sh);
-    const double sw = ctw - btw;
+    double cb[2] = {0.0, 0.0};   // c^T x_w, b^T y_w
+    for (int tt = I.at_begin + threadIdx.x; tt < I.at_end; tt += NT) cb[0] += __ldcg(V.at_part + tt);
+    for (int i = threadIdx.x; i < I.m; i += NT) cb[1] += __ldcg(V.rowb + I.m_off + i);
+    block_sum_n<2>(cb, sh);
+    const double sw = cb[0] - cb[1];
     const double eta = sw / I.den;
     const double tau = I.tau, kappa = I.kappa;
     const double ot = tau + kappa;
@@ -299,10 +325,14 @@ __global__ void __launch_bounds__(NT) k_bwd_eta(DevView V) {
 // y = y_w - eta y_p over a slice of the constraints per CTA, with the
 // constraint-space partials ||A x - tau b||^2, ||A x||^2, b^T y;
 // the last CTA of each instance takes the verdict (readings P5/P6).
+// Copies of pattern entries (H^T) staged per pass of k_post.
+constexpr int POST_STAGE = 2048;
+
 template <typename T>
 __global__ void __launch_bounds__(NT) k_post(DevView V) {
-    __shared__ double sh[32];
+    __shared__ double sh[8 * NT / 32];
     __shared__ int flag;
+    __shared__ double cz[POST_STAGE], call[POST_STAGE];   // per copy: z, and s + z + v
     const int4 t = V.tiles[blockIdx.x];
     InstDev& I = V.inst[t.x];
     if (I.status != HSDE_RUNNING) return;
@@ -310,38 +340,39 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
     const double eta = I.eta, tau = I.tau;
     const double ot = I.tau + I.kappa;            // omega_tau of the next iteration
     double a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    for (int e = t.y + threadIdx.x; e < t.z; e += NT) {
-        const double x = V.xw[e] - eta * V.xp[e];
+    // one pattern entry per thread (TILE_N == NT)
+    const int e = t.y + threadIdx.x;
+    const bool has = e < t.z;
+    double x = 0.0;
+    int k0 = 0, k1 = 0;
+    if (has) {
+        x = V.xw[e] - eta * V.xp[e];
         V.x[e] = x;
-        double hz = 0.0, hall = 0.0;
-        const int k1 = V.sc_ptr[e + 1];
-        int k = V.sc_ptr[e];
-        // four copies at a time: their loads are issued together (an entry
-        // shared by many cliques otherwise waits on one chain per copy);
-        // the sums keep the copies' order
-        for (; k + 4 <= k1; k += 4) {
-            int p[4];
-            double zz[4], ss[4], vv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) p[u] = V.sc_idx[k + u];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                zz[u] = ld<T>(V.z, p[u]);
-                ss[u] = ld<T>(V.s, p[u]);
-                vv[u] = ld<T>(V.v, p[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                hz += zz[u];
-                hall += ss[u] + zz[u] + vv[u];
-            }
-        }
-        for (; k < k1; ++k) {
-            const int p = V.sc_idx[k];
+        k0 = V.sc_ptr[e];
+        k1 = V.sc_ptr[e + 1];
+    }
+    // H^T z and H^T (s + z + v): the tile's copies are one contiguous range;
+    // the CTA loads them together (coalesced indices, one gather per copy)
+    // into shared memory, then each entry sums its own copies in order.
+    double hz = 0.0, hall = 0.0;
+    const int c0 = V.sc_ptr[t.y], c1 = V.sc_ptr[t.z];
+    for (int cb = c0; cb < c1; cb += POST_STAGE) {
+        const int ce = min(c1, cb + POST_STAGE);
+        __syncthreads();
+        for (int c = cb + threadIdx.x; c < ce; c += NT) {
+            const int p = V.sc_idx[c];
             const double zz = ld<T>(V.z, p);
-            hz += zz;
-            hall += ld<T>(V.s, p) + zz + ld<T>(V.v, p);
+            cz[c - cb] = zz;
+            call[c - cb] = ld<T>(V.s, p) + zz + ld<T>(V.v, p);
         }
+        __syncthreads();
+        const int a = max(k0, cb), b = min(k1, ce);
+        for (int k = a; k < b; ++k) {
+            hz += cz[k - cb];
+            hall += call[k - cb];
+        }
+    }
+    if (has) {
         const double ce = V.c[e];
         V.f[e] = (x - ot * ce + 0.5 * hall) * V.inv_delta[e];
         if (check) {
@@ -381,16 +412,12 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
         }
     }
     if (check) {
-        a1 = block_sum(a1, sh);
-        a2 = block_sum(a2, sh);
-        a3 = block_sum(a3, sh);
-        b1 = block_sum(b1, sh);
-        b2 = block_sum(b2, sh);
-        b3 = block_sum(b3, sh);
+        double v6[6] = {a1, a2, a3, b1, b2, b3};
+        block_sum_n<6>(v6, sh);
         if (threadIdx.x == 0) {
             double* pp = V.part + (int64_t)blockIdx.x * KPART;
-            pp[1] = a1; pp[2] = a2; pp[3] = a3;
-            pp[4] = b1; pp[5] = b2; pp[6] = b3;
+            pp[1] = v6[0]; pp[2] = v6[1]; pp[3] = v6[2];
+            pp[4] = v6[3]; pp[5] = v6[4]; pp[6] = v6[5];
         }
     }
     if (!last_cta(V.counters + 2 * t.x + 1, I.tile_end - I.tile_begin, &flag)) return;
@@ -400,18 +427,16 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
         I.vcold = 0;                                // stored eigenbases are valid from now on
     }
     if (!check) return;
-    a1 = 0; a2 = 0; a3 = 0;
-    double r0 = 0, r1 = 0, r2 = 0;
+    double v7[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int tt = I.tile_begin + threadIdx.x; tt < I.tile_end; tt += NT) {
         const double* pp = V.part + (int64_t)tt * KPART;
-        a1 += __ldcg(pp + 1); a2 += __ldcg(pp + 2); a3 += __ldcg(pp + 3);
-        r0 += __ldcg(pp + 4); r1 += __ldcg(pp + 5); r2 += __ldcg(pp + 6);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) v7[i] += __ldcg(pp + 1 + i);
     }
-    a1 = block_sum(a1, sh); a2 = block_sum(a2, sh); a3 = block_sum(a3, sh);
-    r0 = block_sum(r0, sh); r1 = block_sum(r1, sh); r2 = block_sum(r2, sh);
-    double hs = 0;
-    for (int k = I.cl_begin + threadIdx.x; k < I.cl_end; k += NT) hs += __ldcg(V.cl_part + k);
-    hs = block_sum(hs, sh);
+    for (int k = I.cl_begin + threadIdx.x; k < I.cl_end; k += NT) v7[6] += __ldcg(V.cl_part + k);
+    block_sum_n<7>(v7, sh);
+    a1 = v7[0]; a2 = v7[1]; a3 = v7[2];
+    const double r0 = v7[3], r1 = v7[4], r2 = v7[5], hs = v7[6];
     if (threadIdx.x != 0) return;
     const double ctx = a3, bty = r2;
     double pres = INFINITY, dres = INFINITY, gap = INFINITY, pobj = NAN, dobj = NAN;
