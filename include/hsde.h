@@ -105,7 +105,10 @@ typedef struct hsde_options {
                              1 on.  Results then depend on the solve history, so
                              a resumed run (hsde_set_state) matches a straight
                              run to rounding, not bitwise.                      */
-    int32_t warm_refresh; /* cold start every k-th iteration, default 32         */
+    int32_t warm_refresh; /* every k-th iteration the stored bases get one
+                             Newton-Schulz step V <- V (3I - V^T V)/2 against
+                             the rounding drift of their orthogonality,
+                             default 32                                        */
     int32_t _pad;
 } hsde_options;
 

@@ -26,8 +26,9 @@
 // is a coalesced 2-vector; no permutation has to be tracked:
 // s = V max(diag A, 0) V^T with V(i, slot) = Vs[slot][i].
 // Warm start: V of the previous iteration (per clique, FP32/FP64 as the
-// clique arrays) seeds the next solve through A <- V^T A V, with a cold start
-// every `refresh` iterations to bound the loss of orthogonality.
+// clique arrays) seeds the next solve through A <- V^T A V; every `refresh`
+// iterations one Newton-Schulz step V <- V (3I - V^T V)/2 first restores the
+// orthogonality that rounding erodes from one iteration to the next.
 //
 // A group of G threads owns one clique; groups never wait on each other
 // (sub-warp shuffles for G < 32, named barriers for G > 32).
@@ -316,7 +317,11 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
     const int64_t off = V.cl_off[k];
     const double eta = I.eta;
     T* Vst = V.vstore ? reinterpret_cast<T*>(V.vstore) + V.vs_off[k] : nullptr;
-    const bool use_warm = warm && Vst != nullptr && !I.vcold && refresh > 1 && (I.iter % refresh) != 1;
+    const bool use_warm = warm && Vst != nullptr && !I.vcold;
+    // every refresh-th iteration the stored basis, whose orthogonality
+    // drifts by rounding from one iteration to the next, gets one
+    // Newton-Schulz step V <- V (3I - V^T V) / 2 before use
+    const bool reorth = use_warm && refresh > 0 && (I.iter % refresh) == (1 % refresh);
 
     // zero A0 (padding included); V0 = I or the stored basis (both slot-major)
     for (int idx = lane; idx < CP * CP; idx += G) {
@@ -383,6 +388,55 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
     RoundPlan<Cfg> plan;
     plan.build(lane);
     const int cq = (c + 1) & ~1;   // A and its products vanish beyond c
+    if (reorth) {
+        // Gram matrix G = V^T V (slot x slot) into An, 2 x 2 tiles over all CP
+        // rows (the padding slots' unit vectors included)
+        for (int tix = lane; tix < K * K; tix += G) {
+            const int ts = tix / K, tt = tix - (tix / K) * K;
+            T g00 = 0, g01 = 0, g10 = 0, g11 = 0;
+            for (int q = 0; q < CP; q += 2) {
+                const V2 a0 = *reinterpret_cast<const V2*>(Vc + (2 * ts) * LD + q);
+                const V2 a1 = *reinterpret_cast<const V2*>(Vc + (2 * ts + 1) * LD + q);
+                const V2 b0 = *reinterpret_cast<const V2*>(Vc + (2 * tt) * LD + q);
+                const V2 b1 = *reinterpret_cast<const V2*>(Vc + (2 * tt + 1) * LD + q);
+                g00 += a0.x * b0.x + a0.y * b0.y;
+                g01 += a0.x * b1.x + a0.y * b1.y;
+                g10 += a1.x * b0.x + a1.y * b0.y;
+                g11 += a1.x * b1.x + a1.y * b1.y;
+            }
+            V2 r0, r1;
+            r0.x = g00; r0.y = g01; r1.x = g10; r1.y = g11;
+            *reinterpret_cast<V2*>(An + (2 * ts) * LD + 2 * tt) = r0;
+            *reinterpret_cast<V2*>(An + (2 * ts + 1) * LD + 2 * tt) = r1;
+        }
+        gsync<G>(gid);
+        // slot-major: V_s <- 1.5 V_s - 0.5 G V_s
+        for (int tix = lane; tix < K * K; tix += G) {
+            const int ts = tix / K, ti = tix - (tix / K) * K;
+            T p00 = 0, p01 = 0, p10 = 0, p11 = 0;
+            for (int j = 0; j < CP; j += 2) {
+                const V2 g0 = *reinterpret_cast<const V2*>(An + (2 * ts) * LD + j);
+                const V2 g1 = *reinterpret_cast<const V2*>(An + (2 * ts + 1) * LD + j);
+                const V2 v0 = *reinterpret_cast<const V2*>(Vc + j * LD + 2 * ti);
+                const V2 v1 = *reinterpret_cast<const V2*>(Vc + (j + 1) * LD + 2 * ti);
+                p00 += g0.x * v0.x + g0.y * v1.x;
+                p01 += g0.x * v0.y + g0.y * v1.y;
+                p10 += g1.x * v0.x + g1.y * v1.x;
+                p11 += g1.x * v0.y + g1.y * v1.y;
+            }
+            const V2 c0 = *reinterpret_cast<const V2*>(Vc + (2 * ts) * LD + 2 * ti);
+            const V2 c1 = *reinterpret_cast<const V2*>(Vc + (2 * ts + 1) * LD + 2 * ti);
+            V2 n0, n1;
+            n0.x = T(1.5) * c0.x - T(0.5) * p00;
+            n0.y = T(1.5) * c0.y - T(0.5) * p01;
+            n1.x = T(1.5) * c1.x - T(0.5) * p10;
+            n1.y = T(1.5) * c1.y - T(0.5) * p11;
+            *reinterpret_cast<V2*>(Vn + (2 * ts) * LD + 2 * ti) = n0;
+            *reinterpret_cast<V2*>(Vn + (2 * ts + 1) * LD + 2 * ti) = n1;
+        }
+        gsync<G>(gid);
+        T* t2 = Vc; Vc = Vn; Vn = t2;
+    }
     if (use_warm) {
         // An = V^T A (slot x original; A symmetric and full), 2 x 2 tiles
         for (int tix = lane; tix < K * K; tix += G) {
