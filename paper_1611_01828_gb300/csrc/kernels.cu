@@ -266,25 +266,67 @@ __global__ void __launch_bounds__(NT) k_bwd_eta(DevView V) {
             part = (V.diag[e] ? 1.0 : 2.0) * V.c[e] * xv;
         }
     } else {
-        // groups of G lanes (a power of two <= 32, aligned in the warp), one
-        // row per group at a time; the loop bound is uniform over the CTA so
-        // every lane of a warp reaches each shuffle.
+        // The tile's products A_ji y_w,i (at most AT_TILE_NNZ, one contiguous
+        // range) are formed by the whole CTA with independent coalesced loads
+        // and kept in shared memory.  Groups of G lanes (a power of two <= 32,
+        // aligned in the warp) then reduce one row each at a time (the loop
+        // bound is uniform over the CTA, so every lane of a warp reaches each
+        // shuffle), and one thread per row finishes it.  Everything a row
+        // needs besides its sum is loaded up front.
+        __shared__ double prod[AT_TILE_NNZ];
+        __shared__ double rowacc[NT];
+        __shared__ int rowptr[NT + 1];
+        const int nrow = t.z - t.y;      // <= TILE_N == NT
+        const int er = t.y + threadIdx.x;
+        const bool hasr = (int)threadIdx.x < nrow;
+        double fr = 0.0, idr = 0.0, cr = 0.0;
+        bool dr = false;
+        if (hasr) {
+            fr = V.f[er];
+            idr = V.inv_delta[er];
+            cr = V.c[er];
+            dr = V.diag[er] != 0;
+        }
+        for (int r = threadIdx.x; r <= nrow; r += NT) rowptr[r] = V.At_ptr[t.y + r];
+        const int jt0 = V.At_ptr[t.y], jt1 = V.At_ptr[t.z];
+        // eight nonzeros per thread at a time: their index/value loads, then
+        // their gathers, are issued together
+        constexpr int U = 8;
+        for (int jb = jt0 + threadIdx.x; jb < jt1; jb += U * NT) {
+            int col[U];
+            double val[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int j = jb + u * NT;
+                col[u] = j < jt1 ? V.At_col[j] : 0;
+                val[u] = j < jt1 ? V.At_val[j] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int j = jb + u * NT;
+                if (j < jt1) prod[j - jt0] = val[u] * V.yw[col[u]];
+            }
+        }
+        __syncthreads();
         const int grp = threadIdx.x / G, lane = threadIdx.x & (G - 1), ngrp = NT / G;
-        for (int base = t.y; base < t.z; base += ngrp) {
-            const int e = base + grp;
-            const bool valid = e < t.z;
+        for (int base = 0; base < nrow; base += ngrp) {
+            const int r = base + grp;
+            const bool valid = r < nrow;
             double acc = 0.0;
             if (valid) {
-                const int j1 = V.At_ptr[e + 1];
-                for (int j = V.At_ptr[e] + lane; j < j1; j += G) acc += V.At_val[j] * V.yw[V.At_col[j]];
+                const int j1 = rowptr[r + 1] - jt0;
+                for (int j = rowptr[r] - jt0 + lane; j < j1; j += G) acc += prod[j];
             }
             for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (valid && lane == 0) {
-                const double xv = V.f[e] + V.inv_delta[e] * acc;
-                V.xw[e] = xv;
-                V.atyw[e] = acc;
-                part += (V.diag[e] ? 1.0 : 2.0) * V.c[e] * xv;
-            }
+            if (valid && lane == 0) rowacc[r] = acc;
+        }
+        __syncthreads();
+        if (hasr) {
+            const double acc = rowacc[threadIdx.x];
+            const double xv = fr + idr * acc;
+            V.xw[er] = xv;
+            V.atyw[er] = acc;
+            part = (dr ? 1.0 : 2.0) * cr * xv;
         }
     }
     part = block_sum(part, sh);
