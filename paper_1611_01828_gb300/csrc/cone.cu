@@ -323,22 +323,26 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
     // Newton-Schulz step V <- V (3I - V^T V) / 2 before use
     const bool reorth = use_warm && refresh > 0 && (I.iter % refresh) == (1 % refresh);
 
-    // zero A0 (padding included); V0 = I or the stored basis (both slot-major)
-    for (int idx = lane; idx < CP * CP; idx += G) {
-        const int i = idx / CP, j = idx - (idx / CP) * CP;
-        A0[i * LD + j] = T(0);
-        V0[i * LD + j] = use_warm ? Vst[idx] : ((i == j) ? T(1) : T(0));
+    // The stored basis is read with all of a thread's loads in flight at
+    // once (they are issued before any shared-memory store); zero A0
+    // (padding included) and set V0 = I or the stored basis (slot-major).
+    constexpr int IPT = (CP * CP + G - 1) / G;
+    T vst[IPT];
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+        const int idx = lane + q * G;
+        vst[q] = (use_warm && idx < CP * CP) ? Vst[idx] : T(0);
     }
-    // Gather + rank-one correction, a = s_hat - z, over the lower entries
-    // (packed order e = j - off).  With STASH each thread keeps its entries'
-    // a, H_k xh and v_hat in registers until the rebuild writes s, z, v.
+    // With STASH each thread keeps its lower entries' a, H_k xh and v_hat in
+    // registers until the rebuild writes s, z, v; their first loads are
+    // issued here too.
     int apos[STASH ? EPT : 1];   // arow * LD + bcol; -1: no entry
     unsigned diag_bits = 0u;
     double avs[STASH ? EPT : 1], gxs[STASH ? EPT : 1];
     T vns[STASH ? EPT : 1];
+    int gi[STASH ? EPT : 1];
+    T so[STASH ? EPT : 1], zo[STASH ? EPT : 1], vo[STASH ? EPT : 1];
     if constexpr (STASH) {
-        int gi[EPT];
-        T so[EPT], zo[EPT], vo[EPT];
 #pragma unroll
         for (int q = 0; q < EPT; ++q) {
             const int e = lane + q * G;
@@ -354,6 +358,19 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
                 vo[q] = v[off + e];
             }
         }
+    }
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+        const int idx = lane + q * G;
+        if (idx < CP * CP) {
+            const int i = idx / CP, j = idx - (idx / CP) * CP;
+            A0[i * LD + j] = T(0);
+            V0[i * LD + j] = use_warm ? vst[q] : ((i == j) ? T(1) : T(0));
+        }
+    }
+    // Gather + rank-one correction, a = s_hat - z, over the lower entries
+    // (packed order e = j - off).
+    if constexpr (STASH) {
         gsync<G>(gid);   // A0 zeroed
 #pragma unroll
         for (int q = 0; q < EPT; ++q) {
