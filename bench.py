@@ -225,6 +225,26 @@ def traffic_from_profile(kernel_tag):
 
 
 # ----------------------------------------------------------------------------
+# replicas: one independent instance per rank, no collective on the data path
+# ----------------------------------------------------------------------------
+def reduce_max_over_ranks(values, world, device=None):
+    """Each timing's maximum over the ranks (the slowest replica sets the
+    time of the whole job)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def replica_throughput(world, units_per_rank, seconds):
+    """Whole-job rate: every rank processed `units_per_rank`; `seconds` is the
+    maximum over ranks."""
+    return world * units_per_rank / seconds
+
+
+# ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
 def run_ours(args):
@@ -350,12 +370,9 @@ def run_ours(args):
     batched = None if args.no_batched else batched_leg(args, hsde, torch, dev, stream, timed_steps)
 
     # aggregate over ranks (max time)
-    tt = torch.tensor([mixed_ms, fp64_ms, e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    mixed_ms, fp64_ms, e2e_s = [float(x) for x in tt.tolist()]
-    value = world * args.steps / (mixed_ms / 1e3)
-    fp64_value = world * K64 / (fp64_ms / 1e3)
+    mixed_ms, fp64_ms, e2e_s = reduce_max_over_ranks([mixed_ms, fp64_ms, e2e_s], world, dev)
+    value = replica_throughput(world, args.steps, mixed_ms / 1e3)
+    fp64_value = replica_throughput(world, K64, fp64_ms / 1e3)
 
     # roofline of the dominant phase
     peaks = load_peaks()
@@ -415,7 +432,7 @@ def run_ours(args):
         "jacobi_sweeps": sweep_stats(phases),
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * Ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": L * 8, "d2h_bytes_per_step": L * 8,
+        "e2e": {"value": replica_throughput(world, Ke, e2e_s), "unit": UNIT, "h2d_bytes_per_step": L * 8, "d2h_bytes_per_step": L * 8,
                 "how": "per step: hsde_set_state from pinned host memory, hsde_iterate(1), hsde_get_state to "
                        "pinned host memory (full iterate both ways)"},
         "batched": batched,
@@ -445,7 +462,9 @@ def batched_leg(args, hsde, torch, dev, stream, timed_steps):
     kern = H.hsde_get_profile()["kernels_per_iteration"]
     sizes = list(H.sizes)
     H.close()
-    value = B * K / (ms / 1e3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    (ms,) = reduce_max_over_ranks([ms], world, dev)
+    value = replica_throughput(world, B * K, ms / 1e3)
     avg = {k: (a[0] / a[2], a[1]) for k, a in phases.items() if k not in ("iteration", "_sweeps_mean") and a[2]}
     dom = max(avg, key=lambda k: avg[k][0])
     dom_ms, dom_units = avg[dom]
