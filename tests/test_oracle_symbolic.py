@@ -1,9 +1,10 @@
 """Pins of the oracle's symbolic analysis (Section 2.1-2.2, Section 3.1, Section 4.3).
 
 Each pin comes from outside the oracle: closed-form clique structure of
-block-arrow patterns, a brute-force minimum-degree elimination written here
-from the definition, networkx's chordality test and maximal-clique
-enumeration, and independently measured regression values (golden file).
+block-arrow patterns (golden file), minimum-degree eliminations written here
+from the definition (a brute-force one for small graphs, a heap-based one
+for the 2000-vertex grids), networkx's chordality test and maximal-clique
+enumeration.
 """
 import json
 import os
@@ -117,15 +118,75 @@ def test_block_arrow_shapes(l, d, h):
     assert {frozenset(c.tolist()) for c in st.cliques} == {frozenset(c) for c in synth.block_arrow_cliques(l, d, h)}
 
 
-@pytest.mark.parametrize("R,K,key", [(20, 100, "grid_20x100"), (10, 100, "grid_10x100")])
-def test_grid_regression_values(R, K, key):
-    g = GOLD[key]
-    st = symbolic.analyze(synth.maxcut_grid(R, K, synth.rng_for(1)))
-    sz = [len(c) for c in st.cliques]
-    assert st.p == g["p"] and min(sz) == g["c_min"] and max(sz) == g["c_max"]
-    assert st.n_d == g["n_d"]
-    if "P" in g:
-        assert st.P == g["P"]
+def _heap_md_cliques(n, pairs):
+    """Minimum degree (ties: smallest vertex) on the elimination graph, from
+    the definition, with adjacency sets and a lazily invalidated heap of
+    (degree, vertex); returns the maximal cliques among the candidates
+    {v} U (alive neighbours of v) as sorted tuples."""
+    import heapq
+    adj = [set() for _ in range(n)]
+    for i, j in pairs:
+        if i != j:
+            adj[i].add(j)
+            adj[j].add(i)
+    heap = [(len(adj[v]), v) for v in range(n)]
+    heapq.heapify(heap)
+    done = [False] * n
+    cands = []
+    while heap:
+        d, v = heapq.heappop(heap)
+        if done[v] or d != len(adj[v]):
+            continue
+        nb = sorted(adj[v])
+        done[v] = True
+        cands.append(tuple(sorted(nb + [v])))
+        for u in nb:
+            adj[u].discard(v)
+        for a in range(len(nb)):
+            for b in range(a + 1, len(nb)):
+                x, y = nb[a], nb[b]
+                if y not in adj[x]:
+                    adj[x].add(y)
+                    adj[y].add(x)
+        for u in nb:
+            heapq.heappush(heap, (len(adj[u]), u))
+    # maximal: not a subset of another candidate (a candidate can only lie
+    # inside the candidate of one of its own members)
+    sets = [frozenset(c) for c in cands]
+    by_member = {}
+    for k, c in enumerate(sets):
+        for u in c:
+            by_member.setdefault(u, []).append(k)
+    out = []
+    for k, c in enumerate(sets):
+        if not any(j != k and len(sets[j]) > len(c) and c <= sets[j] for u in c for j in by_member[u]):
+            out.append(cands[k])
+    return out
+
+
+def test_heap_md_matches_brute_force_on_small_graphs():
+    for seed in range(4):
+        n = 12 + seed
+        p = _random_problem(n, 2 * n, 100 + seed)
+        pat = symbolic.aggregate_pattern(p)
+        _, cand = _brute_md(n, pat)
+        brute = {frozenset(c) for c in cand if not any(c < d for d in cand)}
+        assert {frozenset(c) for c in _heap_md_cliques(n, pat)} == brute
+
+
+@pytest.mark.parametrize("R,K", [(20, 100), (10, 100)])
+def test_grid_structure_matches_independent_elimination(R, K):
+    # the max-cut grids of the benchmark workloads: p, clique sizes,
+    # n_d = sum c^2 (Section 3.2) and P = sum c (c + 1) / 2
+    p = synth.maxcut_grid(R, K, synth.rng_for(1))
+    st = symbolic.analyze(p)
+    want = _heap_md_cliques(p.n, symbolic.aggregate_pattern(p))
+    sz = sorted(len(c) for c in want)
+    got = sorted(len(c) for c in st.cliques)
+    assert st.p == len(want) and got == sz
+    assert {tuple(sorted(c.tolist())) for c in st.cliques} == set(want)
+    assert st.n_d == sum(c * c for c in sz)
+    assert st.P == sum(c * (c + 1) // 2 for c in sz)
 
 
 def test_index_maps_and_D():
