@@ -19,6 +19,10 @@ hsde      Section 3 (vectorised decomposed pair, embedding matrix Q) and
           the infeasibility certificates.
 dense     A literal dense (I+Q)^{-1} on tiny instances, used to pin the
           block-eliminated affine step.
+adjoint   Reverse mode through K unrolled iterations (Eqs. Step1-Step3):
+          the adjoint affine solve with the literal I - Q and the
+          Daleckii-Krein derivative of the psd projection; pinned by
+          central differences.
 
 Readings where the paper is silent or garbled are listed in each function's
 docstring; all of them are pinned by tests under ``tests/`` except the ADMM
