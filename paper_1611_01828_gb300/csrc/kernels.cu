@@ -176,14 +176,15 @@ __global__ void __launch_bounds__(NT) k_spmv_At(DevView V, int mode) {
 // ===========================================================================
 // Fused iteration kernels.  Per iteration (after the cone projections of the
 // previous one have produced s, z, v and k_post has produced f):
-//   k_fwd      q = y + omega_tau b - A f; diagonal S: y_w = S^{-1} q
-//   k_solve    dense S: y_w = S^{-1} q                     (only if any S is dense)
-//   k_bwd_eta  x_w = f + Delta^{-1} A^T y_w; the last CTA of each instance
-//              computes eta, tau, kappa, y = y_w - eta y_p and the
-//              constraint-space sums of the stopping rule
-//   k_cone ... per clique bucket, in parallel
-//   k_post     x = x_w - eta x_p; stopping-rule sums; the last CTA of each
-//              instance takes the verdict; f of the next iteration
+//   k_fwd          q = y + omega_tau b - A f; diagonal S: y_w = S^{-1} q
+//   k_solve_dense  dense S: y_w = S^{-1} q                 (only if any S is dense)
+//   k_bwd_eta      x_w = f + Delta^{-1} A^T y_w over nonzero-balanced A^T
+//                  tiles; the last CTA of each instance computes eta, tau
+//                  and kappa
+//   k_cone ...     per clique bucket, in parallel
+//   k_post         x = x_w - eta x_p and y = y_w - eta y_p (a slice of the
+//                  constraints per CTA); all stopping-rule sums; the last CTA
+//                  of each instance takes the verdict; f of the next iteration
 // "Last CTA" is the usual completion-counter pattern: every CTA publishes its
 // partial sums, fences, and increments a per-instance counter; the CTA that
 // sees the final count reduces the partials in tile order.  Nothing waits.
