@@ -93,7 +93,9 @@ while True:
     el = time.perf_counter() - t0
     if (it >= {min_it} and el >= budget) or it >= {max_it}:
         break
-print(json.dumps(dict(iters=it, seconds=el, setup_s=setup_s)))
+st = ref.V.st
+sizes = dict(n=int(p.n), m=int(p.m), p=int(st.p), c_max=int(max(len(c) for c in st.cliques)), N=int(st.N), P=int(st.P))
+print(json.dumps(dict(iters=it, seconds=el, setup_s=setup_s, sizes=sizes)))
 """
 
 
@@ -222,6 +224,13 @@ def traffic_from_profile(kernel_tag):
         return float(tb)
     except ValueError:
         return None
+
+
+def workload_config(n, m, p, c_max, N, P, precision, l2, world):
+    """The `config` of both arms' JSON lines (same keys, same workload)."""
+    return {"workload": WORKLOAD, "n": int(n), "m": int(m), "cliques": int(p), "c_max": int(c_max),
+            "N_pattern_lower": int(N), "P_packed": int(P), "instances_per_gpu": 1, "precision": precision,
+            "l2": l2, "step": "one ADMM iteration incl. stopping-rule check", "parallelism": f"replicas x{world}"}
 
 
 # ----------------------------------------------------------------------------
@@ -418,11 +427,9 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": mixed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded; SDPLIB stand-in)",
-        "config": {"workload": WORKLOAD, "n": sizes.n, "m": sizes.m, "cliques": sizes.p, "c_max": sizes.c_max,
-                   "N_pattern_lower": int(sizes.N), "P_packed": int(sizes.P), "instances_per_gpu": 1,
-                   "precision": "mixed: FP32 cone projections + gather/scatter, FP64 x/y/A/S^-1/reductions",
-                   "l2": "flushed between steps (512 MB write, outside the timed events)",
-                   "step": "one ADMM iteration incl. stopping-rule check", "parallelism": f"replicas x{world}"},
+        "config": workload_config(sizes.n, sizes.m, sizes.p, sizes.c_max, sizes.N, sizes.P,
+                                  "mixed: FP32 cone projections + gather/scatter, FP64 x/y/A/S^-1/reductions",
+                                  "flushed between steps (512 MB write, outside the timed events)", world),
         "fp64_plain": {"value": fp64_value, "unit": UNIT, "ms_per_step": fp64_ms / K64, "steps": K64,
                        "dtype": "f64", "form": "FP64 everywhere, cold-start Jacobi every iteration"},
         "mixed_over_fp64": value / fp64_value,
@@ -524,7 +531,9 @@ def run_reference(args):
     out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * d["seconds"] / d["iters"], "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded; SDPLIB stand-in)",
-           "config": {"workload": WORKLOAD, "step": "one ADMM iteration incl. stopping-rule check"},
+           "config": workload_config(d["sizes"]["n"], d["sizes"]["m"], d["sizes"]["p"], d["sizes"]["c_max"],
+                                     d["sizes"]["N"], d["sizes"]["P"], "FP64 oracle (NumPy/SciPy, one host core)",
+                                     "not applicable (CPU)", world),
            "impl": "reference",
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": f"{d['iters']} oracle iterations after {args.warmup} warm-up iterations "
