@@ -11,6 +11,7 @@
 #include <atomic>
 #include <thread>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -449,6 +450,15 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         h->x_off[b] = Ntot; h->p_off[b] = Ptot; h->m_off[b] = (int32_t)Mtot;
         Ntot += I.N; Ptot += I.P; Mtot += H.m; ncl += H.S.p(); nnzA += (int64_t)H.A_col.size();
         scn += (int64_t)H.sc_idx.size();
+    }
+    // the device index arrays (pattern entries, packed positions, constraint
+    // rows and the CSR offsets of A and A^T) are 32-bit over the whole batch
+    {
+        constexpr int64_t lim = INT32_MAX;
+        if (Ntot > lim || Ptot > lim || Mtot > lim || nnzA > lim || scn > lim || ncl > lim)
+            return fail(HSDE_ERANGE, "batch too large for 32-bit indices: N = " + std::to_string(Ntot) +
+                                         ", P = " + std::to_string(Ptot) + ", m = " + std::to_string(Mtot) +
+                                         ", nnz(A) = " + std::to_string(nnzA));
     }
     std::vector<int64_t> hvso;
     int64_t vsn = 0;
