@@ -68,7 +68,15 @@ def dk_vjp(A, Gbar):
     return V @ (_dk_gamma(lam) * B) @ V.T
 
 
+def _check_literal(hs):
+    # the derivative is taken through the literal Eqs. Step1-Step3 on the
+    # original data: no relaxation, no scaling (whose factors depend on b, c)
+    if hs.alpha != 1.0 or hs.scaled:
+        raise ValueError("reverse mode needs HSDE(..., alpha=1, scaling=False)")
+
+
 def sparse_Q(hs):
+    _check_literal(hs)
     V = hs.V
     A, H = V.A, V.H
     nF, nd, m = hs.nF, hs.nd, hs.m
@@ -86,6 +94,7 @@ def sparse_Q(hs):
 
 
 def objective(hs, K):
+    _check_literal(hs)
     u, nu = hs.initial()
     for _ in range(K):
         u, nu, _ = hs.step(u, nu)
@@ -101,6 +110,7 @@ def gradient(hs, K, seed=None):
     With `seed = (xbar, ybar, taubar, kappabar)`: the gradient of
     <xbar, x_K> + <ybar, y_K> + taubar tau_K + kappabar kappa_K instead
     (f returned as that value)."""
+    _check_literal(hs)
     nF, nd, m = hs.nF, hs.nd, hs.m
     dim = hs.dim
     Q = sparse_Q(hs)

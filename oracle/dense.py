@@ -12,10 +12,10 @@ import numpy as np
 
 def build_Q(hs):
     """Q = [[0,0,-A^T,-H^T,c],[0,0,0,I,0],[A,0,0,0,-b],[H,-I,0,0,0],[-c^T,0,b^T,0,0]]
-    in the variable order u = (x, s, y, v, tau)."""
-    V = hs.V
-    A = V.A.toarray()
-    H = V.H.toarray()
+    in the variable order u = (x, s, y, v, tau), with the data the iteration
+    uses (hs.A, hs.b, hs.c: scaled when the oracle scales, reading P7)."""
+    A = hs.A.toarray()
+    H = hs.V.H.toarray()
     nF, nd, m = hs.nF, hs.nd, hs.m
     ix = slice(0, nF)
     is_ = slice(nF, nF + nd)
@@ -25,14 +25,14 @@ def build_Q(hs):
     Q = np.zeros((hs.dim, hs.dim))
     Q[ix, iy] = -A.T
     Q[ix, iv] = -H.T
-    Q[ix, it] = V.c
+    Q[ix, it] = hs.c
     Q[is_, iv] = np.eye(nd)
     Q[iy, ix] = A
-    Q[iy, it] = -V.b
+    Q[iy, it] = -hs.b
     Q[iv, ix] = H
     Q[iv, is_] = -np.eye(nd)
-    Q[it, ix] = -V.c
-    Q[it, iy] = V.b
+    Q[it, ix] = -hs.c
+    Q[it, iy] = hs.b
     return Q
 
 
@@ -43,5 +43,6 @@ def affine_dense(hs, omega, Q=None):
 
 def step_dense(hs, u, nu, Q):
     uhat = affine_dense(hs, u + nu, Q)
-    u_new = hs.project_K(uhat - nu)
-    return u_new, nu - uhat + u_new, uhat
+    urel = hs.alpha * uhat + (1.0 - hs.alpha) * u
+    u_new = hs.project_K(urel - nu)
+    return u_new, nu - urel + u_new, uhat

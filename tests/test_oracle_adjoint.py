@@ -42,7 +42,7 @@ def test_dk_vjp_matches_finite_differences():
 
 
 def test_sparse_Q_equals_dense_Q():
-    hs = hsde.HSDE(synth.block_arrow_n50())
+    hs = hsde.HSDE(synth.block_arrow_n50(), alpha=1.0, scaling=False)
     assert np.array_equal(adjoint.sparse_Q(hs).toarray(), dense.build_Q(hs))
 
 
@@ -55,9 +55,9 @@ def test_unrolled_gradient_matches_central_differences(case):
     else:
         p0 = synth.block_arrow(3, 3, 2, 5, np.random.default_rng(2), kappa=30.0, assign="roundrobin")
         K = 30
-    st = hsde.HSDE(p0).V.st
+    st = hsde.HSDE(p0, alpha=1.0, scaling=False).V.st
     p = _C_on_pattern(p0, st)
-    hs = hsde.HSDE(p)
+    hs = hsde.HSDE(p, alpha=1.0, scaling=False)
     f, cbar, bbar = adjoint.gradient(hs, K)
     assert f == pytest.approx(adjoint.objective(hs, K), rel=1e-12)
     G = adjoint.grad_C_lower(hs, cbar)
@@ -66,8 +66,8 @@ def test_unrolled_gradient_matches_central_differences(case):
         dC = rng.standard_normal(st.N)
         db = rng.standard_normal(p.m)
         h = 1e-6
-        fp = adjoint.objective(hsde.HSDE(_perturbed(p, dC, db, h)), K)
-        fm = adjoint.objective(hsde.HSDE(_perturbed(p, dC, db, -h)), K)
+        fp = adjoint.objective(hsde.HSDE(_perturbed(p, dC, db, h), alpha=1.0, scaling=False), K)
+        fm = adjoint.objective(hsde.HSDE(_perturbed(p, dC, db, -h), alpha=1.0, scaling=False), K)
         fd = (fp - fm) / (2 * h)
         an = float(np.sum(w * G * dC) + bbar @ db)
         assert abs(fd - an) <= 1e-5 * (1 + abs(fd)), (fd, an)

@@ -104,3 +104,46 @@ def test_transposed_clique_block(monkeypatch):
     monkeypatch.setattr(hsde.HSDE, "project_S", orig)
     want = hs.project_S(s)
     assert np.linalg.norm(got - want) > 1e-3
+
+
+def test_unscaling_without_the_row_scaling(monkeypatch):
+    """Forgetting D when mapping the scaled y back (y = y~/rho instead of
+    D y~/rho) must break the hand-built optimum's verdict."""
+    import tests.test_oracle_solve as tos
+    def bad(self, u, nu):
+        x, s, y, _, tau = self.split(u)
+        z = nu[self.nF:self.nF + self.nd]
+        return (x / self.sigma, s / self.sigma, y / self.rho, z / self.rho, tau, float(nu[-1]))
+    p, Cm = tos._dense_trace_one(4, 3)
+    hs = hsde.HSDE(p)
+    assert not np.allclose(hs.d, 1.0)
+    lam, V = np.linalg.eigh(Cm)
+    X = np.outer(V[:, 0], V[:, 0]); Z = Cm - lam[0] * np.eye(4)
+    vec = lambda M: np.array([M[i, j] for (i, j) in hs.V.ent])
+    x, s, y, v, z = tos._to_scaled(hs, vec(X), hs.V.H @ vec(X), np.array([lam[0]]), hs.V.H @ vec(Z),
+                                   hs.V.H @ vec(Z))
+    u = np.concatenate([x, s, y, v, [1.0]])
+    nu = np.concatenate([np.zeros(hs.nF), z, [0.0], np.zeros(hs.nd), [0.0]])
+    assert hs.verdict(hs.residuals(u, nu), 1e-4) == hsde.SOLVED
+    monkeypatch.setattr(hsde.HSDE, "unscale", bad)
+    assert hs.verdict(hs.residuals(u, nu), 1e-4) != hsde.SOLVED
+
+
+def test_relaxation_missing_in_the_dual_update(monkeypatch):
+    """nu <- nu - u_hat + u_new (the relaxed point left out of Eq. Step3)
+    must not solve the closed-form trace-one problem."""
+    import tests.test_oracle_solve as tos
+    def bad_step(self, u, nu):
+        uhat = self.affine(u + nu)
+        urel = self.alpha * uhat + (1.0 - self.alpha) * u
+        u_new = self.project_K(urel - nu)
+        return u_new, nu - uhat + u_new, uhat
+    p, Cm = tos._dense_trace_one(5, 4)
+    lam_min = np.linalg.eigvalsh(Cm).min()
+    monkeypatch.setattr(hsde.HSDE, "step", bad_step)
+    try:
+        with np.errstate(all="ignore"):
+            res = hsde.HSDE(p, alpha=1.8).solve(eps=1e-7, max_iter=5000)
+    except np.linalg.LinAlgError:
+        return                                              # diverged: caught
+    assert not (res.status == hsde.SOLVED and abs(res.info["pobj"] - lam_min) <= 1e-4 * max(1.0, abs(lam_min)))

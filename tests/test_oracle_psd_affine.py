@@ -105,7 +105,11 @@ def test_affine_matches_dense_solve(prob):
     p = {"tiny": lambda: _tiny(), "tiny_dense": lambda: _tiny(dense_constraints=True, seed=3),
          "arrow_n50": synth.block_arrow_n50, "arrow_n50_inf": lambda: synth.block_arrow_n50(True),
          "grid": lambda: synth.maxcut_grid(3, 4, np.random.default_rng(2))}[prob]()
-    hs = hsde.HSDE(p)
+    for scaling in (False, True):
+        _affine_vs_dense(hsde.HSDE(p, scaling=scaling))
+
+
+def _affine_vs_dense(hs):
     Q = dense.build_Q(hs)
     rng = np.random.default_rng(11)
     for _ in range(3):
@@ -119,7 +123,7 @@ def test_third_block_elimination_matrix():
     """Eq. ThirdBlkElm is I + Ahat^T Ahat (not I + Ahat Ahat^T): reading P2."""
     hs = hsde.HSDE(_tiny(m=3))
     Ah = hs.Ahat.toarray()
-    A = hs.V.A.toarray(); H = hs.V.H.toarray()
+    A = hs.A.toarray(); H = hs.V.H.toarray()      # the (scaled) data the iteration uses
     D = np.diag(hs.D)
     nd = hs.nd
     blk = np.block([[np.eye(hs.nF) + D + A.T @ A, -H.T], [-H, 2 * np.eye(nd)]])
@@ -131,9 +135,10 @@ def test_third_block_elimination_matrix():
     assert np.allclose(hs.solve_factor(g), np.linalg.solve(M, g), atol=1e-12)
 
 
-def test_dense_iterates_match_eliminated_iterates():
+@pytest.mark.parametrize("alpha,scaling", [(1.0, False), (1.8, True)])
+def test_dense_iterates_match_eliminated_iterates(alpha, scaling):
     p = synth.block_arrow_n50()
-    hs = hsde.HSDE(p)
+    hs = hsde.HSDE(p, alpha=alpha, scaling=scaling)
     Q = dense.build_Q(hs)
     u, nu = hs.initial()
     u2, nu2 = u.copy(), nu.copy()
