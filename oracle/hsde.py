@@ -34,9 +34,15 @@ Follows the paper step by step:
     dres = ||A^T yb + H^T zb - c|| / (1 + ||c||)
     gap  = |c^T xb - b^T yb| / (1 + |c^T xb| + |b^T yb|)
   SOLVED iff tau > 0 and all three <= eps; else PRIMAL_INFEASIBLE iff
-  b^T y > 0 and ||A^T y + H^T z|| / b^T y <= eps; else DUAL_INFEASIBLE iff
-  c^T x < 0 and ||(A x, H x - s)|| / (-c^T x) <= eps.  Checked after every
+  b^T y > 0 and ||A^T y + H^T z|| / b^T y <= eps and the two terms cancel,
+  ||A^T y + H^T z|| <= CERT_CANCEL (||A^T y|| + ||H^T z||); else
+  DUAL_INFEASIBLE iff c^T x < 0 and ||(A x, H x - s)|| / (-c^T x) <= eps and
+  ||(A x, H x - s)|| <= CERT_CANCEL (||H x|| + ||s||).  Checked after every
   ``check_every``-th iteration; MAX_ITER when max_iter is reached.
+  The cancellation condition is part of the reading: the ratio alone is not
+  invariant to the scale of b (or c), and on block-arrows whose b is large
+  (||b|| ~ 5e5) the first iterate, with tau already 0, has a ratio of 9e-5
+  although the instance is feasible; its two terms do not cancel at all.
 * Reading P7 (the paper applies the cited ADMM of O'Donoghue et al.
   "directly" and says nothing of its practical variants): optional
   over-relaxation and data scaling, both switched by arguments.
@@ -76,6 +82,8 @@ STATUS_NAMES = {0: "running", 1: "solved", 2: "primal_infeasible", 3: "dual_infe
 ALPHA = 1.8
 SCALE_NORM = 10.0
 DUAL_WEIGHT = 1.5
+# certificates must also cancel to this fraction of their terms (reading P6)
+CERT_CANCEL = 1e-2
 
 
 class Vectorised:
@@ -367,14 +375,19 @@ class HSDE:
             info.update(pres=np.inf, dres=np.inf, gap=np.inf, pobj=np.nan, dobj=np.nan)
         info["pinf_ratio"] = (np.linalg.norm(Aty_Htz) / bty) if bty > 0 else np.inf
         info["dinf_ratio"] = (np.sqrt(np.sum(Ax ** 2) + np.sum(Hx_s ** 2)) / (-ctx)) if ctx < 0 else np.inf
+        # how far the two terms of each certificate cancel (scale-free)
+        den_p = np.linalg.norm(A.T @ y) + np.linalg.norm(H.T @ z)
+        den_d = np.linalg.norm(H @ x) + np.linalg.norm(s)
+        info["pinf_cancel"] = np.linalg.norm(Aty_Htz) / den_p if den_p > 0 else np.inf
+        info["dinf_cancel"] = np.sqrt(np.sum(Ax ** 2) + np.sum(Hx_s ** 2)) / den_d if den_d > 0 else np.inf
         return info
 
     def verdict(self, info, eps):
         if info["tau"] > 0 and info["pres"] <= eps and info["dres"] <= eps and info["gap"] <= eps:
             return SOLVED
-        if info["bty"] > 0 and info["pinf_ratio"] <= eps:
+        if info["bty"] > 0 and info["pinf_ratio"] <= eps and info["pinf_cancel"] <= CERT_CANCEL:
             return PRIMAL_INFEASIBLE
-        if info["ctx"] < 0 and info["dinf_ratio"] <= eps:
+        if info["ctx"] < 0 and info["dinf_ratio"] <= eps and info["dinf_cancel"] <= CERT_CANCEL:
             return DUAL_INFEASIBLE
         return RUNNING
 

@@ -249,3 +249,18 @@ def test_relaxed_scaled_and_literal_forms_reach_the_same_point(name):
         for (y, Z) in (ca, cb):
             assert a.V.b @ y == pytest.approx(1.0)
             assert np.linalg.norm(a.V.A.T @ y + Z) <= 1e-6
+
+
+def test_no_certificate_from_a_first_iterate_that_does_not_cancel():
+    """Reading P6's cancellation condition: on the l = 500 block-arrow (feasible
+    by construction, ||b|| ~ 5e5) the first iterate already has tau = 0 and
+    ||A^T y + H^T z|| / b^T y below 1e-4, but A^T y and H^T z do not cancel;
+    the ratio alone would call the instance primal infeasible."""
+    hs = hsde.HSDE(synth.block_arrow_sweep(500, 10))
+    u, nu = hs.initial()
+    u, nu, _ = hs.step(u, nu)
+    info = hs.residuals(u, nu)
+    assert info["tau"] == 0.0 and info["bty"] > 0
+    assert info["pinf_ratio"] <= 1e-4                   # the ratio alone passes
+    assert info["pinf_cancel"] > 0.1                    # the terms do not cancel
+    assert hs.verdict(info, 1e-4) == hsde.RUNNING
