@@ -23,7 +23,11 @@
  *   state     [x (N) | s (P) | y (m) | v (P) | tau | z (P) | kappa]
  *             = (x, s, y, v, tau) of u and (z, kappa) of nu (Section 3.2;
  *             the free-cone parts h, r, w of nu are identically zero from the
- *             standard start, Eq. Step3, and are not stored).
+ *             standard start, Eq. Step3, and are not stored).  With data
+ *             scaling on (hsde_options.scaling) the state is that of the
+ *             scaled problem: x~ = sigma x, s~ = sigma s, y~ = rho D^{-1} y,
+ *             v~ = rho v, z~ = rho z; the solution and certificate queries
+ *             return unscaled values.
  * Inner products and norms are those of the full column-stack vec: entries
  * off the diagonal count twice.
  *
@@ -109,7 +113,19 @@ typedef struct hsde_options {
                              Newton-Schulz step V <- V (3I - V^T V)/2 against
                              the rounding drift of their orthogonality,
                              default 32                                        */
-    int32_t _pad;
+    int32_t scaling;      /* data scaling (the practical form of the cited
+                             ADMM, not specified by the paper): 1 (default) runs
+                             on A~ = D A (unit-norm constraint rows),
+                             b~ = sigma D b, c~ = rho c with one factor
+                             sigma = scale_norm / max(||D b||, ||c||) and
+                             rho = dual_weight * sigma; 0 runs on the data as
+                             given.  The stopping rule is always evaluated on
+                             the unscaled iterate against the original data. */
+    double  alpha;        /* over-relaxation: the cone step projects
+                             alpha u_hat + (1 - alpha) u - nu; in (0, 2),
+                             default 1.8; 1 is the literal Eqs. Step1-Step3   */
+    double  scale_norm;   /* target norm of the scaled b~ and c~, default 10   */
+    double  dual_weight;  /* extra factor of rho over sigma, default 1.5       */
 } hsde_options;
 
 typedef struct hsde_sizes {
@@ -132,6 +148,10 @@ typedef struct hsde_info {
     double  pinf_ratio, dinf_ratio;  /* certificate ratios (reading P6)          */
     double  setup_ms;     /* host + device setup ("Pre- time" of Tables 2-4)    */
     double  iterate_ms;   /* wall time spent inside hsde_iterate               */
+    int32_t jacobi_unconverged;  /* cliques whose eigensolve stopped at
+                                    jacobi_max_sweeps above jacobi_tol in the
+                                    last iteration (0 in a healthy run)      */
+    int32_t jacobi_unconverged_iterations;  /* iterations with at least one  */
 } hsde_info;
 
 #define HSDE_MAX_PHASES 16
@@ -278,9 +298,10 @@ HSDE_API int  hsde_spd_inverse_noalloc(double* S, int32_t m, void* cuda_stream);
 
 /* Replace the data c = C (N pattern values, lower CSC order) and b (m values)
  * of instance i, keeping the pattern, the constraint matrices and the cached
- * factor S (which does not depend on c or b); M^{-1} zeta and
- * 1 + zeta^T M^{-1} zeta (Eq. MatrixInverseResult) are recomputed.  The
- * iterate is left as it is.  Errors: HSDE_EINVAL (null or non-finite). */
+ * factor S (which does not depend on c or b); the scaling factors sigma and
+ * rho, M^{-1} zeta and 1 + zeta^T M^{-1} zeta (Eq. MatrixInverseResult) are
+ * recomputed.  The iterate is left as it is.  Errors: HSDE_EINVAL (null or
+ * non-finite). */
 HSDE_API int  hsde_set_data(hsde_handle* h, int32_t i, const double* c, const double* b);
 
 /* Unrolled differentiation (single-instance handles).  hsde_unrolled_forward
@@ -297,7 +318,10 @@ HSDE_API int  hsde_set_data(hsde_handle* h, int32_t i, const double* c, const do
  * adjoint solve (I+Q)^{-T} = (I-Q)^{-1} with the same cached factor.  Each
  * checkpoint segment is recomputed once to record its eigendecompositions.
  * Not in the paper.  Afterwards the handle's iterate is undefined (use
- * hsde_set_state).  Errors: HSDE_EINVAL (B != 1, K or ckpt < 1),
+ * hsde_set_state).  The handle must run the literal iteration on the data
+ * as given (options alpha = 1 and scaling = 0): the scaling factors depend
+ * on c and b.  Errors: HSDE_EINVAL (B != 1, K or ckpt < 1, alpha != 1 or
+ * scaling on),
  * HSDE_ESTATE (backward without forward), HSDE_ENOMEM, HSDE_ECUDA. */
 HSDE_API int  hsde_unrolled_forward(hsde_handle* h, int32_t K, int32_t ckpt, double* x, double* y,
                                     double* tau, double* kappa);

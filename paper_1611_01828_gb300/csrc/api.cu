@@ -63,12 +63,39 @@ struct HostPrep {
     std::vector<int32_t> At_ptr, At_col;      // local constraint indices
     std::vector<double> At_val;
     std::vector<double> b;
+    // data scaling (hsde_options.scaling): A~ = D A, b~ = sigma D b, c~ = rho c
+    std::vector<double> dscale;               // d_i (1 when not scaling)
+    double sigma = 1.0, rho = 1.0;
+    double bnorm = 0.0, cnorm = 0.0;          // ||b||, ||c|| of the original data
     bool dense = false;
     std::vector<double> Sdense;               // m*m (dense case)
     std::vector<double> Sdiag_inv;            // m (diagonal case)
 };
 
-int prepare(const hsde_problem* P, HostPrep& H, std::string& err) {
+// Scaling factors of one instance from its ORIGINAL data (the practical form
+// of the cited ADMM; the paper applies it without saying how): sigma and rho
+// from max(||D b||, ||c||), where D b is the row-normalised b.
+void scale_factors(const HostPrep& H, const double* b, const double* c, const hsde_options& O, double& sigma,
+                   double& rho, double& bnorm, double& cnorm) {
+    double nb = 0.0, bb = 0.0, cc = 0.0;
+    for (int32_t i = 0; i < H.m; ++i) {
+        const double db = H.dscale[i] * b[i];
+        nb += db * db;
+        bb += b[i] * b[i];
+    }
+    for (size_t e = 0; e < H.diag.size(); ++e) cc += (H.diag[e] ? 1.0 : 2.0) * c[e] * c[e];
+    bnorm = std::sqrt(bb);
+    cnorm = std::sqrt(cc);
+    sigma = rho = 1.0;
+    if (!O.scaling) return;
+    const double mx = std::max(std::sqrt(nb), cnorm);
+    if (mx > 0.0) {
+        sigma = O.scale_norm / mx;
+        rho = O.dual_weight * O.scale_norm / mx;
+    }
+}
+
+int prepare(const hsde_problem* P, const hsde_options& O, HostPrep& H, std::string& err) {
     int rc = build_symbolic(P, H.S, err);
     if (rc != HSDE_OK) return rc;
     const Symbolic& S = H.S;
@@ -98,18 +125,24 @@ int prepare(const hsde_problem* P, HostPrep& H, std::string& err) {
         std::vector<int32_t> fill(H.sc_ptr.begin(), H.sc_ptr.end() - 1);
         for (size_t j = 0; j < S.gather.size(); ++j) H.sc_idx[fill[S.gather[j]]++] = (int32_t)j;
     }
-    // A (rows = constraints) with full-vec weights, and A^T (rows = entries)
+    // A (rows = constraints) with full-vec weights, and A^T (rows = entries);
+    // with scaling, every row i is multiplied by d_i = 1 / ||A_i|| (full-vec)
     const int32_t m = P->m;
     H.A_ptr.assign(m + 1, 0);
+    H.dscale.assign(m, 1.0);
     const int64_t a0 = m > 0 ? P->A_ptr[0] : 0;
     std::vector<std::pair<int32_t, double>> row;
     for (int32_t i = 0; i < m; ++i) {
         row.clear();
+        double nrm = 0.0;
         for (int64_t k = P->A_ptr[i] - a0; k < P->A_ptr[i + 1] - a0; ++k) {
             const int32_t r = P->A_row[k], c = P->A_col[k];
             const int32_t e = S.pos(r, c);
             row.push_back({e, P->A_val[k]});
+            nrm += (r == c ? 1.0 : 2.0) * P->A_val[k] * P->A_val[k];
         }
+        if (O.scaling && nrm > 0.0) H.dscale[i] = 1.0 / std::sqrt(nrm);
+        for (auto& pr : row) pr.second *= H.dscale[i];
         std::sort(row.begin(), row.end(),
                   [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
                       return a.first < b.first;
@@ -138,7 +171,11 @@ int prepare(const hsde_problem* P, HostPrep& H, std::string& err) {
             }
         for (int64_t e = 0; e < N; ++e) max_at = std::max(max_at, H.At_ptr[e + 1] - H.At_ptr[e]);
     }
-    H.b.assign(P->b, P->b + m);
+    // b~ = sigma D b, c~ = rho c (the factors from the original data)
+    scale_factors(H, P->b, H.cvec.data(), O, H.sigma, H.rho, H.bnorm, H.cnorm);
+    H.b.resize(m);
+    for (int32_t i = 0; i < m; ++i) H.b[i] = H.sigma * H.dscale[i] * P->b[i];
+    for (double& cv : H.cvec) cv *= H.rho;
     // S = I + A Delta^{-1} A^T (full-vec inner products); diagonal if no two
     // constraints share a pattern entry.
     H.dense = max_at > 1;
@@ -374,7 +411,10 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     if (O) opt = *O;
     if (!(opt.eps_tol > 0) || opt.max_iter <= 0 || opt.check_every <= 0 ||
         (opt.precision != HSDE_FP64 && opt.precision != HSDE_MIXED) || opt.jacobi_max_sweeps < 0 ||
-        opt.jacobi_tol < 0 || opt.warm_start < -1 || opt.warm_start > 1 || opt.warm_refresh < 0)
+        opt.jacobi_tol < 0 || opt.warm_start < -1 || opt.warm_start > 1 || opt.warm_refresh < 0 ||
+        (opt.scaling != 0 && opt.scaling != 1) || !(opt.alpha > 0.0 && opt.alpha < 2.0) ||
+        !(opt.scale_norm > 0.0) || !(opt.dual_weight > 0.0) || !std::isfinite(opt.scale_norm) ||
+        !std::isfinite(opt.dual_weight))
         return fail(HSDE_EINVAL, "invalid options");
 
     auto* h = new hsde_handle();
@@ -404,7 +444,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
                 const int32_t b = next.fetch_add(1);
                 if (b >= B) return;
                 try {
-                    rcs[b] = prepare(&P[b], h->prep[b], errs[b]);
+                    rcs[b] = prepare(&P[b], opt, h->prep[b], errs[b]);
                 } catch (const std::bad_alloc&) {
                     rcs[b] = HSDE_ENOMEM;
                     errs[b] = "host allocation failed";
@@ -447,15 +487,17 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         I.status = HSDE_RUNNING;
         I.vcold = 1;
         I.tau = 1.0; I.kappa = 1.0;
+        I.sigma = H.sigma; I.rho = H.rho; I.bnorm = H.bnorm; I.cnorm = H.cnorm;
         h->x_off[b] = Ntot; h->p_off[b] = Ptot; h->m_off[b] = (int32_t)Mtot;
         Ntot += I.N; Ptot += I.P; Mtot += H.m; ncl += H.S.p(); nnzA += (int64_t)H.A_col.size();
         scn += (int64_t)H.sc_idx.size();
     }
     // the device index arrays (pattern entries, packed positions, constraint
-    // rows and the CSR offsets of A and A^T) are 32-bit over the whole batch
+    // rows and the CSR offsets of A and A^T) are 32-bit over the whole batch;
+    // the warp-per-row kernels index rows * 32 threads in 32 bits
     {
         constexpr int64_t lim = INT32_MAX;
-        if (Ntot > lim || Ptot > lim || Mtot > lim || nnzA > lim || scn > lim || ncl > lim)
+        if (Ntot > lim || Ptot > lim || Mtot > lim / 32 || nnzA > lim || scn > lim || ncl > lim / 32)
             return fail(HSDE_ERANGE, "batch too large for 32-bit indices: N = " + std::to_string(Ntot) +
                                          ", P = " + std::to_string(Ptot) + ", m = " + std::to_string(Mtot) +
                                          ", nnz(A) = " + std::to_string(nnzA));
@@ -511,12 +553,13 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     const size_t o_vst = cv.take<char>(vsn * Tsz), o_vso = cv.take<int64_t>(hvso.size());
     const size_t o_g = cv.take<int32_t>(Ptot), o_clo = cv.take<int32_t>(ncl), o_cls = cv.take<int32_t>(ncl),
                  o_cli = cv.take<int32_t>(ncl), o_inst = cv.take<InstDev>(B), o_tiles = cv.take<int4>(ntiles),
-                 o_part = cv.take<double>(ntiles * KPART), o_clp = cv.take<double>(ncl),
+                 o_part = cv.take<double>(ntiles * KPART), o_clp = cv.take<double>(2 * ncl),
                  o_att = cv.take<int4>(hat.size()), o_atpart = cv.take<double>(hat.size()),
                  o_clsw = cv.take<int32_t>(ncl),
                  o_blist = cv.take<int32_t>(ncl),
                  o_rowb = cv.take<double>(Mtot), o_cnt = cv.take<int>(2 * (size_t)B),
-                 o_af = cv.take<double>(Mtot), o_atyw = cv.take<double>(Ntot), o_atyp = cv.take<double>(Ntot);
+                 o_af = cv.take<double>(Mtot), o_atyw = cv.take<double>(Ntot), o_atyp = cv.take<double>(Ntot),
+                 o_dinv2 = cv.take<double>(Mtot), o_ax = cv.take<double>(Mtot), o_aty = cv.take<double>(Ntot);
     // Gauss-Jordan scratch and per-dense-instance tables
     int ndense = 0;
     int32_t mmax = 0;
@@ -557,10 +600,14 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     V.atyw = (double*)(ar + o_atyw);
     V.atyp = (double*)(ar + o_atyp);
     V.counters = (int*)(ar + o_cnt);
+    V.dinv2 = (const double*)(ar + o_dinv2);
+    V.ax = (double*)(ar + o_ax);
+    V.aty = (double*)(ar + o_aty);
     V.eps = opt.eps_tol; V.max_iter = opt.max_iter; V.check_every = opt.check_every;
+    V.alpha = opt.alpha;
 
     // ---- concatenated host buffers with absolute indices ----
-    std::vector<double> hc, hid, hAtv, hb, hAv, hsd;
+    std::vector<double> hc, hid, hAtv, hb, hAv, hsd, hdinv2;
     std::vector<uint8_t> hdiag;
     std::vector<int32_t> hscp, hsci, hatp, hatc, hap, hac, hri, hg, hclo, hcls, hcli;
     std::vector<int4> htiles;
@@ -589,6 +636,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         for (int32_t e : H.A_col) hac.push_back((int32_t)(xo + e));
         hAv.insert(hAv.end(), H.A_val.begin(), H.A_val.end());
         hb.insert(hb.end(), H.b.begin(), H.b.end());
+        for (int32_t i = 0; i < H.m; ++i) hdinv2.push_back(1.0 / (H.dscale[i] * H.dscale[i]));
         if (!H.dense)
             for (int32_t i = 0; i < H.m; ++i) hsd[mo + i] = H.Sdiag_inv[i];
         for (int32_t e : H.S.gather) hg.push_back((int32_t)(xo + e));
@@ -611,7 +659,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     UP(o_c, hc); UP(o_id, hid); UP(o_diag, hdiag); UP(o_scp, hscp); UP(o_sci, hsci);
     UP(o_atp, hatp); UP(o_atc, hatc); UP(o_atv, hAtv); UP(o_b, hb); UP(o_ap, hap); UP(o_ac, hac);
     UP(o_av, hAv); UP(o_ri, hri); UP(o_sd, hsd); UP(o_g, hg); UP(o_clo, hclo); UP(o_cls, hcls);
-    UP(o_cli, hcli); UP(o_vso, hvso);
+    UP(o_cli, hcli); UP(o_vso, hvso); UP(o_dinv2, hdinv2);
     {
         std::vector<InstDev> iv(inst);
         CK(cudaMemcpyAsync(ar + o_inst, iv.data(), sizeof(InstDev) * B, cudaMemcpyHostToDevice, st));
@@ -739,6 +787,10 @@ void hsde_default_options(hsde_options* o) {
     o->profile = 0;
     o->warm_start = -1;
     o->warm_refresh = 0;
+    o->scaling = 1;
+    o->alpha = 1.8;
+    o->scale_norm = 10.0;
+    o->dual_weight = 1.5;
 }
 
 const char* hsde_last_error(void) { return g_err.c_str(); }
@@ -881,6 +933,8 @@ int hsde_get_info(hsde_handle* h, int32_t i, hsde_info* out) {
     out->pobj = I.pobj; out->dobj = I.dobj; out->tau = I.tau; out->kappa = I.kappa;
     out->pinf_ratio = I.pinf; out->dinf_ratio = I.dinf;
     out->setup_ms = h->setup_ms; out->iterate_ms = h->iterate_ms;
+    out->jacobi_unconverged = I.unconv_last;
+    out->jacobi_unconverged_iterations = I.unconv_iters;
     return HSDE_OK;
 }
 
@@ -973,6 +1027,13 @@ int hsde_set_state(hsde_handle* h, int32_t i, const double* state, int32_t itera
     h->need_rhs = true;
     CK(cudaMemcpy(h->V.inst + i, &I, sizeof(InstDev), cudaMemcpyHostToDevice));
     h->host_inst[i] = I;
+    // the over-relaxation carries A x and A^T y of the iterate from one
+    // iteration to the next; form them for the loaded one
+    if (h->V.alpha != 1.0) {
+        launch_state_products(h->V, h->m_off[i], h->m_off[i] + m, h->x_off[i], h->x_off[i] + N, h->st);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(h->st));
+    }
     return HSDE_OK;
 }
 
@@ -987,19 +1048,20 @@ int hsde_get_solution(hsde_handle* h, int32_t i, double* X, double* y, double* Z
     const HostPrep& H = h->prep[i];
     const int64_t N = H.S.N(), P = H.S.P();
     const double tau = I.tau;
+    // unscaled: X = x~/(sigma tau), y = D y~/(rho tau), Z = H^T z~/(rho tau)
     if (X) {
         CK(cudaMemcpy(X, h->V.x + h->x_off[i], sizeof(double) * N, cudaMemcpyDeviceToHost));
-        for (int64_t e = 0; e < N; ++e) X[e] /= tau;
+        for (int64_t e = 0; e < N; ++e) X[e] /= I.sigma * tau;
     }
     if (y && H.m) {
         CK(cudaMemcpy(y, h->V.y + h->m_off[i], sizeof(double) * H.m, cudaMemcpyDeviceToHost));
-        for (int32_t j = 0; j < H.m; ++j) y[j] /= tau;
+        for (int32_t j = 0; j < H.m; ++j) y[j] = H.dscale[j] * y[j] / (I.rho * tau);
     }
     if (Z) {
         std::vector<double> zp(P);
         if ((rc = get_packed(h, h->V.z, i, zp.data())) != HSDE_OK) return rc;
         scatter_host(H, zp.data(), Z);
-        for (int64_t e = 0; e < N; ++e) Z[e] /= tau;
+        for (int64_t e = 0; e < N; ++e) Z[e] /= I.rho * tau;
     }
     if (pobj) *pobj = I.pobj;
     if (dobj) *dobj = I.dobj;
@@ -1016,23 +1078,25 @@ int hsde_get_certificate(hsde_handle* h, int32_t i, int32_t kind, double* y, dou
         return fail(HSDE_ESTATE, "instance verdict does not match the certificate kind");
     const HostPrep& H = h->prep[i];
     const int64_t N = H.S.N(), P = H.S.P();
+    // I.bty = b^T y and I.ctx = c^T x of the unscaled homogeneous iterate
+    // (y = D y~/rho, z = z~/rho, x = x~/sigma)
     if (kind == HSDE_PRIMAL_INFEASIBLE) {
         const double bty = I.bty;
         if (y && H.m) {
             CK(cudaMemcpy(y, h->V.y + h->m_off[i], sizeof(double) * H.m, cudaMemcpyDeviceToHost));
-            for (int32_t j = 0; j < H.m; ++j) y[j] /= bty;
+            for (int32_t j = 0; j < H.m; ++j) y[j] = H.dscale[j] * y[j] / I.rho / bty;
         }
         if (Z) {
             std::vector<double> zp(P);
             if ((rc = get_packed(h, h->V.z, i, zp.data())) != HSDE_OK) return rc;
             scatter_host(H, zp.data(), Z);
-            for (int64_t e = 0; e < N; ++e) Z[e] /= bty;
+            for (int64_t e = 0; e < N; ++e) Z[e] = Z[e] / I.rho / bty;
         }
     } else {
         const double nctx = -I.ctx;
         if (X) {
             CK(cudaMemcpy(X, h->V.x + h->x_off[i], sizeof(double) * N, cudaMemcpyDeviceToHost));
-            for (int64_t e = 0; e < N; ++e) X[e] /= nctx;
+            for (int64_t e = 0; e < N; ++e) X[e] = X[e] / I.sigma / nctx;
         }
     }
     return HSDE_OK;
@@ -1184,6 +1248,8 @@ int reset_standard_start(hsde_handle* h) {
     CK(cudaMemsetAsync(V.z, 0, T * V.Ptot, h->st));
     CK(cudaMemsetAsync(V.v, 0, T * V.Ptot, h->st));
     if (V.Mtot) CK(cudaMemsetAsync(V.y, 0, sizeof(double) * V.Mtot, h->st));
+    if (V.Mtot) CK(cudaMemsetAsync(V.ax, 0, sizeof(double) * V.Mtot, h->st));
+    CK(cudaMemsetAsync(V.aty, 0, sizeof(double) * V.Ntot, h->st));
     int rc = sync_inst(h);
     if (rc != HSDE_OK) return rc;
     for (int32_t b = 0; b < h->B; ++b) {
@@ -1227,13 +1293,22 @@ int hsde_set_data(hsde_handle* h, int32_t i, const double* c, const double* b) {
         if (!std::isfinite(c[e])) return fail(HSDE_EINVAL, "non-finite c");
     for (int32_t j = 0; j < H.m; ++j)
         if (!std::isfinite(b[j])) return fail(HSDE_EINVAL, "non-finite b");
-    H.cvec.assign(c, c + N);
-    H.b.assign(b, b + H.m);
-    CK(cudaMemcpyAsync(const_cast<double*>(h->V.c) + h->x_off[i], c, sizeof(double) * N, cudaMemcpyHostToDevice,
-                       h->st));
+    // new scaling factors from the new data (D depends on A only)
+    scale_factors(H, b, c, h->opt, H.sigma, H.rho, H.bnorm, H.cnorm);
+    H.cvec.resize(N);
+    for (int64_t e = 0; e < N; ++e) H.cvec[e] = H.rho * c[e];
+    H.b.resize(H.m);
+    for (int32_t j = 0; j < H.m; ++j) H.b[j] = H.sigma * H.dscale[j] * b[j];
+    if ((rc = sync_inst(h)) != HSDE_OK) return rc;
+    InstDev I = h->host_inst[i];
+    I.sigma = H.sigma; I.rho = H.rho; I.bnorm = H.bnorm; I.cnorm = H.cnorm;
+    h->host_inst[i] = I;
+    CK(cudaMemcpy(h->V.inst + i, &I, sizeof(InstDev), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(const_cast<double*>(h->V.c) + h->x_off[i], H.cvec.data(), sizeof(double) * N,
+                  cudaMemcpyHostToDevice));
     if (H.m)
-        CK(cudaMemcpyAsync(const_cast<double*>(h->V.b) + h->m_off[i], b, sizeof(double) * H.m,
-                           cudaMemcpyHostToDevice, h->st));
+        CK(cudaMemcpy(const_cast<double*>(h->V.b) + h->m_off[i], H.b.data(), sizeof(double) * H.m,
+                      cudaMemcpyHostToDevice));
     // S does not depend on (c, b); M^{-1} zeta and 1 + zeta^T M^{-1} zeta do
     launch_rhs(h->V, h->mixed, Mode::Setup, h->st);
     launch_spmv_A(h->V, Mode::Setup, h->st);
@@ -1253,6 +1328,8 @@ int hsde_unrolled_forward(hsde_handle* h, int32_t K, int32_t ckpt, double* x, do
     if (!h) return fail(HSDE_EINVAL, "null handle");
     if (h->B != 1) return fail(HSDE_EINVAL, "unrolled differentiation needs a single-instance handle");
     if (K < 1 || ckpt < 1) return fail(HSDE_EINVAL, "K and ckpt must be positive");
+    if (h->opt.alpha != 1.0 || h->opt.scaling != 0)
+        return fail(HSDE_EINVAL, "unrolled differentiation needs options alpha = 1 and scaling = 0");
     CK(cudaSetDevice(h->device));
     int rc;
     if ((rc = ensure_unroll_ws(h, K, ckpt)) != HSDE_OK) return rc;

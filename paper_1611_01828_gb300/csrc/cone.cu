@@ -4,12 +4,14 @@
 // Eq. Step3 (z <- z - s_hat + s).
 //
 // For clique k, with xh = x_w - eta x_p gathered through H_k (the corrected
-// x_hat of the affine step):
+// x_hat of the affine step) and the over-relaxation alpha (1: the literal
+// Eqs. Step2-Step3):
 //   s_hat = (s + z - v + H_k xh)/2,  v_hat = (s + z + v - H_k xh)/2
-//   a     = s_hat - z                  (the point projected in Eq. Step2)
+//   a     = alpha s_hat + (1 - alpha) s - z   (the point projected in Eq. Step2)
 //   s     = Pi_psd(a) = V max(Lambda, 0) V^T
-//   z     = s - a,   v = v_hat
-// and the stopping-rule partial ||H_k xh - s||^2 (full-vec weights).
+//   z     = s - a,   v = alpha v_hat + (1 - alpha) v
+// and the stopping-rule partial ||H_k x_new - s||^2 (full-vec weights), with
+// x_new = alpha xh + (1 - alpha) x (x is still the previous iterate here).
 //
 // Eigensolver: two-sided cyclic Jacobi (symmetric Schur decomposition by 2x2
 // rotations, Golub & Van Loan) with a parallel round-robin ordering.  The
@@ -269,6 +271,26 @@ __device__ __forceinline__ void jacobi_round(const RoundPlan<Cfg>& pl, const T* 
     gsync<G>(gid);
 }
 
+// The point projected for one packed entry, from the previous s, z, v of
+// the entry and gx = (H_k x_hat) of it: a = alpha s_hat + (1-alpha) s - z,
+// the new v = alpha v_hat + (1-alpha) v, and hx = (H_k x_new) of it.  alpha
+// is uniform over the launch, so the branch does not diverge; alpha = 1
+// reads nothing more.
+__device__ __forceinline__ void cone_inputs(double so, double zo, double vo, double gx, double al,
+                                            const double* __restrict__ x, int gi, double& av, double& vn,
+                                            double& hx) {
+    if (al == 1.0) {
+        av = 0.5 * (so - zo - vo + gx);
+        vn = 0.5 * (so + zo + vo - gx);
+        hx = gx;
+    } else {
+        const double sh = 0.5 * (so + zo - vo + gx);
+        av = al * sh + (1.0 - al) * so - zo;
+        vn = al * 0.5 * (so + zo + vo - gx) + (1.0 - al) * vo;
+        hx = al * gx + (1.0 - al) * x[gi];
+    }
+}
+
 // Column of entry e in a packed lower column-major c x c block (column b
 // starts at b c - b (b - 1) / 2).
 __device__ __forceinline__ int packed_column(int e, int c) {
@@ -316,6 +338,7 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
     const int nlow = c * (c + 1) / 2;
     const int64_t off = V.cl_off[k];
     const double eta = I.eta;
+    const double al = V.alpha;
     T* Vst = V.vstore ? reinterpret_cast<T*>(V.vstore) + V.vs_off[k] : nullptr;
     const bool use_warm = warm && Vst != nullptr && !I.vcold;
     // every refresh-th iteration the stored basis, whose orthogonality
@@ -377,10 +400,11 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
             if (apos[q] < 0) continue;
             const double gx = V.xw[gi[q]] - eta * V.xp[gi[q]];
             const double so_ = so[q], zo_ = zo[q], vo_ = vo[q];
-            const double av = 0.5 * (so_ - zo_ - vo_ + gx);
-            gxs[q] = gx;
+            double av, vn, hx;
+            cone_inputs(so_, zo_, vo_, gx, al, V.x, gi[q], av, vn, hx);
+            gxs[q] = hx;
             avs[q] = av;
-            vns[q] = (T)(0.5 * (so_ + zo_ + vo_ - gx));
+            vns[q] = (T)vn;
             const int arow = apos[q] / LD, b = apos[q] - (apos[q] / LD) * LD;
             A0[apos[q]] = (T)av;
             A0[b * LD + arow] = (T)av;
@@ -392,7 +416,8 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
             const int arow = b + (e - (b * c - b * (b - 1) / 2));
             const int gi = V.gmap[off + e];
             const double gx = V.xw[gi] - eta * V.xp[gi];
-            const double av = 0.5 * ((double)s[off + e] - (double)z[off + e] - (double)v[off + e] + gx);
+            double av, vn, hx;
+            cone_inputs((double)s[off + e], (double)z[off + e], (double)v[off + e], gx, al, V.x, gi, av, vn, hx);
             A0[arow * LD + b] = (T)av;
             A0[b * LD + arow] = (T)av;
         }
@@ -500,6 +525,7 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
     }
 
     int sweeps_done = 0;
+    bool converged = false;
     for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
         sweeps_done = sweep;
         T offd = 0, dg = 0;
@@ -512,7 +538,8 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
         }
         offd = gsum<G>(offd, red, gid);
         const T tot = gsum<G>(dg, red, gid) + offd;
-        if (offd <= tol2 * tot || sweep == max_sweeps) break;
+        converged = offd <= tol2 * tot;
+        if (converged || sweep == max_sweeps) break;
         for (int r = 0; r < CP - 1; ++r) {
             jacobi_round<Cfg>(plan, A, An, Vc, Vn, rot, tan_, lane, gid);
             T* t1 = A; A = An; An = t1;
@@ -590,7 +617,7 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
     }
     gsync<G>(gid);
 
-    double res = 0.0;
+    double res = 0.0, sres = 0.0;
     if constexpr (STASH) {
 #pragma unroll
         for (int q = 0; q < EPT; ++q) {
@@ -601,7 +628,9 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
             z[j] = (T)(sn - avs[q]);
             v[j] = vns[q];
             const double d = gxs[q] - sn;
-            res += ((diag_bits >> q) & 1u ? 1.0 : 2.0) * d * d;
+            const double w = (diag_bits >> q) & 1u ? 1.0 : 2.0;
+            res += w * d * d;
+            sres += w * sn * sn;
         }
     } else {
         for (int e = lane; e < nlow; e += G) {
@@ -611,19 +640,26 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
             const double sn = (double)An[arow * LD + b];
             const int gi = V.gmap[j];
             const double gx = V.xw[gi] - eta * V.xp[gi];
-            const double so_ = s[j], zo_ = z[j], vo_ = v[j];
-            const double av = 0.5 * (so_ - zo_ - vo_ + gx);
+            double av, vn, hx;
+            cone_inputs((double)s[j], (double)z[j], (double)v[j], gx, al, V.x, gi, av, vn, hx);
             s[j] = (T)sn;
             z[j] = (T)(sn - av);
-            v[j] = (T)(0.5 * (so_ + zo_ + vo_ - gx));
-            const double d = gx - sn;
-            res += (arow == b ? 1.0 : 2.0) * d * d;
+            v[j] = (T)vn;
+            const double d = hx - sn;
+            const double w = arow == b ? 1.0 : 2.0;
+            res += w * d * d;
+            sres += w * sn * sn;
         }
     }
     res = gsum<G>(res, reinterpret_cast<double*>(red), gid);
+    sres = gsum<G>(sres, reinterpret_cast<double*>(red), gid);
     if (lane == 0) {
-        V.cl_part[k] = res;
+        V.cl_part[2 * k] = res;
+        V.cl_part[2 * k + 1] = sres;
         V.cl_sweeps[k] = sweeps_done;
+        // an eigensolve that ran out of sweeps is counted, not hidden (the
+        // projection is then only as accurate as its last sweep)
+        if (!converged) atomicAdd(&V.inst[V.cl_inst[k]].unconv, 1);
     }
 }
 

@@ -53,10 +53,15 @@ struct InstDev {
     int32_t status;          // HSDE_RUNNING ...
     int32_t iter;            // iterations done
     int32_t vcold;           // 1: the stored eigenbases are not valid (cold start next)
+    int32_t unconv;          // cliques whose eigensolve stopped at max_sweeps above the
+                             // tolerance in the current iteration (k_cone counts)
+    int32_t unconv_last;     // the same count for the last completed iteration
+    int32_t unconv_iters;    // iterations with at least one such clique
     // cached by setup
     double den;              // 1 + zeta^T M^{-1} zeta
     double ctp;              // c^T x_p - b^T y_p
-    double bnorm, cnorm;     // ||b||, ||c|| (full-vec norms)
+    double bnorm, cnorm;     // ||b||, ||c|| of the original data (full-vec norms)
+    double sigma, rho;       // data scaling: b~ = sigma D b, c~ = rho c (1, 1 unscaled)
     // iterate scalars
     double tau, kappa, eta;
     // last check
@@ -67,7 +72,10 @@ struct InstDev {
 };
 
 // Number of partial sums stored per N-space tile.
-constexpr int KPART = 8;
+constexpr int KPART = 10;
+// A certificate's two terms must cancel to this fraction of their size
+// (reading P6: the ratio to b^T y or -c^T x alone is not scale-invariant).
+constexpr double CERT_CANCEL = 1e-2;
 // Entries per N-space tile (one CTA of 256 threads each).
 constexpr int TILE_N = 256;
 // Nonzeros of A^T per A^T tile (whole rows; a longer row is a tile alone).
@@ -102,10 +110,13 @@ struct DevView {
     double* part;            // [ntiles * KPART]
     const int4* at_tiles;    // (inst, begin, end, lanes per row; NT: whole CTA on one row)
     double* at_part;         // [nat] c^T x_w partial of each A^T tile
-    double* cl_part;         // [ncl]
+    double* cl_part;         // [2 ncl]: per clique ||H_k x - s_k||^2 and ||s_k||^2 (full-vec)
     int32_t* cl_sweeps;      // [ncl] Jacobi sweeps used by each clique in its last solve
     double* rowb;            // [Mtot] b_i (y_w)_i
     double* af;              // [Mtot] A f of the current iteration
+    const double* dinv2;     // [Mtot] 1 / d_i^2 (row scaling D; 1 unscaled)
+    double* ax;              // [Mtot] A x of the current iterate (over-relaxation)
+    double* aty;             // [Ntot] A^T y of the current iterate (over-relaxation)
     // reverse-mode tape of one iteration (null when not recording)
     void* tape_v;            // per clique: CP x CP eigenvectors, then CP eigenvalues
     const int64_t* tv_off;   // [ncl] offset of each clique's tape block (elements)
@@ -115,6 +126,7 @@ struct DevView {
     int* counters;           // [2B] completion counters of k_bwd_eta and k_post
     // options
     double eps;
+    double alpha;            // over-relaxation (1: the literal Eqs. Step1-Step3)
     int32_t max_iter, check_every;
 };
 
@@ -162,6 +174,9 @@ void launch_solve_dense(const DevView& V, void* st);
 void launch_bwd_eta(const DevView& V, void* st);
 void launch_post(const DevView& V, bool mixed, void* st);
 void launch_setup_den(const DevView& V, void* st);
+// A x and A^T y of the stored iterate into V.ax, V.aty for the constraint
+// rows [r0, r1) and pattern entries [e0, e1) (after hsde_set_state)
+void launch_state_products(const DevView& V, int r0, int r1, int64_t e0, int64_t e1, void* st);
 // cone projection of every clique in one bucket (Eq. Step2 on S, fused with
 // the H gather, the rank-one correction and the nu update of Eq. Step3)
 int  launch_cone(const DevView& V, const Bucket& bk, bool mixed, int max_sweeps, double tol,

@@ -11,10 +11,15 @@
 //   y_w = S^{-1} q,      S = I + A Delta^{-1} A^T        (cached inverse)
 //   x_w = f + Delta^{-1} A^T y_w
 //   eta = (c^T x_w - b^T y_w) / (1 + zeta^T M^{-1} zeta) (Eq. MatrixInverseResult)
-//   x = x_w - eta x_p,  y = y_w - eta y_p,
-//   tau_hat = omega_tau + c^T x - b^T y                   (Eq. FirstBlockElimination)
-//   tau = max(0, tau_hat - kappa), kappa += tau - tau_hat (Eqs. Step2-Step3)
+//   x_hat = x_w - eta x_p,  y_hat = y_w - eta y_p,
+//   tau_hat = omega_tau + c^T x_hat - b^T y_hat          (Eq. FirstBlockElimination)
+// then the cone step on the relaxed point u_rel = alpha u_hat + (1 - alpha) u
+// (alpha = 1: the literal Eqs. Step2-Step3):
+//   x = x_rel,  y = y_rel,
+//   tau = max(0, tau_rel - kappa), kappa += tau - tau_rel
 // The clique part (s_hat, v_hat, the PSD projection and z) is in cone.cu.
+// All of it runs on the scaled data (A~ = D A, b~ = sigma D b, c~ = rho c,
+// or the data as given); the stopping rule unscales (readings P5-P7).
 //
 // Every reduction is a fixed-order tree (no float atomics): results are
 // bitwise reproducible for a given launch configuration.
@@ -343,8 +348,10 @@ __global__ void __launch_bounds__(NT) k_bwd_eta(DevView V) {
     const double tau = I.tau, kappa = I.kappa;
     const double ot = tau + kappa;
     const double tau_hat = ot + sw - eta * I.ctp;
-    const double tau_new = fmax(0.0, tau_hat - kappa);
-    const double kappa_new = kappa - tau_hat + tau_new;
+    const double al = V.alpha;
+    const double tau_rel = (al == 1.0) ? tau_hat : al * tau_hat + (1.0 - al) * tau;
+    const double tau_new = fmax(0.0, tau_rel - kappa);
+    const double kappa_new = kappa - tau_rel + tau_new;
     // y = y_w - eta y_p and the constraint-space sums of the stopping rule
     // follow in k_post, spread over all of its CTAs.
     if (threadIdx.x == 0) {
@@ -362,18 +369,23 @@ __global__ void __launch_bounds__(NT) k_bwd_eta(DevView V) {
     }
 }
 
-// x = x_w - eta x_p; stopping-rule partials over N (r = A^T y + H^T z):
+// x = alpha (x_w - eta x_p) + (1 - alpha) x; stopping-rule partials over N
+// (r = A^T y + H^T z):
 //   ||r - tau c||^2, ||r||^2, c^T x  (full-vec weights), on check iterations;
 // f = Delta^{-1}(x - omega_tau' c + 1/2 H^T (s+z+v)) for the next iteration;
-// y = y_w - eta y_p over a slice of the constraints per CTA, with the
-// constraint-space partials ||A x - tau b||^2, ||A x||^2, b^T y;
-// the last CTA of each instance takes the verdict (readings P5/P6).
+// y = alpha (y_w - eta y_p) + (1 - alpha) y over a slice of the constraints
+// per CTA, with the constraint-space partials ||D^{-1}(A x - tau b)||^2,
+// ||D^{-1} A x||^2, b^T y; the last CTA of each instance takes the verdict
+// (readings P5/P6) on the unscaled values (reading P7).
+// With alpha != 1 the new A x and A^T y need those of the previous iterate:
+// they are kept in V.ax and V.aty (A x_hat and A^T y_hat come from the
+// affine step's own vectors, see below).
 // Copies of pattern entries (H^T) staged per pass of k_post.
 constexpr int POST_STAGE = 2048;
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_post(DevView V) {
-    __shared__ double sh[8 * NT / 32];
+    __shared__ double sh[12 * NT / 32];
     __shared__ int flag;
     __shared__ double cz[POST_STAGE], call[POST_STAGE];   // per copy: z, and s + z + v
     const int4 t = V.tiles[blockIdx.x];
@@ -382,14 +394,18 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
     const bool check = is_check_iter(V, I.iter);
     const double eta = I.eta, tau = I.tau;
     const double ot = I.tau + I.kappa;            // omega_tau of the next iteration
+    const double al = V.alpha;
+    const bool relax = al != 1.0;
     double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    double a4 = 0.0, a5 = 0.0, a6 = 0.0;   // ||A^T y||^2, ||H^T z||^2, ||H x||^2 (certificate cancellation)
     // one pattern entry per thread (TILE_N == NT)
     const int e = t.y + threadIdx.x;
     const bool has = e < t.z;
     double x = 0.0;
     int k0 = 0, k1 = 0;
     if (has) {
-        x = V.xw[e] - eta * V.xp[e];
+        const double xh = V.xw[e] - eta * V.xp[e];
+        x = relax ? al * xh + (1.0 - al) * V.x[e] : xh;
         V.x[e] = x;
         k0 = V.sc_ptr[e];
         k1 = V.sc_ptr[e + 1];
@@ -418,14 +434,22 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
     if (has) {
         const double ce = V.c[e];
         V.f[e] = (x - ot * ce + 0.5 * hall) * V.inv_delta[e];
+        // A^T y_hat = A^T y_w - eta A^T y_p (both kept from this iteration / setup)
+        double aty = V.atyw[e] - eta * V.atyp[e];
+        if (relax) {
+            aty = al * aty + (1.0 - al) * V.aty[e];
+            V.aty[e] = aty;
+        }
         if (check) {
-            // A^T y = A^T y_w - eta A^T y_p (both kept from this iteration / setup)
-            const double r = hz + V.atyw[e] - eta * V.atyp[e];
+            const double r = hz + aty;
             const double w = V.diag[e] ? 1.0 : 2.0;
             const double d = r - tau * ce;
             a1 += w * d * d;
             a2 += w * r * r;
             a3 += w * ce * x;
+            a4 += w * aty * aty;
+            a5 += w * hz * hz;
+            a6 += w * (double)(k1 - k0) * x * x;   // x repeated in each clique containing it
         }
     }
     // This CTA's slice of the constraints.  A x is not formed by an SpMV:
@@ -441,26 +465,35 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
         for (int i = i0 + threadIdx.x; i < i1; i += NT) {
             const int row = I.m_off + i;
             const double bi = V.b[row], yw = V.yw[row], yp = V.yp[row];
-            const double ynew = yw - eta * yp;
-            if (check) {
+            const double yold = V.y[row];
+            double ynew = yw - eta * yp;
+            if (relax) ynew = al * ynew + (1.0 - al) * yold;
+            if (check || relax) {
                 const double afr = V.af[row];
-                const double q = V.y[row] + otp * bi - afr;
-                const double ax = (afr + q - yw) - eta * (-bi - yp);
-                const double d = ax - tau * bi;
-                b1 += d * d;
-                b2 += ax * ax;
-                b3 += bi * ynew;
+                const double q = yold + otp * bi - afr;
+                double ax = (afr + q - yw) - eta * (-bi - yp);
+                if (relax) {
+                    ax = al * ax + (1.0 - al) * V.ax[row];
+                    V.ax[row] = ax;
+                }
+                if (check) {
+                    const double w2 = V.dinv2[row];
+                    const double d = ax - tau * bi;
+                    b1 += w2 * d * d;
+                    b2 += w2 * ax * ax;
+                    b3 += bi * ynew;
+                }
             }
             V.y[row] = ynew;
         }
     }
     if (check) {
-        double v6[6] = {a1, a2, a3, b1, b2, b3};
-        block_sum_n<6>(v6, sh);
+        double v9[9] = {a1, a2, a3, b1, b2, b3, a4, a5, a6};
+        block_sum_n<9>(v9, sh);
         if (threadIdx.x == 0) {
             double* pp = V.part + (int64_t)blockIdx.x * KPART;
-            pp[1] = v6[0]; pp[2] = v6[1]; pp[3] = v6[2];
-            pp[4] = v6[3]; pp[5] = v6[4]; pp[6] = v6[5];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) pp[1 + i] = v9[i];
         }
     }
     if (!last_cta(V.counters + 2 * t.x + 1, I.tile_end - I.tile_begin, &flag)) return;
@@ -468,30 +501,46 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
     if (threadIdx.x == 0) {
         V.counters[2 * t.x + 1] = 0;
         I.vcold = 0;                                // stored eigenbases are valid from now on
+        const int uc = atomicExch(&I.unconv, 0);    // every k_cone of this iteration is done
+        I.unconv_last = uc;
+        if (uc > 0) I.unconv_iters += 1;
     }
     if (!check) return;
-    double v7[7] = {0, 0, 0, 0, 0, 0, 0};
+    double v11[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int tt = I.tile_begin + threadIdx.x; tt < I.tile_end; tt += NT) {
         const double* pp = V.part + (int64_t)tt * KPART;
 #pragma unroll
-        for (int i = 0; i < 6; ++i) v7[i] += __ldcg(pp + 1 + i);
+        for (int i = 0; i < 9; ++i) v11[i] += __ldcg(pp + 1 + i);
     }
-    for (int k = I.cl_begin + threadIdx.x; k < I.cl_end; k += NT) v7[6] += __ldcg(V.cl_part + k);
-    block_sum_n<7>(v7, sh);
-    a1 = v7[0]; a2 = v7[1]; a3 = v7[2];
-    const double r0 = v7[3], r1 = v7[4], r2 = v7[5], hs = v7[6];
+    for (int k = I.cl_begin + threadIdx.x; k < I.cl_end; k += NT) {
+        v11[9] += __ldcg(V.cl_part + 2 * k);
+        v11[10] += __ldcg(V.cl_part + 2 * k + 1);
+    }
+    block_sum_n<11>(v11, sh);
+    a1 = v11[0]; a2 = v11[1]; a3 = v11[2];
+    const double r0 = v11[3], r1 = v11[4], r2 = v11[5], hs = v11[9];
+    const double aty2 = v11[6], hz2 = v11[7], hx2 = v11[8], ss2 = v11[10];
     if (threadIdx.x != 0) return;
-    const double ctx = a3, bty = r2;
+    // unscaled values (reading P7): x = x~/sigma, s = s~/sigma, y = D y~/rho,
+    // z = z~/rho, so c^T x = c~^T x~/(rho sigma), b^T y = b~^T y~/(sigma rho),
+    // A x - tau b = D^{-1}(A~ x~ - tau b~)/sigma, A^T y + H^T z = r~/rho
+    const double sg = I.sigma, rh = I.rho;
+    const double ctx = a3 / (rh * sg), bty = r2 / (sg * rh);
     double pres = INFINITY, dres = INFINITY, gap = INFINITY, pobj = NAN, dobj = NAN;
     if (tau > 0) {
-        pres = sqrt(r0 + hs) / tau / (1.0 + I.bnorm);
-        dres = sqrt(a1) / tau / (1.0 + I.cnorm);
+        pres = sqrt(r0 + hs) / (sg * tau) / (1.0 + I.bnorm);
+        dres = sqrt(a1) / (rh * tau) / (1.0 + I.cnorm);
         pobj = ctx / tau;
         dobj = bty / tau;
         gap = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
     }
-    const double pinf = bty > 0 ? sqrt(a2) / bty : INFINITY;
-    const double dinf = ctx < 0 ? sqrt(r1 + hs) / (-ctx) : INFINITY;
+    const double pinf = bty > 0 ? sqrt(a2) / rh / bty : INFINITY;
+    const double dinf = ctx < 0 ? sqrt(r1 + hs) / sg / (-ctx) : INFINITY;
+    // reading P6: a certificate's two terms must also cancel (scale-free, so
+    // the scaled sums serve as they are)
+    const double pden = sqrt(aty2) + sqrt(hz2), dden = sqrt(hx2) + sqrt(ss2);
+    const double pcan = pden > 0 ? sqrt(a2) / pden : INFINITY;
+    const double dcan = dden > 0 ? sqrt(r1 + hs) / dden : INFINITY;
     I.pres = pres; I.dres = dres; I.gap = gap; I.pobj = pobj; I.dobj = dobj;
     I.pinf = pinf; I.dinf = dinf; I.ctx = ctx; I.bty = bty;
     int st = HSDE_RUNNING;
@@ -499,9 +548,9 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
         st = HSDE_NUMERICAL_ERROR;
     } else if (tau > 0 && pres <= V.eps && dres <= V.eps && gap <= V.eps) {
         st = HSDE_SOLVED;
-    } else if (bty > 0 && pinf <= V.eps) {
+    } else if (bty > 0 && pinf <= V.eps && pcan <= CERT_CANCEL) {
         st = HSDE_PRIMAL_INFEASIBLE;
-    } else if (ctx < 0 && dinf <= V.eps) {
+    } else if (ctx < 0 && dinf <= V.eps && dcan <= CERT_CANCEL) {
         st = HSDE_DUAL_INFEASIBLE;
     } else if (I.iter >= V.max_iter) {
         st = HSDE_MAX_ITER;
@@ -509,31 +558,42 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
     I.status = st;
 }
 
-// den = 1 + c^T x_p - b^T y_p, ctp = den - 1, ||b||, ||c||.  One CTA per instance.
+// den = 1 + c^T x_p - b^T y_p, ctp = den - 1.  One CTA per instance.  (The
+// norms of the original b and c used by the stopping rule are set on the host.)
 __global__ void __launch_bounds__(NT) k_setup_den(DevView V) {
     __shared__ double sh[32];
     InstDev& I = V.inst[blockIdx.x];
     double ctp = 0.0;
     for (int t = I.tile_begin + threadIdx.x; t < I.tile_end; t += NT) ctp += V.part[(int64_t)t * KPART];
     ctp = block_sum(ctp, sh);
-    double btp = 0.0, bb = 0.0;
-    for (int i = threadIdx.x; i < I.m; i += NT) {
-        const double bi = V.b[I.m_off + i];
-        btp += bi * V.yp[I.m_off + i];
-        bb += bi * bi;
-    }
+    double btp = 0.0;
+    for (int i = threadIdx.x; i < I.m; i += NT) btp += V.b[I.m_off + i] * V.yp[I.m_off + i];
     btp = block_sum(btp, sh);
-    bb = block_sum(bb, sh);
-    double cc = 0.0;
-    for (int64_t e = I.x_off + threadIdx.x; e < I.x_off + I.N; e += NT)
-        cc += (V.diag[e] ? 1.0 : 2.0) * V.c[e] * V.c[e];
-    cc = block_sum(cc, sh);
     if (threadIdx.x == 0) {
         I.ctp = ctp - btp;
         I.den = 1.0 + I.ctp;
-        I.bnorm = sqrt(bb);
-        I.cnorm = sqrt(cc);
     }
+}
+
+// A x and A^T y of the stored iterate (rows [r0, r1) and entries [e0, e1) of
+// one instance), for the over-relaxation after a state is loaded.
+__global__ void __launch_bounds__(NT) k_state_ax(DevView V, int r0, int r1) {
+    const int row = r0 + (int)(((int64_t)blockIdx.x * NT + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (row >= r1) return;
+    double acc = 0.0;
+    const int j1 = V.A_ptr[row + 1];
+    for (int j = V.A_ptr[row] + lane; j < j1; j += 32) acc += V.A_val[j] * V.x[V.A_col[j]];
+    acc = warp_sum(acc);
+    if (lane == 0) V.ax[row] = acc;
+}
+
+__global__ void __launch_bounds__(NT) k_state_aty(DevView V, int64_t e0, int64_t e1) {
+    const int64_t e = e0 + (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (e >= e1) return;
+    double acc = 0.0;
+    const int j1 = V.At_ptr[e + 1];
+    for (int j = V.At_ptr[e]; j < j1; ++j) acc += V.At_val[j] * V.y[V.At_col[j]];
+    V.aty[e] = acc;
 }
 
 // One in-place Gauss-Jordan step (pivot k) on every dense S with m > k.
@@ -587,7 +647,8 @@ __global__ void k_gj_update(double* pool, const int64_t* offs, const int32_t* ms
 // launchers
 // ---------------------------------------------------------------------------
 static inline cudaStream_t S_(void* st) { return reinterpret_cast<cudaStream_t>(st); }
-static inline int rows_grid(int rows) { return (rows * 32 + NT - 1) / NT; }
+// one warp per row; rows < 2^31 / 32 is guaranteed by the setup limits
+static inline int rows_grid(int rows) { return (int)(((int64_t)rows * 32 + NT - 1) / NT); }
 
 void launch_rhs(const DevView& V, bool mixed, Mode mode, void* st) {
     if (V.ntiles == 0) return;
@@ -607,6 +668,11 @@ void launch_spmv_At(const DevView& V, Mode mode, void* st) {
     k_spmv_At<<<V.ntiles, NT, 0, S_(st)>>>(V, (int)mode);
 }
 void launch_setup_den(const DevView& V, void* st) { k_setup_den<<<V.B, NT, 0, S_(st)>>>(V); }
+
+void launch_state_products(const DevView& V, int r0, int r1, int64_t e0, int64_t e1, void* st) {
+    if (r1 > r0) k_state_ax<<<rows_grid(r1 - r0), NT, 0, S_(st)>>>(V, r0, r1);
+    if (e1 > e0) k_state_aty<<<(unsigned)((e1 - e0 + NT - 1) / NT), NT, 0, S_(st)>>>(V, e0, e1);
+}
 
 void launch_fwd(const DevView& V, void* st) {
     if (V.Mtot > 0) k_fwd<<<rows_grid(V.Mtot), NT, 0, S_(st)>>>(V);

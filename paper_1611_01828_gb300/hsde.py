@@ -19,6 +19,7 @@ RUNNING, SOLVED, PRIMAL_INFEASIBLE, DUAL_INFEASIBLE, MAX_ITER, NUMERICAL_ERROR =
 STATUS_NAMES = {0: "running", 1: "solved", 2: "primal_infeasible", 3: "dual_infeasible", 4: "max_iter",
                 5: "numerical_error"}
 FP64, MIXED = 0, 1
+MAX_CLIQUE = 64          # largest clique the eigensolvers of this build take (HSDE_ERANGE above)
 
 _i32p = C.POINTER(C.c_int32)
 _i64p = C.POINTER(C.c_int64)
@@ -37,7 +38,8 @@ class hsde_options(C.Structure):
                 ("precision", C.c_int32), ("device", C.c_int32), ("cuda_stream", C.c_void_p),
                 ("jacobi_max_sweeps", C.c_int32), ("use_graph", C.c_int32), ("jacobi_tol", C.c_double),
                 ("profile", C.c_int32), ("warm_start", C.c_int32), ("warm_refresh", C.c_int32),
-                ("_pad", C.c_int32)]
+                ("scaling", C.c_int32), ("alpha", C.c_double), ("scale_norm", C.c_double),
+                ("dual_weight", C.c_double)]
 
 
 class hsde_sizes(C.Structure):
@@ -50,7 +52,8 @@ class hsde_info(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("pres", C.c_double),
                 ("dres", C.c_double), ("gap", C.c_double), ("pobj", C.c_double), ("dobj", C.c_double),
                 ("tau", C.c_double), ("kappa", C.c_double), ("pinf_ratio", C.c_double),
-                ("dinf_ratio", C.c_double), ("setup_ms", C.c_double), ("iterate_ms", C.c_double)]
+                ("dinf_ratio", C.c_double), ("setup_ms", C.c_double), ("iterate_ms", C.c_double),
+                ("jacobi_unconverged", C.c_int32), ("jacobi_unconverged_iterations", C.c_int32)]
 
 
 MAX_PHASES = 16

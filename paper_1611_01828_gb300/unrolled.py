@@ -5,6 +5,10 @@ Forward runs the iterations inside libhsde (hsde_unrolled_forward) for data
 sweep (hsde_unrolled_backward: Daleckii-Krein adjoint of the clique
 projections, adjoint affine solve with the cached factor, checkpointing).
 This module only moves values between tensors and the C-ABI.
+
+The handle must run the literal iteration on the data as given: create it
+with ``**LITERAL`` (alpha = 1, no data scaling), because the scaling factors
+depend on c and b and the library differentiates the unscaled steps.
 """
 from __future__ import annotations
 
@@ -12,6 +16,9 @@ import numpy as np
 import torch
 
 from . import hsde
+
+# options of a handle that can be differentiated (the library refuses others)
+LITERAL = dict(alpha=1.0, scaling=0)
 
 
 def pattern_weights(handle) -> np.ndarray:

@@ -98,3 +98,31 @@ def test_invalid_inputs_rejected(hs):
         with pytest.raises(hs.HSDEError) as ei:
             hs.hsde_analyze(q)
         assert ei.value.code == hs.HSDE_EINVAL
+
+
+def test_default_options_of_the_practical_form(hs):
+    # reading P7: the same defaults as the oracle
+    from oracle import hsde as ohsde
+    o = hs.default_options()
+    assert o.alpha == ohsde.ALPHA and o.scaling == 1
+    assert o.scale_norm == ohsde.SCALE_NORM and o.dual_weight == ohsde.DUAL_WEIGHT
+
+
+@pytest.mark.parametrize("kw", [dict(alpha=0.0), dict(alpha=2.0), dict(scaling=2), dict(scale_norm=0.0),
+                                dict(dual_weight=-1.0), dict(eps_tol=0.0), dict(max_iter=0)])
+def test_invalid_options_rejected_before_any_device_call(hs, kw):
+    with pytest.raises(hs.HSDEError) as ei:
+        hs.Handle(synth.block_arrow_n50(), **kw)
+    assert ei.value.code == hs.HSDE_EINVAL
+
+
+def test_clique_beyond_the_largest_eigensolver_is_rejected(hs):
+    """A clique larger than the library's eigensolvers take gives HSDE_ERANGE
+    at setup, before any device call (so this needs no GPU)."""
+    big = 8 + max(64, int(hs.MAX_CLIQUE))
+    p = synth.block_arrow(2, big - 5, 5, 4, np.random.default_rng(3))
+    assert hs.hsde_analyze(p)["c_max"] == big
+    with pytest.raises(hs.HSDEError) as ei:
+        hs.Handle(p)
+    assert ei.value.code == hs.HSDE_ERANGE
+    assert str(big) in str(ei.value)

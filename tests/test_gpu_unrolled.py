@@ -61,13 +61,13 @@ def test_fp64_gradient_matches_oracle(env, case):
         p0, K = synth.block_arrow(3, 3, 2, 5, np.random.default_rng(2), kappa=30.0, assign="roundrobin"), 30
     else:
         p0, K = synth.block_arrow_n50(), 25
-    st = ohsde.HSDE(p0).V.st
+    st = ohsde.HSDE(p0, alpha=1.0, scaling=False).V.st
     p = _on_pattern(p0, st)
-    ref = ohsde.HSDE(p)
+    ref = ohsde.HSDE(p, alpha=1.0, scaling=False)
     f_r, cbar, bbar = adjoint.gradient(ref, K)
     w = np.where(st.pat_row == st.pat_col, 1.0, 2.0)
     gC_ref = w * adjoint.grad_C_lower(ref, cbar)
-    with hsde.Handle(p, precision="fp64") as H:
+    with hsde.Handle(p, precision="fp64", **unrolled.LITERAL) as H:
         f, gC, gb = _grad(torch, hsde, unrolled, H, p.C_val, p.b, K, 7)
     assert f == pytest.approx(f_r, rel=1e-7)        # FP64 forward parity (rounding order)
     assert np.linalg.norm(gC - gC_ref) <= 1e-6 * np.linalg.norm(gC_ref)
@@ -78,7 +78,7 @@ def test_fp64_gradient_matches_oracle(env, case):
 def diff_grid(env):
     torch, hsde, unrolled = env
     p = synth.differentiation_maxcut_grid()
-    H = hsde.Handle(p, precision="fp64")
+    H = hsde.Handle(p, precision="fp64", **unrolled.LITERAL)
     c0 = unrolled.pattern_values(H, p.C_row, p.C_col, p.C_val)
     yield p, H, c0
     H.close()
@@ -114,9 +114,9 @@ def test_diff_grid_gradient_matches_oracle(env, diff_grid):
     p, H, c0 = diff_grid
     K, ckpt = 200, 20
     _, gC, gb = _grad(torch, hsde, unrolled, H, c0, p.b, K, ckpt)
-    st = ohsde.HSDE(p).V.st
+    st = ohsde.HSDE(p, alpha=1.0, scaling=False).V.st
     q = _on_pattern(p, st)
-    ref = ohsde.HSDE(q)
+    ref = ohsde.HSDE(q, alpha=1.0, scaling=False)
     f_r, cbar, bbar = adjoint.gradient(ref, K)
     w = np.where(st.pat_row == st.pat_col, 1.0, 2.0)
     gC_ref = w * adjoint.grad_C_lower(ref, cbar)
@@ -129,7 +129,7 @@ def test_diff_grid_mixed_gradient_close_to_fp64(env, diff_grid):
     p, H, c0 = diff_grid
     K, ckpt = 200, 20
     _, gC64, gb64 = _grad(torch, hsde, unrolled, H, c0, p.b, K, ckpt)
-    with hsde.Handle(p, precision="mixed") as Hm:
+    with hsde.Handle(p, precision="mixed", **unrolled.LITERAL) as Hm:
         _, gC32, gb32 = _grad(torch, hsde, unrolled, Hm, c0, p.b, K, ckpt)
     g64 = np.concatenate([gC64, gb64]); g32 = np.concatenate([gC32, gb32])
     assert np.linalg.norm(g32 - g64) <= 2e-2 * np.linalg.norm(g64)
