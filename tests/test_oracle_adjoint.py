@@ -71,3 +71,43 @@ def test_unrolled_gradient_matches_central_differences(case):
         fd = (fp - fm) / (2 * h)
         an = float(np.sum(w * G * dC) + bbar @ db)
         assert abs(fd - an) <= 1e-5 * (1 + abs(fd)), (fd, an)
+
+
+@pytest.mark.parametrize("rel,h,expect_half", [
+    (0.0, 1e-6, True),        # exactly zero: a central difference sees 1/2 (Moreau)
+    (1e-12, 1e-6, True),      # below ZERO_REL: the step crosses it, so 1/2 again
+    (1e-8, 1e-11, False),     # above ZERO_REL, with a step that does not cross it: 1
+])
+def test_dk_zero_eigenvalue_threshold_against_differences(rel, h, expect_half):
+    """The derivative of Pi_psd at an eigenvalue near zero (reading P13),
+    checked against central differences of the projection itself: the
+    Daleckii-Krein product with the 1e-10 threshold agrees with what a
+    difference of the given step sees, and the diagonal factor of the
+    near-zero direction is 1/2 or 1 accordingly."""
+    rng = np.random.default_rng(7)
+    c = 5
+    Q, _ = np.linalg.qr(rng.standard_normal((c, c)))
+    lam = np.array([2.0, 1.0, rel * 2.0, -1.0, -0.5])
+    A = (Q * lam) @ Q.T
+    G = rng.standard_normal((c, c)); G = 0.5 * (G + G.T)
+    fd = (hsde.project_psd(A + h * G) - hsde.project_psd(A - h * G)) / (2 * h)
+    dk = adjoint.dk_vjp(A, G)
+    assert np.linalg.norm(dk - fd) <= 1e-4 * np.linalg.norm(fd)
+    # the near-zero direction q: <q q^T, dPi[q q^T]> is its diagonal factor
+    q = Q[:, 2]
+    P = np.outer(q, q)
+    g = float(np.sum(P * adjoint.dk_vjp(A, P)))
+    assert g == pytest.approx(0.5 if expect_half else 1.0, abs=1e-6)
+
+
+def test_dk_threshold_is_needed_at_that_step():
+    """Without the threshold, an eigenvalue at 1e-12 of the largest would get
+    the factor 1, which a central difference of step 1e-6 does not see."""
+    rng = np.random.default_rng(8)
+    Q, _ = np.linalg.qr(rng.standard_normal((4, 4)))
+    A = (Q * np.array([1.0, 2e-12, -0.3, 0.4])) @ Q.T
+    P = np.outer(Q[:, 1], Q[:, 1])
+    h = 1e-6
+    fd = float(np.sum(P * (hsde.project_psd(A + h * P) - hsde.project_psd(A - h * P)))) / (2 * h)
+    assert fd == pytest.approx(0.5, abs=1e-4)
+    assert float(np.sum(P * adjoint.dk_vjp(A, P))) == pytest.approx(fd, abs=1e-4)
