@@ -11,6 +11,7 @@
 //  * E' (lower, CSC order) = the edges {v, u}, u in N(v), plus the diagonal;
 //  * packed clique order: (a,b), b = 0..c-1, a = b..c-1.
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <functional>
 #include <queue>
@@ -19,6 +20,77 @@
 #include "internal.h"
 
 namespace hsde {
+
+namespace {
+
+// Set of vertex indices with O(1) insert / erase / membership (open
+// addressing, linear probing, tombstones).  Used for the neighbourhoods of
+// high-degree vertices during the elimination, where a sorted-vector union
+// would cost the whole neighbourhood per update (an arrow vertex adjacent to
+// every other vertex made the analysis quadratic in n).
+class VSet {
+  public:
+    size_t size() const { return live_; }
+    bool insert(int32_t k) {
+        if ((used_ + 1) * 2 > slots_.size()) {
+            size_t n = 64;
+            while (n < 4 * (live_ + 1)) n *= 2;      // tombstones are dropped by the rehash
+            rehash(n);
+        }
+        size_t i = slot(k), tomb = SIZE_MAX;
+        while (slots_[i] != EMPTY) {
+            if (slots_[i] == k) return false;
+            if (slots_[i] == TOMB && tomb == SIZE_MAX) tomb = i;
+            i = (i + 1) & (slots_.size() - 1);
+        }
+        if (tomb != SIZE_MAX) {
+            slots_[tomb] = k;
+        } else {
+            slots_[i] = k;
+            ++used_;
+        }
+        ++live_;
+        return true;
+    }
+    void erase(int32_t k) {
+        if (slots_.empty()) return;
+        size_t i = slot(k);
+        while (slots_[i] != EMPTY) {
+            if (slots_[i] == k) {
+                slots_[i] = TOMB;
+                --live_;
+                return;
+            }
+            i = (i + 1) & (slots_.size() - 1);
+        }
+    }
+    void to_sorted(std::vector<int32_t>& out) const {
+        out.clear();
+        out.reserve(live_);
+        for (int32_t k : slots_)
+            if (k >= 0) out.push_back(k);
+        std::sort(out.begin(), out.end());
+    }
+
+  private:
+    static constexpr int32_t EMPTY = -1, TOMB = -2;
+    std::vector<int32_t> slots_;
+    size_t used_ = 0, live_ = 0;
+    size_t slot(int32_t k) const { return ((uint32_t)k * 2654435761u) & (slots_.size() - 1); }
+    void rehash(size_t n) {
+        std::vector<int32_t> old;
+        old.swap(slots_);
+        slots_.assign(n, EMPTY);
+        used_ = live_ = 0;
+        for (int32_t k : old)
+            if (k >= 0) insert(k);
+    }
+};
+
+// Neighbourhoods above this size live in a VSet instead of a sorted vector.
+constexpr size_t BIG_DEGREE = 256;
+
+}  // namespace
 
 int32_t Symbolic::pos(int32_t r, int32_t c) const {
     if (c < 0 || c >= n) return -1;
@@ -108,6 +180,11 @@ int build_symbolic(const hsde_problem* P, Symbolic& S, std::string& err) {
     std::vector<std::vector<int32_t>> cand;     // K_v in elimination order (sorted)
     cand.reserve(n);
     std::vector<char> alive(n, 1);
+    // a vertex's neighbourhood is the sorted vector adj[v] or, once it is
+    // large, the hash set big[v] (is_big[v]); the sets are the same either way
+    std::vector<VSet> big(n);
+    std::vector<char> is_big(n, 0);
+    auto degree = [&](int32_t v) -> int64_t { return is_big[v] ? (int64_t)big[v].size() : (int64_t)adj[v].size(); };
     using QE = std::pair<int64_t, int32_t>;
     std::priority_queue<QE, std::vector<QE>, std::greater<QE>> heap;
     for (int32_t v = 0; v < n; ++v) heap.push({(int64_t)adj[v].size(), v});
@@ -116,8 +193,14 @@ int build_symbolic(const hsde_problem* P, Symbolic& S, std::string& err) {
         const QE top = heap.top();
         heap.pop();
         const int32_t v = top.second;
-        if (!alive[v] || top.first != (int64_t)adj[v].size()) continue;
-        std::vector<int32_t> nb = std::move(adj[v]);
+        if (!alive[v] || top.first != degree(v)) continue;
+        std::vector<int32_t> nb;
+        if (is_big[v]) {
+            big[v].to_sorted(nb);
+            big[v] = VSet();
+        } else {
+            nb = std::move(adj[v]);
+        }
         adj[v].clear();
         S.order.push_back(v);
         std::vector<int32_t> K = nb;
@@ -125,17 +208,28 @@ int build_symbolic(const hsde_problem* P, Symbolic& S, std::string& err) {
         cand.push_back(std::move(K));
         alive[v] = 0;
         for (int32_t u : nb) {
+            // N(u) <- (N(u) U N(v)) minus {u, v}
+            if (is_big[u]) {
+                for (int32_t w : nb)
+                    if (w != u) big[u].insert(w);
+                big[u].erase(v);
+                continue;
+            }
             auto& au = adj[u];
             merged.clear();
             merged.reserve(au.size() + nb.size());
             std::set_union(au.begin(), au.end(), nb.begin(), nb.end(), std::back_inserter(merged));
-            // drop u itself and the eliminated v
             merged.erase(std::remove_if(merged.begin(), merged.end(),
                                         [&](int32_t w) { return w == u || w == v; }),
                          merged.end());
             au.swap(merged);
+            if (au.size() > BIG_DEGREE) {
+                for (int32_t w : au) big[u].insert(w);
+                is_big[u] = 1;
+                std::vector<int32_t>().swap(au);
+            }
         }
-        for (int32_t u : nb) heap.push({(int64_t)adj[u].size(), u});
+        for (int32_t u : nb) heap.push({degree(u), u});
     }
 
     // ---- maximal cliques ----

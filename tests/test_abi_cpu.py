@@ -126,3 +126,29 @@ def test_clique_beyond_the_largest_eigensolver_is_rejected(hs):
         hs.Handle(p)
     assert ei.value.code == hs.HSDE_ERANGE
     assert str(big) in str(ei.value)
+
+
+def test_large_block_arrow_structure_closed_form(hs):
+    """The l = 2000, d = 50, h = 5 block-arrow (n = 100,005; the arrow rows are
+    adjacent to every vertex): zero fill, the cliques are block_j U arrow in
+    block order, N = l (d(d+1)/2 + d h) + h(h+1)/2, and D counts l cliques on
+    the arrow corner and one elsewhere.  Also a guard on the analysis time:
+    the arrow rows once made it quadratic in n."""
+    import time
+    l, d, h = 2000, 50, 5
+    p = synth.block_arrow_sweep(l, d, h)
+    t0 = time.perf_counter()
+    st = hs.hsde_analyze(p)
+    dt = time.perf_counter() - t0
+    n = l * d + h
+    assert st["p"] == l and st["c_max"] == d + h
+    assert st["N"] == l * (d * (d + 1) // 2 + d * h) + h * (h + 1) // 2
+    ptr, idx = st["clique_ptr"], st["clique_idx"]
+    arrow = np.arange(n - h, n)
+    for j in (0, 1, l // 2, l - 1):
+        mem = idx[ptr[j]:ptr[j + 1]]
+        assert np.array_equal(mem, np.concatenate([np.arange(j * d, (j + 1) * d), arrow]))
+    col = np.repeat(np.arange(n), np.diff(st["pat_colptr"]))
+    corner = (st["pat_row"] >= n - h) & (col >= n - h)
+    assert np.all(st["D"][corner] == l) and np.all(st["D"][~corner] == 1)
+    assert dt < 20.0, dt
