@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Throughput of the HSDE-ADMM hot path on one GB300 (or N, one process each).
 
-Workload (default): the max-cut SDP on the open 20 x 100 grid, n = 2000,
+Workload (headline): the max-cut SDP on the open 20 x 100 grid, n = 2000,
 m = 2000 (diag(X) = 1), C the weighted Laplacian with +-1 weights, made
 chordal by exact minimum degree: 1530 cliques of size 3..45.  It stands in
 for the maxG32 row of Tables 1 and 3 (SDPLIB is not available).
@@ -11,8 +11,19 @@ S^{-1} solve, rank-one correction, clique eigen-projections, nu update and
 the stopping-rule reductions.  The timed region replays the library's CUDA
 graph one iteration at a time with CUDA events on the launching stream; the
 L2 cache (129 MB) is flushed by writing a 512 MB buffer between steps,
-outside the timed events.  `value` is mixed-precision iterations/s (all ranks);
-the plain FP64 form is timed the same way and reported beside it.
+outside the timed events.  `value` is mixed-precision iterations/s (all
+ranks), timed without the in-graph phase events; phase times come from a
+separate profiled pass.  The run uses the library's default form
+(over-relaxation and data scaling); before the timed window the iteration
+runs `--settle` untimed steps so that the eigensolver's warm start has
+settled (its sweeps per clique are reported beside the value).
+
+Further legs (each a key of the one JSON line): the plain FP64 form (with
+and without the warm start), time to the 1e-4 verdict, the end-to-end rate
+through the C-ABI with host buffers, the 256-instance serving batch, the
+n = 50 block-arrow and its infeasible copy, the l = 2000, d = 50 block-arrow
+(the eigensolve throughput case, with its roofline), and the gradient of
+the objective after 200 unrolled iterations.
 
 Prints ONE JSON line (rank 0).
 """
@@ -35,7 +46,33 @@ if ROOT not in sys.path:
 METRIC = "ADMM iters/s & time to 1e-4 residual: batched FP32 vs plain FP64 form, 1 GB300"
 UNIT = "iterations/s"
 WORKLOAD = "maxcut_grid20x100_n2000_m2000"
+NEVER = 1e-300        # eps_tol of the throughput handles: they never stop on a verdict
+BIG = 1 << 30         # their max_iter
 
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--settle", type=int, default=100,
+                    help="untimed iterations before the warm-up (lets the eigensolver warm start settle)")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--oracle-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=0, help="0: same as --steps")
+    ap.add_argument("--skip-verdict", action="store_true", help="skip the time-to-verdict and e2e legs")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-instance batched leg")
+    ap.add_argument("--batched-steps", type=int, default=30)
+    ap.add_argument("--only-batched", action="store_true", help="run only the batched leg (profiling)")
+    ap.add_argument("--batched-instances", type=int, default=0,
+                    help="0: all 256; else the first k instances (smaller profiling case)")
+    ap.add_argument("--no-legs", action="store_true", help="skip the n = 50, l = 2000 and gradient legs")
+    ap.add_argument("--only-leg", default="", help="run one leg only: arrow2000, n50, gradient (profiling)")
+    ap.add_argument("--arrow-l", type=int, default=2000, help="l of the eigensolve-throughput block-arrow leg")
+    ap.add_argument("--arrow-d", type=int, default=50)
+    ap.add_argument("--arrow-steps", type=int, default=20)
+    return ap.parse_args()
 
 
 def sweep_stats(phases):
@@ -49,33 +86,16 @@ def sweep_stats(phases):
                          if k.startswith("cone_") and a[2]}
     return out
 
-def parse():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--oracle-seconds", type=float, default=12.0)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--fp64-steps", type=int, default=0, help="0: same as --steps")
-    ap.add_argument("--skip-verdict", action="store_true", help="skip the time-to-verdict and e2e legs")
-    ap.add_argument("--no-batched", action="store_true", help="skip the 256-instance batched leg")
-    ap.add_argument("--batched-steps", type=int, default=30)
-    ap.add_argument("--only-batched", action="store_true", help="run only the batched leg (profiling)")
-    ap.add_argument("--batched-instances", type=int, default=0,
-                    help="0: all 256; else the first k instances (smaller profiling case)")
-    return ap.parse_args()
-
 
 # ----------------------------------------------------------------------------
-# CPU oracle sample (fresh process, single-threaded BLAS)
+# CPU oracle sample (fresh process; BLAS threads as asked)
 # ----------------------------------------------------------------------------
 ORACLE_SNIPPET = r"""
 import json, os, sys, time
 sys.path.insert(0, {root!r})
 import synth
 from oracle import hsde
-p = synth.maxcut_grid_instance(instance={inst})
+p = {make}
 t0 = time.perf_counter()
 ref = hsde.HSDE(p)
 setup_s = time.perf_counter() - t0
@@ -99,15 +119,27 @@ print(json.dumps(dict(iters=it, seconds=el, setup_s=setup_s, sizes=sizes)))
 """
 
 
-def oracle_sample(seconds, warm=2, min_it=3, max_it=100000, inst=0):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    code = ORACLE_SNIPPET.format(root=ROOT, warm=warm, secs=seconds, min_it=min_it, max_it=max_it, inst=inst)
+def oracle_sample(seconds, warm=2, min_it=3, max_it=100000, make="synth.maxcut_grid_instance(instance=0)", threads=1,
+                  solve=False):
+    """Oracle iterations/s on the host cores (threads = BLAS threads).  With
+    solve=True it runs to its verdict instead and reports the time."""
+    n = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=n, OPENBLAS_NUM_THREADS=n, MKL_NUM_THREADS=n, CUDA_VISIBLE_DEVICES="")
+    if solve:
+        code = (f"import json, sys, time\nsys.path.insert(0, {ROOT!r})\nimport synth\nfrom oracle import hsde\n"
+                f"p = {make}\nt0 = time.perf_counter()\nref = hsde.HSDE(p)\nt1 = time.perf_counter()\n"
+                f"r = ref.solve()\nt2 = time.perf_counter()\n"
+                f"print(json.dumps(dict(verdict=hsde.STATUS_NAMES[r.status], iterations=r.iterations, "
+                f"seconds=t2 - t1, setup_s=t1 - t0, pobj=r.info.get('pobj'))))\n")
+    else:
+        code = ORACLE_SNIPPET.format(root=ROOT, warm=warm, secs=seconds, min_it=min_it, max_it=max_it, make=make)
     res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if res.returncode != 0:
         raise RuntimeError("oracle sample failed: " + res.stderr[-2000:])
     d = json.loads(res.stdout.strip().splitlines()[-1])
-    d["value"] = d["iters"] / d["seconds"]
+    if not solve:
+        d["value"] = d["iters"] / d["seconds"]
+    d["threads"] = threads
     return d
 
 
@@ -189,10 +221,12 @@ def post_bytes(sizes, mixed, nnzA):
 
 
 def load_peaks():
+    """(peaks, source): the measured MEASURED_PEAKS.json, else the
+    recipe's fallback (6.8 TB/s copy, 1.9 PFLOP/s bf16 burst)."""
     try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "of measured"
     except Exception:
-        return None
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "of fallback"
 
 
 def fp32_peak_tflops(sm_mhz):
@@ -226,6 +260,33 @@ def traffic_from_profile(kernel_tag):
         return None
 
 
+def phase_roofline(phases, sizes_list, nnzA_list, mixed, traffic_tag=None):
+    """Roofline of the dominant phase of a profiled pass: the cone buckets
+    against the FP32 ALU peak (algorithmic 11 c^3 per clique), the affine and
+    post phases against HBM (algorithmic bytes of every instance)."""
+    peaks, src = load_peaks()
+    avg = {k: (a[0] / a[2], a[1]) for k, a in phases.items() if k not in ("iteration", "_sweeps_mean") and a[2]}
+    dom = max(avg, key=lambda k: avg[k][0])
+    dom_ms, dom_units = avg[dom]
+    if dom.startswith("cone_"):
+        peak = fp32_peak_tflops(2070.0)
+        ach = cone_flops(dom_units) / (dom_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": f"k_cone ({dom}, {'FP32' if mixed else 'FP64'} Jacobi)", "achieved": ach,
+                "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (max SM clock)",
+                "algorithmic_flops_per_launch": cone_flops(dom_units)}
+    else:
+        peak = peaks.get("hbm_gbs", 6800.0)
+        fn = affine_bytes if dom == "affine" else post_bytes
+        byts = sum(fn(sz, mixed, nz) for sz, nz in zip(sizes_list, nnzA_list))
+        ach = byts / (dom_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "peak_source": f"hbm_gbs (burst copy), {src}", "algorithmic_bytes_per_launch": byts}
+    roof["traffic"] = traffic_from_profile(traffic_tag.format(dom=dom)) if traffic_tag else None
+    roof["phase_ms"] = dom_ms
+    return roof, {k: round(v[0] * 1e3, 2) for k, v in avg.items()}
+
+
 def workload_config(n, m, p, c_max, N, P, precision, l2, world):
     """The `config` of both arms' JSON lines (same keys, same workload)."""
     return {"workload": WORKLOAD, "n": int(n), "m": int(m), "cliques": int(p), "c_max": int(c_max),
@@ -256,48 +317,53 @@ def replica_throughput(world, units_per_rank, seconds):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
-def run_ours(args):
-    import numpy as np
-    import torch
-    import torch.distributed as dist
+class Runner:
+    """Device, stream, L2 flush buffer and the timed loop shared by the legs."""
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    def __init__(self, world, rank, local):
+        import torch
+        import torch.distributed as dist
+        self.torch, self.dist = torch, dist
+        self.world, self.rank, self.local = world, rank, local
+        torch.cuda.set_device(local)
+        self.dev = torch.device("cuda", local)
+        # a real stream shared by the library, the L2 flush and the timing
+        # events (torch's default stream is the legacy NULL stream)
+        self.stream = torch.cuda.Stream(self.dev)
+        torch.cuda.set_stream(self.stream)
+        self.flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=self.dev)
+        from paper_1611_01828_gb300 import hsde
+        self.hsde = hsde
 
-    import synth
-    from paper_1611_01828_gb300 import hsde
+    def handle(self, probs, **kw):
+        return self.hsde.Handle(probs, cuda_stream=self.stream.cuda_stream, **kw)
 
-    prob = synth.maxcut_grid_instance(instance=rank)
-    # a real stream shared by the library, the L2 flush and the timing events
-    # (torch's default stream is the legacy NULL stream)
-    stream = torch.cuda.Stream(dev)
-    torch.cuda.set_stream(stream)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    def barrier(self):
+        self.torch.cuda.synchronize(self.dev)
+        if self.world > 1:
+            self.dist.barrier()
+        self.torch.cuda.synchronize(self.dev)
 
-    def barrier():
-        torch.cuda.synchronize(dev)
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-
-    def timed_steps(H, K, W, profile):
+    def timed_steps(self, H, K, W, profile=False, settle=0):
+        """`settle` untimed iterations, W warm-up iterations, then K timed
+        ones, each between two CUDA events on the library's stream, with the
+        L2 flushed before each (outside the events).  With profile=True the
+        handle's in-graph phase events are read after every step."""
+        torch = self.torch
+        if settle > 0:
+            H.hsde_iterate(settle, want_status=False)
         for _ in range(W):
-            flush.zero_()
+            self.flush.zero_()
             H.hsde_iterate(1, want_status=False)
-        torch.cuda.synchronize(dev)
+        torch.cuda.synchronize(self.dev)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         phases = {}
-        barrier()
+        self.barrier()
         for i in range(K):
-            flush.zero_()
-            ev[i][0].record(stream)
+            self.flush.zero_()
+            ev[i][0].record(self.stream)
             H.hsde_iterate(1, want_status=False)
-            ev[i][1].record(stream)
+            ev[i][1].record(self.stream)
             if profile:
                 pr = H.hsde_get_profile()
                 for k, (ms, units) in pr["phases"].items():
@@ -308,216 +374,322 @@ def run_ours(args):
                 sw = phases.setdefault("_sweeps_mean", [0.0, 0, 0, 0])
                 sw[0] += pr["sweeps_mean"]
                 sw[2] += 1
-        barrier()
-        total_ms = sum(a.elapsed_time(b) for a, b in ev)
-        return total_ms, phases
+        self.barrier()
+        return sum(a.elapsed_time(b) for a, b in ev), phases
 
-    if args.only_batched:
-        print(json.dumps({"batched": batched_leg(args, hsde, torch, dev, stream, timed_steps)}), flush=True)
-        return
-    big = 1 << 30
+    def to_verdict(self, probs, prec, chunk=50, **kw):
+        """Wall time from the standard start to every instance's verdict with
+        the default options (eps 1e-4, at most 2000 iterations)."""
+        H = self.handle(probs, precision=prec, **kw)
+        self.torch.cuda.synchronize(self.dev)
+        t0 = time.perf_counter()
+        st = H.solve(chunk=chunk)
+        dt = time.perf_counter() - t0
+        infos = [H.hsde_get_info(i) for i in range(H.B)]
+        H.close()
+        return st, infos, dt
+
+
+def headline_leg(R, args, prob):
+    """The max-cut grid: mixed iterations/s (the value), a profiled pass for
+    the phase split and roofline, the FP64 form with and without the warm
+    start, time to the verdict, and the end-to-end rate through the C-ABI."""
+    hsde = R.hsde
     t0 = time.perf_counter()
-    Hm = hsde.Handle(prob, precision="mixed", profile=1, max_iter=big,
-                     cuda_stream=stream.cuda_stream)
-    setup_mixed_ms = (time.perf_counter() - t0) * 1e3
+    Hm = R.handle(prob, precision="mixed", profile=0, max_iter=BIG, eps_tol=NEVER)
+    setup_ms = (time.perf_counter() - t0) * 1e3
     sizes = Hm.sizes[0]
-    nnzA = int(prob.A_ptr[-1])
     kern_per_it = Hm.hsde_get_profile()["kernels_per_iteration"]
-
-    clocks = Clocks(local)
+    clocks = Clocks(R.local)
     clocks.start()
-    mixed_ms, phases = timed_steps(Hm, args.steps, args.warmup, True)
+    mixed_ms, _ = R.timed_steps(Hm, args.steps, args.warmup, settle=args.settle)
     ck = clocks.stop()
+    pr = Hm.hsde_get_profile()
+    sweeps_last = {"mean_per_clique": round(pr["sweeps_mean"], 3), "max": pr["sweeps_max"]}
     st = Hm.hsde_iterate(0)
     assert int(st[0]) == hsde.RUNNING, "instance stopped during the timed steps"
-
-    K64 = args.fp64_steps or args.steps
-    Hd = hsde.Handle(prob, precision="fp64", profile=0, max_iter=big, warm_start=0,
-                     cuda_stream=stream.cuda_stream)
-    fp64_ms, _ = timed_steps(Hd, K64, args.warmup, False)
-    Hd.close()
-
-    # time to the 1e-4 verdict (defaults: eps 1e-4, at most 2000 iterations)
-    def to_verdict(prec):
-        H = hsde.Handle(prob, precision=prec, cuda_stream=stream.cuda_stream,
-                        warm_start=(0 if prec == "fp64" else -1))
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        st = H.solve(chunk=50)
-        dt = time.perf_counter() - t0
-        info = H.hsde_get_info(0)
-        H.close()
-        return dict(verdict=hsde.STATUS_NAMES[int(st[0])], iterations=info["iterations"], seconds=dt,
-                    pobj=info["pobj"], pres=info["pres"], dres=info["dres"], gap=info["gap"])
-
-    ttv_mixed = to_verdict("mixed") if not args.skip_verdict else None
-    ttv_fp64 = to_verdict("fp64") if not args.skip_verdict else None
-
-    # e2e through the C-ABI with pinned host buffers: per step the iterate goes
-    # host -> device (hsde_set_state), one iteration runs, and the iterate
-    # comes back device -> host (hsde_get_state).
-    L = int(sizes.state_len)
-    hbuf = torch.empty(L, dtype=torch.float64, pin_memory=True).numpy()
-    hbuf[:] = Hm.hsde_get_state(0)
-    it0 = Hm.hsde_get_info(0)["iterations"]
-    Ke = max(20, args.steps // 4) if not args.skip_verdict else 3
-    for _ in range(3):
-        Hm.hsde_set_state(0, hbuf, it0)
-        Hm.hsde_iterate(1, want_status=False)
-        hbuf[:] = Hm.hsde_get_state(0)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(Ke):
-        Hm.hsde_set_state(0, hbuf, it0)
-        Hm.hsde_iterate(1, want_status=False)
-        hbuf[:] = Hm.hsde_get_state(0)
-    torch.cuda.synchronize(dev)
-    e2e_s = time.perf_counter() - t0
-    barrier()
     Hm.close()
 
-    batched = None if args.no_batched else batched_leg(args, hsde, torch, dev, stream, timed_steps)
+    # profiled pass (in-graph events around every phase): phase split, roofline
+    Hp = R.handle(prob, precision="mixed", profile=1, max_iter=BIG, eps_tol=NEVER)
+    _, phases = R.timed_steps(Hp, max(20, args.steps // 4), args.warmup, profile=True, settle=args.settle)
+    Hp.close()
+    nnzA = int(prob.A_ptr[-1])
+    roof, phase_us = phase_roofline(phases, [sizes], [nnzA], True, traffic_tag="k_{dom}_maxcut_grid20x100")
 
-    # aggregate over ranks (max time)
-    mixed_ms, fp64_ms, e2e_s = reduce_max_over_ranks([mixed_ms, fp64_ms, e2e_s], world, dev)
+    # FP64: the plain form (cold-start Jacobi) and with the same warm start
+    K64 = args.fp64_steps or args.steps
+    fp64 = {}
+    for tag, warm in (("plain", 0), ("warm_start", 1)):
+        Hd = R.handle(prob, precision="fp64", profile=0, max_iter=BIG, eps_tol=NEVER, warm_start=warm)
+        ms, _ = R.timed_steps(Hd, K64, args.warmup, settle=args.settle)
+        Hd.close()
+        fp64[tag] = ms
+
+    ttv = None
+    if not args.skip_verdict:
+        ttv = {"eps_tol": 1e-4, "max_iter": 2000}
+        for prec in ("mixed", "fp64"):
+            st, infos, dt = R.to_verdict(prob, prec)
+            i = infos[0]
+            ttv[prec] = dict(verdict=hsde.STATUS_NAMES[int(st[0])], iterations=i["iterations"], seconds=dt,
+                             pobj=i["pobj"], pres=i["pres"], dres=i["dres"], gap=i["gap"])
+
+    # e2e through the C-ABI with pinned host buffers: per step the iterate
+    # goes host -> device (hsde_set_state), one iteration runs, and the
+    # iterate comes back device -> host (hsde_get_state).
+    He = R.handle(prob, precision="mixed", max_iter=BIG, eps_tol=NEVER)
+    He.hsde_iterate(args.settle, want_status=False)
+    L = int(sizes.state_len)
+    hbuf = R.torch.empty(L, dtype=R.torch.float64, pin_memory=True).numpy()
+    hbuf[:] = He.hsde_get_state(0)
+    it0 = He.hsde_get_info(0)["iterations"]
+    Ke = max(20, args.steps // 4) if not args.skip_verdict else 3
+    for _ in range(3):
+        He.hsde_set_state(0, hbuf, it0)
+        He.hsde_iterate(1, want_status=False)
+        hbuf[:] = He.hsde_get_state(0)
+    R.barrier()
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        He.hsde_set_state(0, hbuf, it0)
+        He.hsde_iterate(1, want_status=False)
+        hbuf[:] = He.hsde_get_state(0)
+    R.torch.cuda.synchronize(R.dev)
+    e2e_s = time.perf_counter() - t0
+    R.barrier()
+    He.close()
+    return dict(sizes=sizes, setup_ms=setup_ms, kern_per_it=kern_per_it, clocks=ck, mixed_ms=mixed_ms,
+                sweeps_last=sweeps_last, phases=phases, roof=roof, phase_us=phase_us, fp64=fp64, K64=K64,
+                ttv=ttv, e2e_s=e2e_s, Ke=Ke, L=L)
+
+
+def batched_leg(R, args):
+    """All 256 instances of the batched-serving configuration in one handle:
+    grids and block-arrows with n ~ U[100, 1500], 10% primal- and 10%
+    dual-infeasible.  A step is one ADMM iteration of every instance."""
+    import synth
+    hsde = R.hsde
+    t0 = time.perf_counter()
+    sel = range(args.batched_instances) if args.batched_instances > 0 else None
+    probs = synth.serving_batch(seed_instance=R.rank, select=sel)
+    gen_s = time.perf_counter() - t0
+    B = len(probs)
+    t0 = time.perf_counter()
+    H = R.handle(probs, precision="mixed", profile=0, max_iter=BIG, eps_tol=NEVER)
+    setup_s = time.perf_counter() - t0
+    K = args.batched_steps
+    ms, _ = R.timed_steps(H, K, 3)
+    kern = H.hsde_get_profile()["kernels_per_iteration"]
+    sizes = list(H.sizes)
+    H.close()
+    Hp = R.handle(probs, precision="mixed", profile=1, max_iter=BIG, eps_tol=NEVER)
+    _, phases = R.timed_steps(Hp, max(5, K // 3), 2, profile=True)
+    Hp.close()
+    (ms,) = reduce_max_over_ranks([ms], R.world, R.dev)
+    value = replica_throughput(R.world, B * K, ms / 1e3)
+    roof, phase_us = phase_roofline(phases, sizes, [int(p.A_ptr[-1]) for p in probs], True)
+    # the FP64 form, same batch: plain (cold Jacobi) and with the warm start
+    K64 = max(3, K // 6)
+    f64 = {}
+    for tag, warm in (("plain", 0), ("warm_start", 1)):
+        Hd = R.handle(probs, precision="fp64", warm_start=warm, max_iter=BIG, eps_tol=NEVER)
+        ms64, _ = R.timed_steps(Hd, K64, 2)
+        Hd.close()
+        f64[tag] = B * K64 / (ms64 / 1e3)
+    # every instance to its verdict (defaults: eps 1e-4, at most 2000 iterations)
+    st, infos, ttv = R.to_verdict(probs, "mixed", chunk=100)
+    names = [hsde.STATUS_NAMES[int(x)] for x in st]
+    want = {"feasible": "solved", "primal_infeasible": "primal_infeasible", "dual_infeasible": "dual_infeasible"}
+    resolved = [(p, nm) for p, nm in zip(probs, names) if nm != "max_iter"]
+    agree = sum(1 for p, nm in resolved if nm == want[p.kind])
+    return {"workload": f"batch{B}_grid_and_block_arrow_n100-1500", "instances": B,
+            "value": value, "unit": "instance-iterations/s", "ms_per_step": ms / K, "steps": K,
+            "fp64": {"plain": f64["plain"], "warm_start": f64["warm_start"], "steps": K64},
+            "mixed_over_fp64": {"plain": value / f64["plain"], "warm_start_matched": value / f64["warm_start"]},
+            "setup_s": setup_s, "generate_s": gen_s, "kernels_per_iteration": kern,
+            "phase_us": phase_us, "jacobi_sweeps": sweep_stats(phases), "roofline": roof,
+            "time_to_all_verdicts_s": ttv, "max_iterations": max(i["iterations"] for i in infos),
+            "verdicts": {"solved": names.count("solved"),
+                         "certified_infeasible": names.count("primal_infeasible") + names.count("dual_infeasible"),
+                         "unresolved_max_iter": names.count("max_iter"),
+                         "numerical_error": names.count("numerical_error"),
+                         "by_kind": {k: names.count(k) for k in sorted(set(names))}},
+            "resolved_agreeing_with_construction": f"{agree}/{len(resolved)}",
+            "l2": "working set > L2 (S^-1 of the block-arrows) and flushed between steps"}
+
+
+def n50_leg(R):
+    """The n = 50 block-arrow (8 cliques of 8, m = 20) and its copy with
+    tr X = -1 appended: time to the verdict, mixed and FP64 on the GPU, and
+    the oracle on one host core."""
+    import synth
+    out = {}
+    for tag, inf in (("feasible", False), ("primal_infeasible", True)):
+        p = synth.block_arrow_n50(inf)
+        row = {}
+        for prec in ("mixed", "fp64"):
+            st, infos, dt = R.to_verdict(p, prec, chunk=25)
+            row[prec] = dict(verdict=R.hsde.STATUS_NAMES[int(st[0])], iterations=infos[0]["iterations"],
+                             seconds=dt, pobj=infos[0]["pobj"])
+        if R.rank == 0:
+            d = oracle_sample(0, make=f"synth.block_arrow_n50({inf})", solve=True)
+            row["oracle_1core"] = dict(verdict=d["verdict"], iterations=d["iterations"], seconds=d["seconds"],
+                                       pobj=d["pobj"])
+        out[tag] = row
+    return out
+
+
+def arrow_leg(R, args):
+    """The block-arrow with l blocks of d plus an arrow of 5 (default l = 2000,
+    d = 50: 2000 cliques of 55, N = 3.05M pattern entries, m = 4000 with a
+    dense 4000 x 4000 S): the eigensolve throughput case.  Mixed and FP64
+    iterations/s, the phase split and the roofline of the dominant phase,
+    setup time, and the mixed run to its verdict."""
+    import synth
+    l, d = args.arrow_l, args.arrow_d
+    t0 = time.perf_counter()
+    p = synth.block_arrow_sweep(l, d)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    H = R.handle(p, precision="mixed", profile=0, max_iter=BIG, eps_tol=NEVER)
+    setup_s = time.perf_counter() - t0
+    sizes = H.sizes[0]
+    K = args.arrow_steps
+    ms, _ = R.timed_steps(H, K, 3, settle=20)
+    H.close()
+    Hp = R.handle(p, precision="mixed", profile=1, max_iter=BIG, eps_tol=NEVER)
+    _, phases = R.timed_steps(Hp, max(5, K // 2), 2, profile=True, settle=20)
+    Hp.close()
+    roof, phase_us = phase_roofline(phases, [sizes], [int(p.A_ptr[-1])], True,
+                                    traffic_tag=f"k_{{dom}}_block_arrow_l{l}_d{d}")
+    f64 = {}
+    for tag, warm in (("plain", 0), ("warm_start", 1)):
+        Hd = R.handle(p, precision="fp64", warm_start=warm, max_iter=BIG, eps_tol=NEVER)
+        m64, ph64 = R.timed_steps(Hd, max(3, K // 4), 2, settle=5)
+        Hd.close()
+        f64[tag] = max(3, K // 4) / (m64 / 1e3)
+    st, infos, ttv = R.to_verdict(p, "mixed", chunk=100)
+    v = K / (ms / 1e3)
+    return {"workload": f"block_arrow_l{l}_d{d}_h5", "n": int(sizes.n), "m": int(sizes.m), "cliques": int(sizes.p),
+            "c_max": int(sizes.c_max), "N_pattern_lower": int(sizes.N), "P_packed": int(sizes.P),
+            "S_dense": int(sizes.S_dense), "value": v, "unit": UNIT, "steps": K, "ms_per_step": ms / K,
+            "fp64": f64, "mixed_over_fp64": {"plain": v / f64["plain"], "warm_start_matched": v / f64["warm_start"]},
+            "setup_s": setup_s, "generate_s": gen_s, "phase_us": phase_us, "jacobi_sweeps": sweep_stats(phases),
+            "roofline": roof,
+            "time_to_verdict": dict(verdict=R.hsde.STATUS_NAMES[int(st[0])], iterations=infos[0]["iterations"],
+                                    seconds=ttv, pobj=infos[0]["pobj"], pres=infos[0]["pres"],
+                                    dres=infos[0]["dres"])}
+
+
+def gradient_leg(R):
+    """Gradient of f(C, b) = c^T x_K / (tau_K + kappa_K) after K = 200
+    unrolled iterations (checkpoint every 20) on the n = 1000 max-cut grid,
+    through the library's forward and reverse sweeps, FP64 and mixed."""
+    import numpy as np
+    import synth
+    from paper_1611_01828_gb300 import unrolled
+    p = synth.differentiation_maxcut_grid()
+    out = {"workload": "maxcut_grid10x100_n1000", "K": 200, "checkpoint_every": 20}
+    for prec in ("fp64", "mixed"):
+        H = R.handle(p, precision=prec, **unrolled.LITERAL)
+        c0 = unrolled.pattern_values(H, p.C_row, p.C_col, p.C_val)
+        H.hsde_set_data(0, c0, p.b)
+        H.hsde_unrolled_forward(200, 20)          # warm-up (allocates the workspace)
+        H.hsde_unrolled_backward(np.ones(H.sizes[0].N), np.zeros(H.sizes[0].m), 0.0, 0.0)
+        R.torch.cuda.synchronize(R.dev)
+        t0 = time.perf_counter()
+        x, y, tau, kappa = H.hsde_unrolled_forward(200, 20)
+        t1 = time.perf_counter()
+        H.hsde_unrolled_backward(np.ones(H.sizes[0].N), np.zeros(H.sizes[0].m), 0.0, 0.0)
+        t2 = time.perf_counter()
+        H.close()
+        out[prec] = {"forward_s": t1 - t0, "backward_s": t2 - t1, "total_s": t2 - t0}
+    return out
+
+
+def run_ours(args):
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    R = Runner(world, rank, local)
+    import synth
+
+    if args.only_batched or args.only_leg:
+        leg = {"batched": lambda: batched_leg(R, args), "arrow2000": lambda: arrow_leg(R, args),
+               "n50": lambda: n50_leg(R), "gradient": lambda: gradient_leg(R)}
+        key = "batched" if args.only_batched else args.only_leg
+        print(json.dumps({key: leg[key]()}), flush=True)
+        return
+
+    prob = synth.maxcut_grid_instance(instance=rank)
+    hl = headline_leg(R, args, prob)
+    batched = None if args.no_batched else batched_leg(R, args)
+    legs = {}
+    if not args.no_legs:
+        legs["n50"] = n50_leg(R)
+        legs["block_arrow"] = arrow_leg(R, args)
+        legs["gradient"] = gradient_leg(R)
+
+    mixed_ms, p_ms, w_ms, e2e_s = reduce_max_over_ranks(
+        [hl["mixed_ms"], hl["fp64"]["plain"], hl["fp64"]["warm_start"], hl["e2e_s"]], world, R.dev)
     value = replica_throughput(world, args.steps, mixed_ms / 1e3)
-    fp64_value = replica_throughput(world, K64, fp64_ms / 1e3)
-
-    # roofline of the dominant phase
-    peaks = load_peaks()
-    avg = {k: (a[0] / a[2], a[1]) for k, a in phases.items() if k not in ("iteration", "_sweeps_mean") and a[2]}
-    dom = max(avg, key=lambda k: avg[k][0])
-    dom_ms, dom_units = avg[dom]
-    if dom.startswith("cone_"):
-        sm_for_peak = 2070.0
-        peak = fp32_peak_tflops(sm_for_peak)
-        achieved = cone_flops(dom_units) / (dom_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": f"k_cone ({dom}, FP32 Jacobi)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (max SM clock)",
-                "traffic": traffic_from_profile(f"k_{dom}_maxcut_grid20x100"),
-                "phase_ms": dom_ms, "algorithmic_flops_per_launch": cone_flops(dom_units)}
-    else:
-        peak = (peaks or {}).get("hbm_gbs", 6800.0)
-        byts = affine_bytes(sizes, True, nnzA) if dom == "affine" else post_bytes(sizes, True, nnzA)
-        achieved = byts / (dom_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)",
-                "traffic": None, "phase_ms": dom_ms, "algorithmic_bytes_per_launch": byts}
-    phase_avg = {k: round(v[0] * 1e3, 2) for k, v in avg.items()}
-    phase_avg_it = phases.get("iteration")
-    if phase_avg_it:
-        phase_avg["iteration"] = round(phase_avg_it[0] / phase_avg_it[2] * 1e3, 2)
+    f64_plain = replica_throughput(world, hl["K64"], p_ms / 1e3)
+    f64_warm = replica_throughput(world, hl["K64"], w_ms / 1e3)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        d = oracle_sample(args.oracle_seconds)
-        cpu = {"value": d["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{d['iters']} oracle iterations of the same n=2000 max-cut instance "
-                         f"({d['seconds']:.1f} s, FP64 NumPy/SciPy, single-threaded BLAS, after 2 warm-up "
-                         f"iterations and {d['setup_s']:.1f} s setup)"}
+        d1 = oracle_sample(args.oracle_seconds, threads=1)
+        nall = os.cpu_count() or 1
+        dn = oracle_sample(args.oracle_seconds, threads=nall)
+        cpu = {"value": d1["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{d1['iters']} oracle iterations of the same n=2000 max-cut instance "
+                         f"({d1['seconds']:.1f} s, FP64 NumPy/SciPy, single-threaded BLAS, after 2 warm-up "
+                         f"iterations and {d1['setup_s']:.1f} s setup)",
+               "all_cores": {"value": dn["value"], "cores": nall,
+                             "sample": f"{dn['iters']} iterations in {dn['seconds']:.1f} s with {nall} BLAS threads"}}
 
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     if rank != 0:
         return
+    sizes = hl["sizes"]
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mixed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded; SDPLIB stand-in)",
         "config": workload_config(sizes.n, sizes.m, sizes.p, sizes.c_max, sizes.N, sizes.P,
-                                  "mixed: FP32 cone projections + gather/scatter, FP64 x/y/A/S^-1/reductions",
+                                  "mixed: FP32 cone projections + gather/scatter, FP64 x/y/A/S^-1/reductions; "
+                                  "over-relaxation 1.8 and data scaling (library defaults)",
                                   "flushed between steps (512 MB write, outside the timed events)", world),
-        "fp64_plain": {"value": fp64_value, "unit": UNIT, "ms_per_step": fp64_ms / K64, "steps": K64,
-                       "dtype": "f64", "form": "FP64 everywhere, cold-start Jacobi every iteration"},
-        "mixed_over_fp64": value / fp64_value,
-        "time_to_verdict": {"mixed": ttv_mixed, "fp64": ttv_fp64, "eps_tol": 1e-4, "max_iter": 2000},
-        "setup_ms": setup_mixed_ms,
-        "phase_us": phase_avg,
-        "jacobi_sweeps": sweep_stats(phases),
-        "roofline": roof,
+        "settle_iterations": args.settle,
+        "jacobi_sweeps_last_timed_iteration": hl["sweeps_last"],
+        "fp64": {"plain": {"value": f64_plain, "unit": UNIT, "ms_per_step": p_ms / hl["K64"], "steps": hl["K64"],
+                           "form": "FP64 everywhere, cold-start Jacobi every iteration"},
+                 "warm_start": {"value": f64_warm, "unit": UNIT, "ms_per_step": w_ms / hl["K64"],
+                                "form": "FP64 everywhere, eigensolver warm start as in the mixed form"}},
+        "mixed_over_fp64": {"plain": value / f64_plain, "warm_start_matched": value / f64_warm},
+        "time_to_verdict": hl["ttv"],
+        "setup_ms": hl["setup_ms"],
+        "phase_us": hl["phase_us"],
+        "jacobi_sweeps": sweep_stats(hl["phases"]),
+        "roofline": hl["roof"],
         "cpu_baseline": cpu,
-        "e2e": {"value": replica_throughput(world, Ke, e2e_s), "unit": UNIT, "h2d_bytes_per_step": L * 8, "d2h_bytes_per_step": L * 8,
+        "e2e": {"value": replica_throughput(world, hl["Ke"], e2e_s), "unit": UNIT,
+                "h2d_bytes_per_step": hl["L"] * 8, "d2h_bytes_per_step": hl["L"] * 8,
                 "how": "per step: hsde_set_state from pinned host memory, hsde_iterate(1), hsde_get_state to "
                        "pinned host memory (full iterate both ways)"},
         "batched": batched,
-        "gpu_launches": kern_per_it * (args.steps + 0),
-        "clocks": ck,
+        "legs": legs,
+        "gpu_launches": hl["kern_per_it"] * args.steps,
+        "clocks": hl["clocks"],
     }
     print(json.dumps(out), flush=True)
-
-
-def batched_leg(args, hsde, torch, dev, stream, timed_steps):
-    """All 256 instances of the batched-serving configuration in one handle:
-    grids and block-arrows with n ~ U[100, 1500], 10% primal- and 10%
-    dual-infeasible.  A step is one ADMM iteration of every instance."""
-    import synth
-    rank = int(os.environ.get("RANK", "0"))
-    t0 = time.perf_counter()
-    sel = range(args.batched_instances) if args.batched_instances > 0 else None
-    probs = synth.serving_batch(seed_instance=rank, select=sel)
-    gen_s = time.perf_counter() - t0
-    B = len(probs)
-    big = 1 << 30
-    t0 = time.perf_counter()
-    H = hsde.Handle(probs, precision="mixed", profile=1, max_iter=big, cuda_stream=stream.cuda_stream)
-    setup_s = time.perf_counter() - t0
-    K = args.batched_steps
-    ms, phases = timed_steps(H, K, 3, True)
-    kern = H.hsde_get_profile()["kernels_per_iteration"]
-    sizes = list(H.sizes)
-    H.close()
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    (ms,) = reduce_max_over_ranks([ms], world, dev)
-    value = replica_throughput(world, B * K, ms / 1e3)
-    avg = {k: (a[0] / a[2], a[1]) for k, a in phases.items() if k not in ("iteration", "_sweeps_mean") and a[2]}
-    dom = max(avg, key=lambda k: avg[k][0])
-    dom_ms, dom_units = avg[dom]
-    peaks = load_peaks() or {}
-    if dom.startswith("cone_"):
-        peak = fp32_peak_tflops(2070.0)
-        ach = cone_flops(dom_units) / (dom_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": f"k_cone ({dom}, FP32 Jacobi)", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach / peak, "phase_ms": dom_ms}
-    else:
-        peak = peaks.get("hbm_gbs", 6800.0)
-        fn = affine_bytes if dom == "affine" else post_bytes
-        byts = sum(fn(sz, True, int(p.A_ptr[-1])) for sz, p in zip(sizes, probs))
-        ach = byts / (dom_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "phase_ms": dom_ms, "algorithmic_bytes_per_launch": byts}
-    # plain FP64 form, same batch
-    Hd = hsde.Handle(probs, precision="fp64", warm_start=0, max_iter=big, cuda_stream=stream.cuda_stream)
-    K64 = max(3, K // 6)
-    ms64, _ = timed_steps(Hd, K64, 2, False)
-    Hd.close()
-    v64 = B * K64 / (ms64 / 1e3)
-    # every instance to its verdict (defaults: eps 1e-4, at most 2000 iterations)
-    Hv = hsde.Handle(probs, precision="mixed", cuda_stream=stream.cuda_stream)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    st = Hv.solve(chunk=100)
-    ttv = time.perf_counter() - t0
-    iters = [Hv.hsde_get_info(i)["iterations"] for i in range(B)]
-    Hv.close()
-    names = [hsde.STATUS_NAMES[int(x)] for x in st]
-    expect = {"feasible": ("solved", "max_iter"), "primal_infeasible": ("primal_infeasible",),
-              "dual_infeasible": ("dual_infeasible",)}
-    agree = sum(1 for p, nm in zip(probs, names) if nm in expect[p.kind])
-    return {"workload": f"batch{B}_grid_and_block_arrow_n100-1500", "instances": B,
-            "value": value, "unit": "instance-iterations/s", "ms_per_step": ms / K, "steps": K,
-            "fp64_plain": {"value": v64, "ms_per_step": ms64 / K64, "steps": K64},
-            "mixed_over_fp64": value / v64,
-            "setup_s": setup_s, "generate_s": gen_s, "kernels_per_iteration": kern,
-            "phase_us": {k: round(v[0] * 1e3, 1) for k, v in avg.items()},
-            "jacobi_sweeps": sweep_stats(phases),
-            "roofline": roof,
-            "time_to_all_verdicts_s": ttv, "max_iterations": max(iters),
-            "verdicts": {k: names.count(k) for k in sorted(set(names))},
-            "verdicts_consistent_with_construction": f"{agree}/{B}",
-            "l2": "working set > L2 (1.5 GB of S^-1) and flushed between steps"}
 
 
 def run_reference(args):

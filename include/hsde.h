@@ -154,7 +154,7 @@ typedef struct hsde_info {
     int32_t jacobi_unconverged_iterations;  /* iterations with at least one  */
 } hsde_info;
 
-#define HSDE_MAX_PHASES 16
+#define HSDE_MAX_PHASES 24
 typedef struct hsde_profile {
     int32_t kernels_per_iteration;   /* kernel launches in one iteration          */
     int32_t nphases;
@@ -258,7 +258,8 @@ HSDE_API int  hsde_get_solution(hsde_handle* h, int32_t i, double* X, double* y,
 HSDE_API int  hsde_get_certificate(hsde_handle* h, int32_t i, int32_t kind, double* y, double* Z,
                           double* X);
 
-/* Launch count of one iteration and, if the handle was set up with
+/* Launch count of one iteration, the Jacobi sweeps of the last iteration
+ * (mean per clique and most) and, if the handle was set up with
  * profile = 1, the device time of each phase of the last iteration (waits
  * for the handle's stream).  Phases: "affine" (A f, S^{-1}, A^T y_w, eta),
  * one "cone_cK" per clique bucket (cliques of size <= K, each on its own

@@ -247,8 +247,8 @@ struct hsde_handle {
     std::vector<int32_t> m_off;
     cudaStream_t st = nullptr;
     bool own_stream = false;
-    cudaStream_t side[10] = {};
-    cudaEvent_t ev_fork = nullptr, ev_join[10] = {};
+    cudaStream_t side[MAX_BUCKETS] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[MAX_BUCKETS] = {};
     void* arena = nullptr;
     size_t arena_bytes = 0;
     DevView V{};
@@ -264,7 +264,7 @@ struct hsde_handle {
     bool profile = false;
     bool capturing = false;
     cudaEvent_t ev_it0 = nullptr, ev_aff = nullptr, ev_chk = nullptr, ev_it1 = nullptr;
-    cudaEvent_t ev_cs[10] = {}, ev_ce[10] = {};
+    cudaEvent_t ev_cs[MAX_BUCKETS] = {}, ev_ce[MAX_BUCKETS] = {};
     std::vector<int64_t> bucket_c3;
     std::vector<std::vector<int32_t>> bucket_ids;   // host copy of each bucket's clique list
     int kernels_per_iter = 0;
@@ -713,9 +713,11 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
 
     // ---- clique buckets (largest cliques first) ----
     {
-        constexpr int NB = 9;
+        std::vector<int> caps;
+        cone_bucket_sizes(caps);
+        const int NB = (int)caps.size();
+        if (NB > MAX_BUCKETS) return fail(HSDE_ECUDA, "internal: more eigensolver buckets than graph branches");
         std::vector<std::vector<int32_t>> lists(NB);
-        const int caps[NB] = {4, 8, 12, 16, 24, 32, 40, 48, 64};
         std::vector<int32_t> ids(ncl);
         for (int64_t k = 0; k < ncl; ++k) ids[k] = (int32_t)k;
         std::stable_sort(ids.begin(), ids.end(), [&](int32_t a, int32_t b) { return hcls[a] > hcls[b]; });
@@ -1106,9 +1108,20 @@ int hsde_get_profile(hsde_handle* h, hsde_profile* out) {
     if (!h || !out) return fail(HSDE_EINVAL, "null argument");
     std::memset(out, 0, sizeof(*out));
     out->kernels_per_iteration = h->kernels_per_iter;
-    if (!h->profile || h->launched == 0) return HSDE_OK;
+    if (h->launched == 0) return HSDE_OK;
     CK(cudaSetDevice(h->device));
     CK(cudaStreamSynchronize(h->st));
+    // Jacobi sweeps of the last solve of every clique (with or without the
+    // phase events)
+    std::vector<int32_t> sw(h->V.ncl);
+    if (h->V.ncl > 0)
+        CK(cudaMemcpy(sw.data(), h->V.cl_sweeps, sizeof(int32_t) * sw.size(), cudaMemcpyDeviceToHost));
+    int64_t tot = 0;
+    int32_t mx = 0;
+    for (int32_t v : sw) { tot += v; mx = std::max(mx, v); }
+    out->sweeps_mean = sw.empty() ? 0.0 : (double)tot / (double)sw.size();
+    out->sweeps_max = mx;
+    if (!h->profile) return HSDE_OK;
     int np = 0;
     auto put = [&](const char* name, cudaEvent_t a, cudaEvent_t b, int64_t units) -> int {
         if (np >= HSDE_MAX_PHASES) return HSDE_OK;
@@ -1130,15 +1143,6 @@ int hsde_get_profile(hsde_handle* h, hsde_profile* out) {
     if ((rc = put("post", h->ev_chk, h->ev_it1, h->V.Ntot)) != HSDE_OK) return rc;
     if ((rc = put("iteration", h->ev_it0, h->ev_it1, h->V.Ntot)) != HSDE_OK) return rc;
     out->nphases = np;
-    // Jacobi sweeps of the last solve of every clique
-    std::vector<int32_t> sw(h->V.ncl);
-    if (h->V.ncl > 0)
-        CK(cudaMemcpy(sw.data(), h->V.cl_sweeps, sizeof(int32_t) * sw.size(), cudaMemcpyDeviceToHost));
-    int64_t tot = 0;
-    int32_t mx = 0;
-    for (int32_t v : sw) { tot += v; mx = std::max(mx, v); }
-    out->sweeps_mean = sw.empty() ? 0.0 : (double)tot / (double)sw.size();
-    out->sweeps_max = mx;
     // cone phases follow "affine" in bucket order
     for (size_t i = 0; i < h->buckets.size() && 1 + i < (size_t)HSDE_MAX_PHASES; ++i) {
         int32_t bm = 0;

@@ -666,8 +666,12 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
 // ---------------------------------------------------------------------------
 // buckets: padded size CP and threads per clique G
 // ---------------------------------------------------------------------------
-#define HSDE_CONE_BUCKETS(X) \
-    X(4, 4) X(8, 8) X(12, 16) X(16, 32) X(24, 96) X(32, 160) X(40, 224) X(48, 320) X(64, 544)
+// (padding a clique of c to CP costs about (CP/c)^3 of the work, so the
+// sizes are spaced by 4 above 16; G gives about one 2x2 block per thread and
+// round: K(K+1)/2 blocks, K = CP/2)
+#define HSDE_CONE_BUCKETS(X)                                                                     \
+    X(4, 4) X(8, 8) X(12, 16) X(16, 32) X(20, 64) X(24, 96) X(28, 128) X(32, 160) X(36, 192)   \
+    X(40, 224) X(44, 256) X(48, 320) X(56, 416) X(64, 544)
 
 // Device limits read by cone_prepare: opt-in shared memory per CTA, SMs.
 static int g_smem_optin = 0;
@@ -710,6 +714,13 @@ int cone_bucket_of(int c) {
     HSDE_CONE_BUCKETS(X)
 #undef X
     return -1;
+}
+
+void cone_bucket_sizes(std::vector<int>& out) {
+    out.clear();
+#define X(cp, g) out.push_back(cp);
+    HSDE_CONE_BUCKETS(X)
+#undef X
 }
 
 int cone_vstore_elems(int c) {

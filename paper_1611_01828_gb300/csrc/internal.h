@@ -153,6 +153,9 @@ struct RevArgs {
     double* gc; double* gb;
 };
 
+// Most eigensolver buckets (graph branches, side streams) of one handle.
+constexpr int MAX_BUCKETS = 16;
+
 // Bucket of cliques handled by one eigensolver variant.
 struct Bucket {
     int32_t cmax;            // padded size CP of the bucket (4 ... 64)
@@ -183,6 +186,7 @@ int  launch_cone(const DevView& V, const Bucket& bk, bool mixed, int max_sweeps,
                  int warm, int refresh, void* st);
 int  cone_smem_bytes(int cmax, bool mixed);
 int  cone_bucket_of(int c);          // padded size of the bucket of a clique of size c, -1 if none
+void cone_bucket_sizes(std::vector<int>& out);   // every bucket's padded size, ascending
 int  cone_vstore_elems(int c);       // stored basis size for a clique of size c
 bool cone_bucket_alone(const Bucket& bk, bool mixed);   // its CTAs each take a whole SM (launched first)
 int  cone_prepare(bool mixed);

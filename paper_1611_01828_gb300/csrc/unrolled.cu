@@ -402,8 +402,10 @@ void launch_apply(const DevView& V, const ApplyArgs& A, bool mixed, bool setup_o
     }
 }
 
-#define HSDE_REV_BUCKETS(X) \
-    X(4, 4) X(8, 8) X(12, 16) X(16, 32) X(24, 64) X(32, 128) X(40, 256) X(48, 512) X(64, 512)
+// the same padded sizes as the forward eigensolver's buckets (cone.cu)
+#define HSDE_REV_BUCKETS(X)                                                                     \
+    X(4, 4) X(8, 8) X(12, 16) X(16, 32) X(20, 64) X(24, 64) X(28, 128) X(32, 128) X(36, 256)   \
+    X(40, 256) X(44, 512) X(48, 512) X(56, 512) X(64, 512)
 
 template <typename T, int CP, int G>
 static int rev_prepare_one() {

@@ -56,7 +56,7 @@ class hsde_info(C.Structure):
                 ("jacobi_unconverged", C.c_int32), ("jacobi_unconverged_iterations", C.c_int32)]
 
 
-MAX_PHASES = 16
+MAX_PHASES = 24
 
 
 class hsde_profile(C.Structure):

@@ -52,3 +52,64 @@ def test_noalloc_rejects_sizes_beyond_its_limit(env):
     rc = hsde.lib.hsde_spd_inverse_noalloc(ctypes.c_void_p(t.data_ptr()), 8193, ctypes.c_void_p(0))
     assert rc == hsde.HSDE_ERANGE
     assert b"8192" in hsde.lib.hsde_last_error()
+
+
+def _cudart():
+    """The CUDA runtime library, to read the device's default memory pool
+    (the pool cudaMallocAsync draws from); None if it cannot be found."""
+    import glob
+    import os
+    cands = []
+    try:
+        import torch
+        cands += glob.glob(os.path.join(os.path.dirname(torch.__file__), "lib", "libcudart.so*"))
+    except Exception:
+        pass
+    cands += glob.glob("/usr/local/cuda/lib64/libcudart.so*") + ["libcudart.so"]
+    for c in cands:
+        try:
+            return ctypes.CDLL(c)
+        except OSError:
+            continue
+    return None
+
+
+USED_MEM_HIGH = 8   # cudaMemPoolAttrUsedMemHigh
+
+
+def test_noalloc_allocates_nothing(env):
+    """The call itself must not allocate device memory: torch's allocator
+    statistics and the default memory pool's high-water mark of used memory
+    are unchanged across a call.  The allocating entry point is the control:
+    the same probe sees its 2m-double scratch."""
+    torch, hsde = env
+    m = 2000
+    stream = torch.cuda.current_stream().cuda_stream
+    a = torch.from_numpy(_spd(m, 21)).cuda()
+    b = a.clone()
+    assert hsde.lib.hsde_spd_inverse_noalloc(ctypes.c_void_p(b.data_ptr()), m, ctypes.c_void_p(stream)) == 0
+    torch.cuda.synchronize()                       # warm-up: the one-time symbol lookup
+    rt = _cudart()
+    pool = ctypes.c_void_p()
+    have_pool = rt is not None and rt.cudaDeviceGetDefaultMemPool(ctypes.byref(pool), torch.cuda.current_device()) == 0
+
+    def high_mark(call):
+        if have_pool:
+            zero = ctypes.c_uint64(0)
+            assert rt.cudaMemPoolSetAttribute(pool, USED_MEM_HIGH, ctypes.byref(zero)) == 0
+        alloc0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+        assert call() == 0
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == alloc0
+        if not have_pool:
+            return None
+        v = ctypes.c_uint64(0)
+        assert rt.cudaMemPoolGetAttribute(pool, USED_MEM_HIGH, ctypes.byref(v)) == 0
+        return v.value
+
+    control = high_mark(lambda: hsde.lib.hsde_spd_inverse(ctypes.c_void_p(a.data_ptr()), m, ctypes.c_void_p(stream)))
+    got = high_mark(lambda: hsde.lib.hsde_spd_inverse_noalloc(ctypes.c_void_p(b.data_ptr()), m,
+                                                              ctypes.c_void_p(stream)))
+    if have_pool:
+        assert control >= 2 * m * 8          # the probe sees the allocating variant's scratch
+        assert got == 0
