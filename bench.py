@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--arrow-l", type=int, default=2000, help="l of the eigensolve-throughput block-arrow leg")
     ap.add_argument("--arrow-d", type=int, default=50)
     ap.add_argument("--arrow-steps", type=int, default=20)
+    ap.add_argument("--arrow-quick", action="store_true",
+                    help="block-arrow leg: mixed timing only (no FP64, no run to the verdict; for profiling)")
     return ap.parse_args()
 
 
@@ -563,6 +565,10 @@ def arrow_leg(R, args):
     Hp.close()
     roof, phase_us = phase_roofline(phases, [sizes], [int(p.A_ptr[-1])], True,
                                     traffic_tag=f"k_{{dom}}_block_arrow_l{l}_d{d}")
+    v = K / (ms / 1e3)
+    if args.arrow_quick:
+        return {"workload": f"block_arrow_l{l}_d{d}_h5", "value": v, "unit": UNIT, "steps": K,
+                "ms_per_step": ms / K, "setup_s": setup_s, "phase_us": phase_us, "roofline": roof}
     f64 = {}
     for tag, warm in (("plain", 0), ("warm_start", 1)):
         Hd = R.handle(p, precision="fp64", warm_start=warm, max_iter=BIG, eps_tol=NEVER)
@@ -570,7 +576,6 @@ def arrow_leg(R, args):
         Hd.close()
         f64[tag] = max(3, K // 4) / (m64 / 1e3)
     st, infos, ttv = R.to_verdict(p, "mixed", chunk=100)
-    v = K / (ms / 1e3)
     return {"workload": f"block_arrow_l{l}_d{d}_h5", "n": int(sizes.n), "m": int(sizes.m), "cliques": int(sizes.p),
             "c_max": int(sizes.c_max), "N_pattern_lower": int(sizes.N), "P_packed": int(sizes.P),
             "S_dense": int(sizes.S_dense), "value": v, "unit": UNIT, "steps": K, "ms_per_step": ms / K,

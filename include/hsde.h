@@ -121,6 +121,13 @@ typedef struct hsde_options {
                              rho = dual_weight * sigma; 0 runs on the data as
                              given.  The stopping rule is always evaluated on
                              the unscaled iterate against the original data. */
+    int32_t structured_factor;   /* 1 (default): when the constraints are local to
+                             cliques, keep S = I + A Delta^{-1} A^T as
+                             block-diagonal plus low rank, S = B + U U^T, and
+                             solve with the matrix inversion lemma (blocks of at
+                             most 128 constraints, rank at most 64, used only when
+                             it reads less than half of a dense inverse); 0: a
+                             dense inverse whenever S is not diagonal          */
     double  alpha;        /* over-relaxation: the cone step projects
                              alpha u_hat + (1 - alpha) u - nu; in (0, 2),
                              default 1.8; 1 is the literal Eqs. Step1-Step3   */
@@ -135,7 +142,8 @@ typedef struct hsde_sizes {
     int64_t P;            /* packed clique storage sum_k c_k(c_k+1)/2             */
     int64_t n_d;          /* sum_k c_k^2 (Section 3.2)                            */
     int64_t state_len;    /* N + 3P + m + 2                                       */
-    int32_t S_dense;      /* 1 if I + A Delta^{-1} A^T is stored dense, 0 if diagonal */
+    int32_t S_dense;      /* how S = I + A Delta^{-1} A^T is kept: 0 diagonal, 1 dense
+                             inverse, 2 block-diagonal plus low rank           */
     int32_t _pad;
 } hsde_sizes;
 

@@ -67,7 +67,9 @@ struct HostPrep {
     std::vector<double> dscale;               // d_i (1 when not scaling)
     double sigma = 1.0, rho = 1.0;
     double bnorm = 0.0, cnorm = 0.0;          // ||b||, ||c|| of the original data
-    bool dense = false;
+    bool dense = false;                       // two constraints share an entry
+    bool lowrank = false;                     // dense S kept as B + U U^T (factor.cu)
+    LowRankHost lr;
     std::vector<double> Sdense;               // m*m (dense case)
     std::vector<double> Sdiag_inv;            // m (diagonal case)
 };
@@ -179,7 +181,12 @@ int prepare(const hsde_problem* P, const hsde_options& O, HostPrep& H, std::stri
     // S = I + A Delta^{-1} A^T (full-vec inner products); diagonal if no two
     // constraints share a pattern entry.
     H.dense = max_at > 1;
-    if (!H.dense) {
+    if (H.dense && O.structured_factor)
+        H.lowrank = build_lowrank(m, N, H.At_ptr.data(), H.At_col.data(), H.At_val.data(), H.diag.data(),
+                                  H.inv_delta.data(), H.lr);
+    if (H.lowrank) {
+        // nothing more: the structured factor replaces the dense S
+    } else if (!H.dense) {
         std::vector<double> d(m, 1.0);
         for (int64_t e = 0; e < N; ++e)
             for (int32_t j = H.At_ptr[e]; j < H.At_ptr[e + 1]; ++j) {
@@ -292,6 +299,7 @@ int enqueue_iteration_v(hsde_handle* h, const DevView& V, int warm, bool events)
     CK(rec(h, h->ev_it0, h->st));
     launch_fwd(V, h->st);
     if (h->any_dense) launch_solve_dense(V, h->st);
+    launch_lr_solve(V, V.q, V.yw, V.rowb, true, h->st);
     launch_bwd_eta(V, h->st);
     CK(rec(h, h->ev_aff, h->st));
     // fork: every clique bucket on its own branch; buckets whose CTAs each
@@ -328,6 +336,7 @@ int count_kernels(const hsde_handle* h) {
     if (V.ntiles > 0) k += 2;          // bwd_eta, post
     if (V.Mtot > 0) k += 1;            // fwd
     if (h->any_dense) k += 1;          // solve_dense
+    if (V.nlr > 0) k += 2;             // structured solve
     for (const auto& b : h->buckets) k += b.count > 0 ? 1 : 0;
     return k;
 }
@@ -412,7 +421,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     if (!(opt.eps_tol > 0) || opt.max_iter <= 0 || opt.check_every <= 0 ||
         (opt.precision != HSDE_FP64 && opt.precision != HSDE_MIXED) || opt.jacobi_max_sweeps < 0 ||
         opt.jacobi_tol < 0 || opt.warm_start < -1 || opt.warm_start > 1 || opt.warm_refresh < 0 ||
-        (opt.scaling != 0 && opt.scaling != 1) || !(opt.alpha > 0.0 && opt.alpha < 2.0) ||
+        (opt.scaling != 0 && opt.scaling != 1) || (opt.structured_factor != 0 && opt.structured_factor != 1) || !(opt.alpha > 0.0 && opt.alpha < 2.0) ||
         !(opt.scale_norm > 0.0) || !(opt.dual_weight > 0.0) || !std::isfinite(opt.scale_norm) ||
         !std::isfinite(opt.dual_weight))
         return fail(HSDE_EINVAL, "invalid options");
@@ -464,6 +473,8 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     }
     // ---- totals and offsets ----
     int64_t Ntot = 0, Ptot = 0, nnzA = 0, Mtot = 0, ncl = 0, ntiles = 0, sinv = 0, scn = 0;
+    int64_t lr_uw = 0, lr_k = 0, lr_hh = 0, lr_bi = 0;   // structured factor pools
+    std::vector<int4> lr_tiles;
     h->x_off.resize(B); h->p_off.resize(B); h->m_off.resize(B);
     std::vector<InstDev> inst(B);
     std::vector<int4> hat;   // A^T tiles
@@ -481,9 +492,21 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         I.at_begin = (int32_t)hat.size();
         append_at_tiles(H, b, Ntot, hat);
         I.at_end = (int32_t)hat.size();
-        I.dense = H.dense ? 1 : 0;
+        I.dense = H.dense ? (H.lowrank ? 2 : 1) : 0;
         I.sinv_off = sinv;
-        if (H.dense) sinv += (int64_t)H.m * H.m;
+        if (I.dense == 1) sinv += (int64_t)H.m * H.m;
+        if (I.dense == 2) {
+            I.lr_r = H.lr.r;
+            I.lr_off = lr_uw; I.kinv_off = lr_k; I.h_off = lr_hh;
+            lr_uw += (int64_t)H.m * H.lr.r;
+            lr_k += (int64_t)H.lr.r * H.lr.r;
+            lr_hh += H.lr.r;
+            lr_bi += (int64_t)H.lr.binv.size();
+            I.lr_tile_begin = (int32_t)lr_tiles.size();
+            for (int32_t r0 = 0; r0 < H.m; r0 += LR_TILE)
+                lr_tiles.push_back(make_int4(b, (int)(Mtot + r0), (int)(Mtot + std::min(H.m, r0 + LR_TILE)), 0));
+            I.lr_tile_end = (int32_t)lr_tiles.size();
+        }
         I.status = HSDE_RUNNING;
         I.vcold = 1;
         I.tau = 1.0; I.kappa = 1.0;
@@ -557,14 +580,19 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
                  o_att = cv.take<int4>(hat.size()), o_atpart = cv.take<double>(hat.size()),
                  o_clsw = cv.take<int32_t>(ncl),
                  o_blist = cv.take<int32_t>(ncl),
-                 o_rowb = cv.take<double>(Mtot), o_cnt = cv.take<int>(2 * (size_t)B),
+                 o_rowb = cv.take<double>(Mtot), o_cnt = cv.take<int>(3 * (size_t)B),
                  o_af = cv.take<double>(Mtot), o_atyw = cv.take<double>(Ntot), o_atyp = cv.take<double>(Ntot),
                  o_dinv2 = cv.take<double>(Mtot), o_ax = cv.take<double>(Mtot), o_aty = cv.take<double>(Ntot);
+    const size_t o_lrbr = cv.take<int64_t>(Mtot), o_lrmem = cv.take<int32_t>(Mtot), o_lrbsz = cv.take<int32_t>(Mtot),
+                 o_lrmembers = cv.take<int32_t>(Mtot), o_lrbinv = cv.take<double>(lr_bi),
+                 o_lrU = cv.take<double>(lr_uw), o_lrW = cv.take<double>(lr_uw), o_lrk = cv.take<double>(lr_k),
+                 o_lrh = cv.take<double>(lr_hh + 1), o_lrpart = cv.take<double>(lr_tiles.size() * (size_t)LR_RMAX),
+                 o_lrtiles = cv.take<int4>(lr_tiles.size());
     // Gauss-Jordan scratch and per-dense-instance tables
     int ndense = 0;
     int32_t mmax = 0;
     for (int32_t b = 0; b < B; ++b)
-        if (h->prep[b].dense) { ++ndense; mmax = std::max(mmax, h->prep[b].m); }
+        if (h->prep[b].dense && !h->prep[b].lowrank) { ++ndense; mmax = std::max(mmax, h->prep[b].m); }
     h->any_dense = ndense > 0;
     const size_t o_gjrow = cv.take<double>(Mtot), o_gjcol = cv.take<double>(Mtot),
                  o_gjoff = cv.take<int64_t>(ndense), o_gjm = cv.take<int32_t>(ndense),
@@ -601,6 +629,12 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     V.atyp = (double*)(ar + o_atyp);
     V.counters = (int*)(ar + o_cnt);
     V.dinv2 = (const double*)(ar + o_dinv2);
+    V.lr_binv_row = (const int64_t*)(ar + o_lrbr); V.lr_mem = (const int32_t*)(ar + o_lrmem);
+    V.lr_bsz = (const int32_t*)(ar + o_lrbsz); V.lr_members = (const int32_t*)(ar + o_lrmembers);
+    V.lr_binv = (const double*)(ar + o_lrbinv); V.lr_U = (const double*)(ar + o_lrU);
+    V.lr_W = (const double*)(ar + o_lrW); V.lr_kinv = (const double*)(ar + o_lrk);
+    V.lr_h = (double*)(ar + o_lrh); V.lr_part = (double*)(ar + o_lrpart);
+    V.lr_tiles = (const int4*)(ar + o_lrtiles); V.nlr = (int32_t)lr_tiles.size();
     V.ax = (double*)(ar + o_ax);
     V.aty = (double*)(ar + o_aty);
     V.eps = opt.eps_tol; V.max_iter = opt.max_iter; V.check_every = opt.check_every;
@@ -661,6 +695,35 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     UP(o_av, hAv); UP(o_ri, hri); UP(o_sd, hsd); UP(o_g, hg); UP(o_clo, hclo); UP(o_cls, hcls);
     UP(o_cli, hcli); UP(o_vso, hvso); UP(o_dinv2, hdinv2);
     {
+        // structured factors: per-row block data with absolute indices, pools
+        std::vector<int64_t> hbr(Mtot, 0);
+        std::vector<int32_t> hmem(Mtot, 0), hbsz(Mtot, 0), hmembers(Mtot, 0);
+        std::vector<double> hbinv, hU, hW, hK;
+        hbinv.reserve(lr_bi); hU.reserve(lr_uw); hW.reserve(lr_uw); hK.reserve(lr_k);
+        for (int32_t b = 0; b < B; ++b) {
+            const HostPrep& H = h->prep[b];
+            if (!H.lowrank) continue;
+            const LowRankHost& L = H.lr;
+            const int32_t mo = h->m_off[b];
+            const int64_t bo = (int64_t)hbinv.size();
+            for (int32_t i = 0; i < H.m; ++i) {
+                const int32_t k = L.row_blk[i], bs = L.blk_ptr[k + 1] - L.blk_ptr[k];
+                hbr[mo + i] = bo + L.blk_off[k] + (int64_t)L.row_pos[i] * bs;
+                hmem[mo + i] = mo + L.blk_ptr[k];
+                hbsz[mo + i] = bs;
+                hmembers[mo + i] = mo + L.members[i];
+            }
+            hbinv.insert(hbinv.end(), L.binv.begin(), L.binv.end());
+            hU.insert(hU.end(), L.U.begin(), L.U.end());
+            hW.insert(hW.end(), L.W.begin(), L.W.end());
+            hK.insert(hK.end(), L.kinv.begin(), L.kinv.end());
+        }
+        UP(o_lrbr, hbr); UP(o_lrmem, hmem); UP(o_lrbsz, hbsz); UP(o_lrmembers, hmembers);
+        UP(o_lrbinv, hbinv); UP(o_lrU, hU); UP(o_lrW, hW); UP(o_lrk, hK); UP(o_lrtiles, lr_tiles);
+        CK(cudaStreamSynchronize(st));
+        for (auto& H : h->prep) H.lr = LowRankHost();
+    }
+    {
         std::vector<InstDev> iv(inst);
         CK(cudaMemcpyAsync(ar + o_inst, iv.data(), sizeof(InstDev) * B, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(ar + o_tiles, htiles.data(), sizeof(int4) * htiles.size(), cudaMemcpyHostToDevice, st));
@@ -673,7 +736,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         // dense instances sorted by m, descending: the active ones at step k are a prefix
         std::vector<int32_t> ord;
         for (int32_t b = 0; b < B; ++b)
-            if (h->prep[b].dense) ord.push_back(b);
+            if (h->prep[b].dense && !h->prep[b].lowrank) ord.push_back(b);
         std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return h->prep[a].m > h->prep[b].m; });
         std::vector<int64_t> offs, boffs, tpre;
         std::vector<int32_t> ms;
@@ -790,6 +853,7 @@ void hsde_default_options(hsde_options* o) {
     o->warm_start = -1;
     o->warm_refresh = 0;
     o->scaling = 1;
+    o->structured_factor = 1;
     o->alpha = 1.8;
     o->scale_norm = 10.0;
     o->dual_weight = 1.5;
@@ -814,7 +878,7 @@ int hsde_analyze(const hsde_problem* P, hsde_symbolic** out) {
     }
 }
 
-static void fill_sizes(const Symbolic& S, int32_t m, bool dense, hsde_sizes* o) {
+static void fill_sizes(const Symbolic& S, int32_t m, int dense, hsde_sizes* o) {
     std::memset(o, 0, sizeof(*o));
     o->n = S.n; o->m = m; o->p = S.p();
     o->N = S.N(); o->P = S.P();
@@ -827,7 +891,7 @@ static void fill_sizes(const Symbolic& S, int32_t m, bool dense, hsde_sizes* o) 
     }
     o->n_d = nd; o->c_max = cmax;
     o->state_len = o->N + 3 * o->P + m + 2;
-    o->S_dense = dense ? 1 : 0;
+    o->S_dense = dense;
 }
 
 int hsde_symbolic_sizes(const hsde_symbolic* s, hsde_sizes* out) {
@@ -910,7 +974,7 @@ int hsde_get_sizes(const hsde_handle* h, int32_t i, hsde_sizes* out) {
     int rc = check_handle(h, i);
     if (rc != HSDE_OK) return rc;
     if (!out) return fail(HSDE_EINVAL, "null output");
-    fill_sizes(h->prep[i].S, h->prep[i].m, h->prep[i].dense, out);
+    fill_sizes(h->prep[i].S, h->prep[i].m, h->prep[i].dense ? (h->prep[i].lowrank ? 2 : 1) : 0, out);
     return HSDE_OK;
 }
 

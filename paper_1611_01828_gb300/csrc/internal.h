@@ -45,11 +45,17 @@ struct InstDev {
     int64_t x_off, N;        // pattern entries
     int64_t p_off, P;        // packed clique entries
     int64_t sinv_off;        // dense S^{-1} offset in the pool (doubles)
+    int64_t lr_off;          // offset of this instance's U and W (m x r each) in their pools
+    int64_t kinv_off;        // offset of K^{-1} (r x r)
+    int64_t h_off;           // offset of the r-vector h of the current solve
     int32_t m_off, m;        // constraints
     int32_t cl_begin, cl_end;      // cliques
     int32_t tile_begin, tile_end;  // N-space tiles
     int32_t at_begin, at_end;      // A^T tiles (nonzero-balanced, k_bwd_eta)
-    int32_t dense;           // S stored dense (1) or diagonal (0)
+    int32_t dense;           // S stored diagonal (0), as a dense inverse (1), or as
+                             // block-diagonal plus low rank (2, factor.cu)
+    int32_t lr_r;            // rank of the low-rank part (dense == 2)
+    int32_t lr_tile_begin, lr_tile_end;   // its row tiles (k_lr_t / k_lr_y)
     int32_t status;          // HSDE_RUNNING ...
     int32_t iter;            // iterations done
     int32_t vcold;           // 1: the stored eigenbases are not valid (cold start next)
@@ -117,13 +123,26 @@ struct DevView {
     const double* dinv2;     // [Mtot] 1 / d_i^2 (row scaling D; 1 unscaled)
     double* ax;              // [Mtot] A x of the current iterate (over-relaxation)
     double* aty;             // [Ntot] A^T y of the current iterate (over-relaxation)
+    // structured S = B + U U^T (instances with dense == 2; factor.cu)
+    const int64_t* lr_binv_row;  // [Mtot] offset of the row's row of its block inverse
+    const int32_t* lr_mem;       // [Mtot] offset of the row's block members in lr_members
+    const int32_t* lr_bsz;       // [Mtot] size of the row's block (0: not structured)
+    const int32_t* lr_members;   // absolute constraint rows of every block
+    const double* lr_binv;       // block inverses, row-major, concatenated
+    const double* lr_U;          // U, m x r row-major per instance
+    const double* lr_W;          // W = B^{-1} U, same layout
+    const double* lr_kinv;       // K^{-1}, r x r per instance
+    double* lr_h;                // h of the current solve, r per instance
+    double* lr_part;             // [nlr * LR_RMAX] tile partials of U^T t
+    const int4* lr_tiles;        // (instance, first row, end row, 0)
+    int32_t nlr;                 // number of row tiles of structured instances
     // reverse-mode tape of one iteration (null when not recording)
     void* tape_v;            // per clique: CP x CP eigenvectors, then CP eigenvalues
     const int64_t* tv_off;   // [ncl] offset of each clique's tape block (elements)
     double* tape_scal;       // [2B] tau_hat and tau_hat - kappa
     double* atyw;            // [Ntot] A^T y_w of the current iteration
     double* atyp;            // [Ntot] A^T y_p (setup)
-    int* counters;           // [2B] completion counters of k_bwd_eta and k_post
+    int* counters;           // [3B] completion counters of k_bwd_eta, k_post and k_lr_t
     // options
     double eps;
     double alpha;            // over-relaxation (1: the literal Eqs. Step1-Step3)
@@ -152,6 +171,33 @@ struct RevArgs {
     const double* otau; const double* ox; const double* oy; const void* os; const void* ov;
     double* gc; double* gb;
 };
+
+// Structured factor limits: blocks of at most LR_BMAX constraints, at most
+// LR_RMAX low-rank columns, LR_TILE rows per tile of the structured solve.
+constexpr int LR_BMAX = 128;
+constexpr int LR_RMAX = 64;
+constexpr int LR_TILE = 64;
+
+// Host-built structured form of S for one instance (factor.cu).
+struct LowRankHost {
+    int32_t r = 0;
+    std::vector<int32_t> blk_ptr;   // [nb+1] into members
+    std::vector<int32_t> members;   // constraints grouped by block, ascending within
+    std::vector<int32_t> row_blk;   // [m] block of each constraint
+    std::vector<int32_t> row_pos;   // [m] its position in the block
+    std::vector<int64_t> blk_off;   // [nb] offset of each block's inverse in binv
+    std::vector<double> binv;       // block inverses, row-major
+    std::vector<double> U, W;       // [m r] row-major
+    std::vector<double> kinv;       // [r r]
+};
+// Builds B, U, W, K^{-1} from A^T (CSR over pattern entries, raw values), the
+// diagonal flags and Delta^{-1}; false if the structure does not pay (a block
+// above LR_BMAX, more than LR_RMAX long entries, or no saving over a dense
+// inverse), in which case S stays dense.
+bool build_lowrank(int32_t m, int64_t N, const int32_t* At_ptr, const int32_t* At_col, const double* At_val,
+                   const uint8_t* diag, const double* inv_delta, LowRankHost& L);
+// y = S^{-1} q for the structured instances (rowb: b_i y_i on iterations, or null)
+void launch_lr_solve(const DevView& V, const double* qin, double* yout, double* rowb, bool iter, void* st);
 
 // Most eigensolver buckets (graph branches, side streams) of one handle.
 constexpr int MAX_BUCKETS = 16;

@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(NT) k_solve(DevView V, int mode) {
         if (lane == 0) out[row] = V.sdiag[row] * V.q[row];
         return;
     }
+    if (I.dense != 1) return;      // structured S: launch_lr_solve
     const int i = row - I.m_off;
     const double* Srow = V.sinv + I.sinv_off + (int64_t)i * I.m;
     const double* qq = V.q + I.m_off;
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(NT) k_solve_dense(DevView V) {
     const int row = (blockIdx.x * NT + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (row >= V.Mtot) return;
     const InstDev& I = V.inst[V.row_inst[row]];
-    if (I.status != HSDE_RUNNING || !I.dense) return;
+    if (I.status != HSDE_RUNNING || I.dense != 1) return;
     const int i = row - I.m_off;
     const double* Srow = V.sinv + I.sinv_off + (int64_t)i * I.m;
     const double* qq = V.q + I.m_off;
@@ -662,6 +663,8 @@ void launch_spmv_A(const DevView& V, Mode mode, void* st) {
 void launch_solve(const DevView& V, Mode mode, void* st) {
     if (V.Mtot == 0) return;
     k_solve<<<rows_grid(V.Mtot), NT, 0, S_(st)>>>(V, (int)mode);
+    if (mode == Mode::Iter) launch_lr_solve(V, V.q, V.yw, V.rowb, true, st);
+    else launch_lr_solve(V, V.q, V.yp, nullptr, false, st);
 }
 void launch_spmv_At(const DevView& V, Mode mode, void* st) {
     if (V.ntiles == 0) return;

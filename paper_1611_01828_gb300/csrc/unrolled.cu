@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(NT) k_ap_solve(DevView V, ApplyArgs A) {
     const int row = (blockIdx.x * NT + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (row >= V.Mtot) return;
     const InstDev& I = V.inst[V.row_inst[row]];
-    if (!I.dense) return;
+    if (I.dense != 1) return;      // diagonal: done in k_ap_q; structured: launch_lr_solve
     const int i = row - I.m_off;
     const double* Srow = V.sinv + I.sinv_off + (int64_t)i * I.m;
     const double* qq = A.q + I.m_off;
@@ -390,6 +390,7 @@ void launch_apply(const DevView& V, const ApplyArgs& A, bool mixed, bool setup_o
         const int rg = (V.Mtot * 32 + NT - 1) / NT;
         k_ap_q<<<rg, NT, 0, Su(st)>>>(V, A);
         k_ap_solve<<<rg, NT, 0, Su(st)>>>(V, A);
+        launch_lr_solve(V, A.q, A.yw, nullptr, false, st);
     }
     if (V.ntiles > 0) k_ap_xw<<<V.ntiles, NT, 0, Su(st)>>>(V, A);
     k_ap_eta<<<V.B, NT, 0, Su(st)>>>(V, A);

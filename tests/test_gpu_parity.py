@@ -89,6 +89,8 @@ PROBS = {
     "arrow_odd": lambda: synth.block_arrow(6, 5, 2, 9, np.random.default_rng(2), assign="roundrobin"),
     "arrow_buckets": lambda: synth.block_arrow(3, 30, 3, 6, np.random.default_rng(3)),   # c = 33 (CTA path)
     "arrow_c16_17": lambda: synth.block_arrow(4, 12, 5, 8, np.random.default_rng(4)),    # c = 17
+    # m = 200: S kept as block-diagonal (pairs) plus rank 15 (the arrow corner)
+    "arrow_l100_d10": lambda: synth.block_arrow_sweep(100, 10),
 }
 
 
@@ -356,3 +358,18 @@ def test_maxcut_grid20x100_to_the_verdict(hs, grid_run, prec):
     assert int(st[0]) == hs.SOLVED
     assert info["iterations"] <= 2000
     assert err <= 1e-4
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_structured_factor_matches_dense_factor(hs, prec, tol):
+    """S = I + A Delta^{-1} A^T kept as blocks plus low rank (the matrix
+    inversion lemma) gives the iterates of the dense inverse, to rounding."""
+    p = PROBS["arrow_l100_d10"]()
+    ref = ohsde.HSDE(p)
+    out = {}
+    for sf in (1, 0):
+        with hs.Handle(p, precision=prec, structured_factor=sf, warm_start=0) as H:
+            assert H.sizes[0].S_dense == (2 if sf else 1)
+            H.hsde_iterate(20)
+            out[sf] = H.hsde_get_state(0)
+    close(ref, out[1], out[0], tol, f"structured vs dense factor ({prec})")
