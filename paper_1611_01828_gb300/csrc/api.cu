@@ -324,6 +324,7 @@ int enqueue_iteration_v(hsde_handle* h, const DevView& V, int warm, bool events)
     }
     for (size_t i = 0; i < nb; ++i) CK(cudaStreamWaitEvent(h->st, h->ev_join[i], 0));
     CK(rec(h, h->ev_chk, h->st));
+    launch_long(V, h->mixed, h->st);
     launch_post(V, h->mixed, h->st);
     CK(rec(h, h->ev_it1, h->st));
     CK(cudaGetLastError());
@@ -334,6 +335,7 @@ int count_kernels(const hsde_handle* h) {
     const DevView& V = h->V;
     int k = 0;
     if (V.ntiles > 0) k += 2;          // bwd_eta, post
+    if (V.nlong > 0) k += 1;           // long entries' H^T sums
     if (V.Mtot > 0) k += 1;            // fwd
     if (h->any_dense) k += 1;          // solve_dense
     if (V.nlr > 0) k += 2;             // structured solve
@@ -474,6 +476,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     // ---- totals and offsets ----
     int64_t Ntot = 0, Ptot = 0, nnzA = 0, Mtot = 0, ncl = 0, ntiles = 0, sinv = 0, scn = 0;
     int64_t lr_uw = 0, lr_k = 0, lr_hh = 0, lr_bi = 0;   // structured factor pools
+    int64_t nlong = 0, sscn = 0;                          // long entries, short copies
     std::vector<int4> lr_tiles;
     h->x_off.resize(B); h->p_off.resize(B); h->m_off.resize(B);
     std::vector<InstDev> inst(B);
@@ -514,6 +517,11 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         h->x_off[b] = Ntot; h->p_off[b] = Ptot; h->m_off[b] = (int32_t)Mtot;
         Ntot += I.N; Ptot += I.P; Mtot += H.m; ncl += H.S.p(); nnzA += (int64_t)H.A_col.size();
         scn += (int64_t)H.sc_idx.size();
+        for (int64_t e = 0; e < H.S.N(); ++e) {
+            const int32_t d = H.sc_ptr[e + 1] - H.sc_ptr[e];
+            if (d > LONG_COPIES) ++nlong;
+            else sscn += d;
+        }
     }
     // the device index arrays (pattern entries, packed positions, constraint
     // rows and the CSR offsets of A and A^T) are 32-bit over the whole batch;
@@ -588,6 +596,9 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
                  o_lrU = cv.take<double>(lr_uw), o_lrW = cv.take<double>(lr_uw), o_lrk = cv.take<double>(lr_k),
                  o_lrh = cv.take<double>(lr_hh + 1), o_lrpart = cv.take<double>(lr_tiles.size() * (size_t)LR_RMAX),
                  o_lrtiles = cv.take<int4>(lr_tiles.size());
+    const size_t o_sscp = cv.take<int32_t>(Ntot + 1), o_ssci = cv.take<int32_t>(sscn),
+                 o_lid = cv.take<int32_t>(Ntot), o_le = cv.take<int32_t>(nlong), o_linst = cv.take<int32_t>(nlong),
+                 o_lhz = cv.take<double>(nlong), o_lall = cv.take<double>(nlong);
     // Gauss-Jordan scratch and per-dense-instance tables
     int ndense = 0;
     int32_t mmax = 0;
@@ -635,6 +646,10 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     V.lr_W = (const double*)(ar + o_lrW); V.lr_kinv = (const double*)(ar + o_lrk);
     V.lr_h = (double*)(ar + o_lrh); V.lr_part = (double*)(ar + o_lrpart);
     V.lr_tiles = (const int4*)(ar + o_lrtiles); V.nlr = (int32_t)lr_tiles.size();
+    V.ssc_ptr = (const int32_t*)(ar + o_sscp); V.ssc_idx = (const int32_t*)(ar + o_ssci);
+    V.long_id = (const int32_t*)(ar + o_lid); V.long_e = (const int32_t*)(ar + o_le);
+    V.long_inst = (const int32_t*)(ar + o_linst); V.lhz = (double*)(ar + o_lhz); V.lall = (double*)(ar + o_lall);
+    V.nlong = (int32_t)nlong;
     V.ax = (double*)(ar + o_ax);
     V.aty = (double*)(ar + o_aty);
     V.eps = opt.eps_tol; V.max_iter = opt.max_iter; V.check_every = opt.check_every;
@@ -644,6 +659,8 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     std::vector<double> hc, hid, hAtv, hb, hAv, hsd, hdinv2;
     std::vector<uint8_t> hdiag;
     std::vector<int32_t> hscp, hsci, hatp, hatc, hap, hac, hri, hg, hclo, hcls, hcli;
+    std::vector<int32_t> hsscp, hssci, hlid, hle, hlinst;   // short H^T CSR and the long entries
+    hsscp.reserve(Ntot + 1); hssci.reserve(sscn); hlid.reserve(Ntot);
     std::vector<int4> htiles;
     hc.reserve(Ntot); hid.reserve(Ntot); hdiag.reserve(Ntot);
     hscp.reserve(Ntot + 1); hatp.reserve(Ntot + 1); hap.reserve(Mtot + 1);
@@ -661,6 +678,18 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
             hatp.push_back(atbase + H.At_ptr[e]);
         }
         for (int32_t j : H.sc_idx) hsci.push_back((int32_t)(po + j));
+        for (int64_t e = 0; e < H.S.N(); ++e) {
+            hsscp.push_back((int32_t)hssci.size());
+            const int32_t j0 = H.sc_ptr[e], j1 = H.sc_ptr[e + 1];
+            if (j1 - j0 > LONG_COPIES) {
+                hlid.push_back((int32_t)hle.size());
+                hle.push_back((int32_t)(xo + e));
+                hlinst.push_back(b);
+            } else {
+                hlid.push_back(-1);
+                for (int32_t j = j0; j < j1; ++j) hssci.push_back((int32_t)(po + H.sc_idx[j]));
+            }
+        }
         for (size_t j = 0; j < H.At_col.size(); ++j) hatc.push_back(mo + H.At_col[j]);
         hAtv.insert(hAtv.end(), H.At_val.begin(), H.At_val.end());
         for (int32_t i = 0; i < H.m; ++i) {
@@ -683,6 +712,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
             htiles.push_back(make_int4(b, (int)(xo + s0), (int)(xo + std::min<int64_t>(H.S.N(), s0 + TILE_N)), 0));
     }
     hscp.push_back((int32_t)hsci.size());
+    hsscp.push_back((int32_t)hssci.size());
     hatp.push_back((int32_t)hatc.size());
     hap.push_back((int32_t)hac.size());
 
@@ -691,6 +721,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     int rc;
 #define UP(off, vec) if ((rc = upload(ar + (off), vec, st)) != HSDE_OK) return rc
     UP(o_c, hc); UP(o_id, hid); UP(o_diag, hdiag); UP(o_scp, hscp); UP(o_sci, hsci);
+    UP(o_sscp, hsscp); UP(o_ssci, hssci); UP(o_lid, hlid); UP(o_le, hle); UP(o_linst, hlinst);
     UP(o_atp, hatp); UP(o_atc, hatc); UP(o_atv, hAtv); UP(o_b, hb); UP(o_ap, hap); UP(o_ac, hac);
     UP(o_av, hAv); UP(o_ri, hri); UP(o_sd, hsd); UP(o_g, hg); UP(o_clo, hclo); UP(o_cls, hcls);
     UP(o_cli, hcli); UP(o_vso, hvso); UP(o_dinv2, hdinv2);

@@ -84,6 +84,8 @@ constexpr int KPART = 10;
 constexpr double CERT_CANCEL = 1e-2;
 // Entries per N-space tile (one CTA of 256 threads each).
 constexpr int TILE_N = 256;
+// Copies above which an entry's H^T sums are formed by a CTA of its own.
+constexpr int LONG_COPIES = 32;
 // Nonzeros of A^T per A^T tile (whole rows; a longer row is a tile alone).
 constexpr int AT_TILE_NNZ = 4096;
 
@@ -97,6 +99,16 @@ struct DevView {
     double* f; double* xw;
     const uint8_t* diag;
     const int32_t* sc_ptr; const int32_t* sc_idx;        // H^T as CSR over entries
+    // entries in more than LONG_COPIES cliques (the arrow corner of a
+    // block-arrow is in every clique) are summed by k_long, a CTA each; the
+    // other copies form the short CSR that k_post stages tile by tile
+    const int32_t* ssc_ptr; const int32_t* ssc_idx;      // H^T without the long entries
+    const int32_t* long_id;  // [Ntot] index of a long entry, -1 otherwise
+    const int32_t* long_e;   // [nlong] its pattern entry
+    const int32_t* long_inst;   // [nlong] its instance
+    double* lhz;             // [nlong] (H^T z) of the long entry
+    double* lall;            // [nlong] (H^T (s + z + v)) of the long entry
+    int32_t nlong;
     const int32_t* At_ptr; const int32_t* At_col; const double* At_val;
     // m space
     double* y; const double* b; double* yp; double* q; double* yw;
@@ -222,6 +234,8 @@ void launch_fwd(const DevView& V, void* st);
 void launch_solve_dense(const DevView& V, void* st);
 void launch_bwd_eta(const DevView& V, void* st);
 void launch_post(const DevView& V, bool mixed, void* st);
+// H^T sums of the long entries (before k_post, and inside launch_rhs in Iter mode)
+void launch_long(const DevView& V, bool mixed, void* st);
 void launch_setup_den(const DevView& V, void* st);
 // A x and A^T y of the stored iterate into V.ax, V.aty for the constraint
 // rows [r0, r1) and pattern entries [e0, e1) (after hsde_set_state)

@@ -93,6 +93,42 @@ __device__ __forceinline__ double ld(const void* p, int64_t i) {
     return (double)reinterpret_cast<const T*>(p)[i];
 }
 
+// s + z + v of one packed copy, added in the precision of the clique arrays
+// (in FP32 for the mixed form: one conversion instead of three, and no FP64
+// additions, which run at a small fraction of the FP32 rate on this GPU).
+// k_post, k_rhs and k_long all use it, so they agree bit for bit.
+template <typename T>
+__device__ __forceinline__ double copy_szv(const DevView& V, int64_t p) {
+    const T* s = reinterpret_cast<const T*>(V.s);
+    const T* z = reinterpret_cast<const T*>(V.z);
+    const T* v = reinterpret_cast<const T*>(V.v);
+    return (double)(s[p] + z[p] + v[p]);
+}
+
+// NV block sums (blockDim.x == NT) through shared memory: every value is
+// summed by one warp in a fixed order (strided lanes, then a butterfly), so
+// each double is added about 12 times per warp instead of 5 times by every
+// thread.  buf holds NV * NT doubles; the result is valid in every thread.
+template <int NV>
+__device__ __forceinline__ void block_sum_t(double (&v)[NV], double* buf) {
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) buf[i * NT + threadIdx.x] = v[i];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int i = w; i < NV; i += NT / 32) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < NT / 32; ++k) s += buf[i * NT + l + 32 * k];
+        s = warp_sum(s);
+        if (l == 0) buf[i * NT] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = buf[i * NT];
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // g0, f = Delta^{-1} g0 ; Setup mode: f = Delta^{-1} c
 // ---------------------------------------------------------------------------
@@ -108,12 +144,37 @@ __global__ void __launch_bounds__(NT) k_rhs(DevView V, int mode) {
     const double ot = I.tau + I.kappa;
     for (int e = t.y + threadIdx.x; e < t.z; e += NT) {
         double acc = 0.0;
-        const int j1 = V.sc_ptr[e + 1];
-        for (int j = V.sc_ptr[e]; j < j1; ++j) {
-            const int p = V.sc_idx[j];
-            acc += ld<T>(V.s, p) + ld<T>(V.z, p) + ld<T>(V.v, p);
+        const int li = V.long_id[e];
+        if (li >= 0) {
+            acc = V.lall[li];                       // k_long, launched just before
+        } else {
+            const int j1 = V.ssc_ptr[e + 1];
+            for (int j = V.ssc_ptr[e]; j < j1; ++j) acc += copy_szv<T>(V, V.ssc_idx[j]);
         }
         V.f[e] = (V.x[e] - ot * V.c[e] + 0.5 * acc) * V.inv_delta[e];
+    }
+}
+
+// H^T z and H^T (s + z + v) of each long entry: one CTA per entry, the
+// copies strided over the threads and summed in a fixed tree (the same
+// values as a sequential sum up to rounding, and the same bits every run).
+template <typename T>
+__global__ void __launch_bounds__(NT) k_long(DevView V) {
+    __shared__ double sh[2 * NT / 32];
+    const int l = blockIdx.x;
+    if (V.inst[V.long_inst[l]].status != HSDE_RUNNING) return;
+    const int e = V.long_e[l];
+    double v2[2] = {0.0, 0.0};
+    const int k1 = V.sc_ptr[e + 1];
+    for (int k = V.sc_ptr[e] + threadIdx.x; k < k1; k += NT) {
+        const int p = V.sc_idx[k];
+        v2[0] += ld<T>(V.z, p);
+        v2[1] += copy_szv<T>(V, p);
+    }
+    block_sum_n<2>(v2, sh);
+    if (threadIdx.x == 0) {
+        V.lhz[l] = v2[0];
+        V.lall[l] = v2[1];
     }
 }
 
@@ -386,9 +447,12 @@ constexpr int POST_STAGE = 2048;
 
 template <typename T>
 __global__ void __launch_bounds__(NT) k_post(DevView V) {
-    __shared__ double sh[12 * NT / 32];
     __shared__ int flag;
-    __shared__ double cz[POST_STAGE], call[POST_STAGE];   // per copy: z, and s + z + v
+    // per staged copy: z, and s + z + v; afterwards the reductions' buffer
+    __shared__ double stage[2 * POST_STAGE];
+    double* cz = stage;
+    double* call = stage + POST_STAGE;
+    static_assert(2 * POST_STAGE >= 11 * NT, "the reductions reuse the staging buffer");
     const int4 t = V.tiles[blockIdx.x];
     InstDev& I = V.inst[t.x];
     if (I.status != HSDE_RUNNING) return;
@@ -398,32 +462,35 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
     const double al = V.alpha;
     const bool relax = al != 1.0;
     double a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    double a4 = 0.0, a5 = 0.0, a6 = 0.0;   // ||A^T y||^2, ||H^T z||^2, ||H x||^2 (certificate cancellation)
+    // ||A^T y||^2, ||H^T z||^2, ||H x||^2 for the certificate cancellation
+    // test, which compares them with 1e-2 only: accumulated in FP32
+    float a4 = 0.f, a5 = 0.f, a6 = 0.f;
     // one pattern entry per thread (TILE_N == NT)
     const int e = t.y + threadIdx.x;
     const bool has = e < t.z;
     double x = 0.0;
-    int k0 = 0, k1 = 0;
+    int k0 = 0, k1 = 0, ncopy = 0;
     if (has) {
         const double xh = V.xw[e] - eta * V.xp[e];
         x = relax ? al * xh + (1.0 - al) * V.x[e] : xh;
         V.x[e] = x;
-        k0 = V.sc_ptr[e];
-        k1 = V.sc_ptr[e + 1];
+        k0 = V.ssc_ptr[e];
+        k1 = V.ssc_ptr[e + 1];
+        ncopy = V.sc_ptr[e + 1] - V.sc_ptr[e];
     }
-    // H^T z and H^T (s + z + v): the tile's copies are one contiguous range;
-    // the CTA loads them together (coalesced indices, one gather per copy)
-    // into shared memory, then each entry sums its own copies in order.
+    // H^T z and H^T (s + z + v): the tile's short copies are one contiguous
+    // range; the CTA loads them together (coalesced indices, one gather per
+    // copy) into shared memory, then each entry sums its own copies in
+    // order.  A long entry takes the sums k_long formed.
     double hz = 0.0, hall = 0.0;
-    const int c0 = V.sc_ptr[t.y], c1 = V.sc_ptr[t.z];
+    const int c0 = V.ssc_ptr[t.y], c1 = V.ssc_ptr[t.z];
     for (int cb = c0; cb < c1; cb += POST_STAGE) {
         const int ce = min(c1, cb + POST_STAGE);
         __syncthreads();
         for (int c = cb + threadIdx.x; c < ce; c += NT) {
-            const int p = V.sc_idx[c];
-            const double zz = ld<T>(V.z, p);
-            cz[c - cb] = zz;
-            call[c - cb] = ld<T>(V.s, p) + zz + ld<T>(V.v, p);
+            const int p = V.ssc_idx[c];
+            cz[c - cb] = ld<T>(V.z, p);
+            call[c - cb] = copy_szv<T>(V, p);
         }
         __syncthreads();
         const int a = max(k0, cb), b = min(k1, ce);
@@ -433,6 +500,11 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
         }
     }
     if (has) {
+        const int li = V.long_id[e];
+        if (li >= 0) {
+            hz = V.lhz[li];
+            hall = V.lall[li];
+        }
         const double ce = V.c[e];
         V.f[e] = (x - ot * ce + 0.5 * hall) * V.inv_delta[e];
         // A^T y_hat = A^T y_w - eta A^T y_p (both kept from this iteration / setup)
@@ -448,9 +520,10 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
             a1 += w * d * d;
             a2 += w * r * r;
             a3 += w * ce * x;
-            a4 += w * aty * aty;
-            a5 += w * hz * hz;
-            a6 += w * (double)(k1 - k0) * x * x;   // x repeated in each clique containing it
+            const float fw = (float)w, fa = (float)aty, fh = (float)hz, fx = (float)x;
+            a4 += fw * fa * fa;
+            a5 += fw * fh * fh;
+            a6 += fw * (float)ncopy * fx * fx;    // x repeated in each clique containing it
         }
     }
     // This CTA's slice of the constraints.  A x is not formed by an SpMV:
@@ -489,8 +562,8 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
         }
     }
     if (check) {
-        double v9[9] = {a1, a2, a3, b1, b2, b3, a4, a5, a6};
-        block_sum_n<9>(v9, sh);
+        double v9[9] = {a1, a2, a3, b1, b2, b3, (double)a4, (double)a5, (double)a6};
+        block_sum_t<9>(v9, stage);
         if (threadIdx.x == 0) {
             double* pp = V.part + (int64_t)blockIdx.x * KPART;
 #pragma unroll
@@ -517,7 +590,7 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
         v11[9] += __ldcg(V.cl_part + 2 * k);
         v11[10] += __ldcg(V.cl_part + 2 * k + 1);
     }
-    block_sum_n<11>(v11, sh);
+    block_sum_t<11>(v11, stage);
     a1 = v11[0]; a2 = v11[1]; a3 = v11[2];
     const double r0 = v11[3], r1 = v11[4], r2 = v11[5], hs = v11[9];
     const double aty2 = v11[6], hz2 = v11[7], hx2 = v11[8], ss2 = v11[10];
@@ -651,8 +724,15 @@ static inline cudaStream_t S_(void* st) { return reinterpret_cast<cudaStream_t>(
 // one warp per row; rows < 2^31 / 32 is guaranteed by the setup limits
 static inline int rows_grid(int rows) { return (int)(((int64_t)rows * 32 + NT - 1) / NT); }
 
+void launch_long(const DevView& V, bool mixed, void* st) {
+    if (V.nlong <= 0) return;
+    if (mixed) k_long<float><<<V.nlong, NT, 0, S_(st)>>>(V);
+    else k_long<double><<<V.nlong, NT, 0, S_(st)>>>(V);
+}
+
 void launch_rhs(const DevView& V, bool mixed, Mode mode, void* st) {
     if (V.ntiles == 0) return;
+    if (mode == Mode::Iter) launch_long(V, mixed, st);
     if (mixed) k_rhs<float><<<V.ntiles, NT, 0, S_(st)>>>(V, (int)mode);
     else k_rhs<double><<<V.ntiles, NT, 0, S_(st)>>>(V, (int)mode);
 }
