@@ -58,7 +58,8 @@ extern "C" {
 #define HSDE_ECUDA    (-3)   /* CUDA runtime error (no device, launch, ...)  */
 #define HSDE_ESTATE   (-4)   /* query does not match the instance's verdict */
 #define HSDE_ERANGE   (-5)   /* size beyond what this build supports (cliques
-                                larger than 64, totals beyond int32 indexing) */
+                                larger than 112 in HSDE_MIXED or 80 in HSDE_FP64,
+                                totals beyond int32 indexing) */
 
 /* per-instance iteration status (readings of the paper's stopping rule) */
 #define HSDE_RUNNING            0

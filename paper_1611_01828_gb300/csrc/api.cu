@@ -468,9 +468,11 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         for (auto& t : pool) t.join();
         for (int32_t b = 0; b < B; ++b) {
             if (rcs[b] != HSDE_OK) return fail(rcs[b], "instance " + std::to_string(b) + ": " + errs[b]);
-            if (cone_bucket_of(h->prep[b].cmax) < 0)
+            if (cone_bucket_of(h->prep[b].cmax, h->mixed) < 0)
                 return fail(HSDE_ERANGE, "instance " + std::to_string(b) + ": clique of size " +
-                                              std::to_string(h->prep[b].cmax) + " exceeds 64");
+                                              std::to_string(h->prep[b].cmax) + " exceeds " +
+                                              std::to_string(cone_max_clique(h->mixed)) + " (" +
+                                              (h->mixed ? "mixed" : "FP64") + " eigensolvers)");
         }
     }
     // ---- totals and offsets ----
@@ -540,7 +542,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
             const Symbolic& S = h->prep[b].S;
             for (int32_t k = 0; k < S.p(); ++k) {
                 hvso.push_back(vsn);
-                vsn += cone_vstore_elems(S.clique_ptr[k + 1] - S.clique_ptr[k]);
+                vsn += cone_vstore_elems(S.clique_ptr[k + 1] - S.clique_ptr[k], h->mixed);
             }
         }
     }
@@ -808,7 +810,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     // ---- clique buckets (largest cliques first) ----
     {
         std::vector<int> caps;
-        cone_bucket_sizes(caps);
+        cone_bucket_sizes(caps, h->mixed);
         const int NB = (int)caps.size();
         if (NB > MAX_BUCKETS) return fail(HSDE_ECUDA, "internal: more eigensolver buckets than graph branches");
         std::vector<std::vector<int32_t>> lists(NB);
@@ -817,7 +819,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         std::stable_sort(ids.begin(), ids.end(), [&](int32_t a, int32_t b) { return hcls[a] > hcls[b]; });
         std::vector<int64_t> c3(NB, 0);
         for (int32_t k : ids) {
-            const int bk = cone_bucket_of(hcls[k]);
+            const int bk = cone_bucket_of(hcls[k], h->mixed);
             for (int t = 0; t < NB; ++t)
                 if (caps[t] == bk) { lists[t].push_back(k); c3[t] += (int64_t)hcls[k] * hcls[k] * hcls[k]; }
         }
@@ -1264,7 +1266,7 @@ int ensure_unroll_ws(hsde_handle* h, int K, int ckpt) {
     int64_t tv = 0;
     for (const auto& H : h->prep)
         for (int32_t k = 0; k < H.S.p(); ++k) {
-            const int cp = cone_bucket_of(H.S.clique_ptr[k + 1] - H.S.clique_ptr[k]);
+            const int cp = cone_bucket_of(H.S.clique_ptr[k + 1] - H.S.clique_ptr[k], h->mixed);
             tvo.push_back(tv);
             tv += (int64_t)cp * cp + cp;
         }

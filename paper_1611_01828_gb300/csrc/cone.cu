@@ -65,6 +65,11 @@ struct ConeCfg {
     static_assert((4 * CP * LD + 3 * K + CP) % 2 == 0, "red is 8-byte aligned");
     static constexpr size_t group_bytes = (t_elems * sizeof(T) + 15) / 16 * 16;
     static constexpr size_t smem = GPB * group_bytes;
+    // resident CTAs the register budget is sized for: many-clique CTAs 8;
+    // one clique per CTA 2 where two fit the shared memory (the kernel waits
+    // on barriers and shared memory, so a second CTA hides that latency),
+    // else 1
+    static constexpr int MINB = GPB > 1 ? 8 : (2 * smem <= 232448 && NTH <= 512 ? 2 : 1);
 };
 
 template <typename T> struct Vec2;
@@ -303,7 +308,7 @@ __device__ __forceinline__ int packed_column(int e, int c) {
 }
 
 template <typename T, int CP, int G>
-__global__ void __launch_bounds__(ConeCfg<T, CP, G>::NTH, ConeCfg<T, CP, G>::GPB > 1 ? 8 : 1)
+__global__ void __launch_bounds__(ConeCfg<T, CP, G>::NTH, ConeCfg<T, CP, G>::MINB)
 k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T tol2, int warm, int refresh) {
     using Cfg = ConeCfg<T, CP, G>;
     using V2 = typename Vec2<T>::type;
@@ -669,9 +674,20 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
 // (padding a clique of c to CP costs about (CP/c)^3 of the work, so the
 // sizes are spaced by 4 above 16; G gives about one 2x2 block per thread and
 // round: K(K+1)/2 blocks, K = CP/2)
+// sizes above 64 hold one clique per CTA of up to 1024 threads; a size
+// exists for a precision only if its CTA fits the opt-in shared memory
+// (FP32 up to 112, FP64 up to 80)
 #define HSDE_CONE_BUCKETS(X)                                                                     \
     X(4, 4) X(8, 8) X(12, 16) X(16, 32) X(20, 64) X(24, 96) X(28, 128) X(32, 160) X(36, 192)   \
-    X(40, 224) X(44, 256) X(48, 320) X(56, 416) X(64, 544)
+    X(40, 224) X(44, 256) X(48, 320) X(56, 416) X(64, 544) X(80, 832) X(96, 1024) X(112, 1024)
+
+// Opt-in shared memory per CTA on this architecture (227 KB).
+constexpr size_t CONE_SMEM_MAX = 232448;
+
+template <typename T, int CP, int G>
+constexpr bool cone_fits() {
+    return ConeCfg<T, CP, G>::smem <= CONE_SMEM_MAX;
+}
 
 // Device limits read by cone_prepare: opt-in shared memory per CTA, SMs.
 static int g_smem_optin = 0;
@@ -679,15 +695,18 @@ static int g_num_sms = 0;
 
 template <typename T, int CP, int G>
 static int prepare_one() {
-    using Cfg = ConeCfg<T, CP, G>;
-    // one clique per CTA: allowed the whole opt-in shared memory, which a
-    // launch asks for when the bucket has few cliques (a CTA alone on its SM)
-    const int want = Cfg::GPB == 1 ? std::max<int>(g_smem_optin, (int)Cfg::smem) : (int)Cfg::smem;
-    if (want > 48 * 1024) {
-        if (cudaFuncSetAttribute(k_cone<T, CP, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, want) != cudaSuccess)
+    if constexpr (!cone_fits<T, CP, G>()) {
+        return HSDE_OK;                                          // never used in this precision
+    } else {
+        using Cfg = ConeCfg<T, CP, G>;
+        // one clique per CTA: allowed the whole opt-in shared memory, which a
+        // launch asks for when the bucket has few cliques (a CTA alone on its SM)
+        const int want = Cfg::GPB == 1 ? std::max<int>(g_smem_optin, (int)Cfg::smem) : (int)Cfg::smem;
+        if (want > 48 * 1024 &&
+            cudaFuncSetAttribute(k_cone<T, CP, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, want) != cudaSuccess)
             return HSDE_ECUDA;
+        return HSDE_OK;
     }
-    return HSDE_OK;
 }
 
 // A bucket of few large cliques sets the latency of the whole cone phase:
@@ -695,36 +714,57 @@ static int prepare_one() {
 // shared-memory bandwidth or issue slots).
 template <typename T, int CP, int G>
 static bool alone_one(const Bucket& bk) {
-    using Cfg = ConeCfg<T, CP, G>;
-    const int grid = (bk.count + Cfg::GPB - 1) / Cfg::GPB;
-    return Cfg::GPB == 1 && CP >= 32 && 3 * grid <= g_num_sms && g_smem_optin >= (int)Cfg::smem;
+    if constexpr (!cone_fits<T, CP, G>()) {
+        return false;
+    } else {
+        using Cfg = ConeCfg<T, CP, G>;
+        const int grid = (bk.count + Cfg::GPB - 1) / Cfg::GPB;
+        return Cfg::GPB == 1 && CP >= 32 && 3 * grid <= g_num_sms && g_smem_optin >= (int)Cfg::smem;
+    }
 }
 
 template <typename T, int CP, int G>
-static void launch_one(const DevView& V, const Bucket& bk, int max_sweeps, double tol, int warm, int refresh,
-                       cudaStream_t st) {
-    using Cfg = ConeCfg<T, CP, G>;
-    const int grid = (bk.count + Cfg::GPB - 1) / Cfg::GPB;
-    const size_t smem = alone_one<T, CP, G>(bk) ? (size_t)g_smem_optin : Cfg::smem;
-    k_cone<T, CP, G><<<grid, Cfg::NTH, smem, st>>>(V, bk.list, bk.count, max_sweeps, (T)(tol * tol), warm, refresh);
+static int launch_one(const DevView& V, const Bucket& bk, int max_sweeps, double tol, int warm, int refresh,
+                      cudaStream_t st) {
+    if constexpr (!cone_fits<T, CP, G>()) {
+        return HSDE_ERANGE;
+    } else {
+        using Cfg = ConeCfg<T, CP, G>;
+        const int grid = (bk.count + Cfg::GPB - 1) / Cfg::GPB;
+        const size_t smem = alone_one<T, CP, G>(bk) ? (size_t)g_smem_optin : Cfg::smem;
+        k_cone<T, CP, G><<<grid, Cfg::NTH, smem, st>>>(V, bk.list, bk.count, max_sweeps, (T)(tol * tol), warm,
+                                                         refresh);
+        return HSDE_OK;
+    }
 }
 
-int cone_bucket_of(int c) {
-#define X(cp, g) if (c <= cp) return cp;
+int cone_bucket_of(int c, bool mixed) {
+#define X(cp, g) \
+    if (c <= cp && (mixed ? cone_fits<float, cp, g>() : cone_fits<double, cp, g>())) return cp;
     HSDE_CONE_BUCKETS(X)
 #undef X
     return -1;
 }
 
-void cone_bucket_sizes(std::vector<int>& out) {
+int cone_max_clique(bool mixed) {
+    int mx = 0;
+#define X(cp, g) \
+    if (mixed ? cone_fits<float, cp, g>() : cone_fits<double, cp, g>()) mx = cp;
+    HSDE_CONE_BUCKETS(X)
+#undef X
+    return mx;
+}
+
+void cone_bucket_sizes(std::vector<int>& out, bool mixed) {
     out.clear();
-#define X(cp, g) out.push_back(cp);
+#define X(cp, g) \
+    if (mixed ? cone_fits<float, cp, g>() : cone_fits<double, cp, g>()) out.push_back(cp);
     HSDE_CONE_BUCKETS(X)
 #undef X
 }
 
-int cone_vstore_elems(int c) {
-    const int cp = cone_bucket_of(c);
+int cone_vstore_elems(int c, bool mixed) {
+    const int cp = cone_bucket_of(c, mixed);
     return cp < 0 ? -1 : cp * cp;
 }
 
@@ -761,11 +801,10 @@ int launch_cone(const DevView& V, const Bucket& bk, bool mixed, int max_sweeps, 
                 void* stp) {
     if (bk.count == 0) return HSDE_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stp);
-#define X(cp, g)                                                                        \
-    if (bk.cmax == cp) {                                                                \
-        if (mixed) launch_one<float, cp, g>(V, bk, max_sweeps, tol, warm, refresh, st); \
-        else launch_one<double, cp, g>(V, bk, max_sweeps, tol, warm, refresh, st);     \
-        return HSDE_OK;                                                                 \
+#define X(cp, g)                                                                                \
+    if (bk.cmax == cp) {                                                                        \
+        return mixed ? launch_one<float, cp, g>(V, bk, max_sweeps, tol, warm, refresh, st)     \
+                     : launch_one<double, cp, g>(V, bk, max_sweeps, tol, warm, refresh, st);   \
     }
     HSDE_CONE_BUCKETS(X)
 #undef X

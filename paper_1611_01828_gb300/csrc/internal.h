@@ -212,11 +212,11 @@ bool build_lowrank(int32_t m, int64_t N, const int32_t* At_ptr, const int32_t* A
 void launch_lr_solve(const DevView& V, const double* qin, double* yout, double* rowb, bool iter, void* st);
 
 // Most eigensolver buckets (graph branches, side streams) of one handle.
-constexpr int MAX_BUCKETS = 16;
+constexpr int MAX_BUCKETS = 20;
 
 // Bucket of cliques handled by one eigensolver variant.
 struct Bucket {
-    int32_t cmax;            // padded size CP of the bucket (4 ... 64)
+    int32_t cmax;            // padded size CP of the bucket (4 ... 112)
     int32_t count;
     int32_t* list;           // device array of clique ids (largest first)
 };
@@ -245,9 +245,11 @@ void launch_state_products(const DevView& V, int r0, int r1, int64_t e0, int64_t
 int  launch_cone(const DevView& V, const Bucket& bk, bool mixed, int max_sweeps, double tol,
                  int warm, int refresh, void* st);
 int  cone_smem_bytes(int cmax, bool mixed);
-int  cone_bucket_of(int c);          // padded size of the bucket of a clique of size c, -1 if none
-void cone_bucket_sizes(std::vector<int>& out);   // every bucket's padded size, ascending
-int  cone_vstore_elems(int c);       // stored basis size for a clique of size c
+// padded size of the bucket of a clique of size c in a precision, -1 if none
+int  cone_bucket_of(int c, bool mixed);
+int  cone_max_clique(bool mixed);    // largest clique the eigensolvers of a precision take
+void cone_bucket_sizes(std::vector<int>& out, bool mixed);   // the precision's buckets, ascending
+int  cone_vstore_elems(int c, bool mixed);   // stored basis size for a clique of size c
 bool cone_bucket_alone(const Bucket& bk, bool mixed);   // its CTAs each take a whole SM (launched first)
 int  cone_prepare(bool mixed);
 // reverse mode (unrolled.cu)

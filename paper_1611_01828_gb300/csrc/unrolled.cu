@@ -406,10 +406,17 @@ void launch_apply(const DevView& V, const ApplyArgs& A, bool mixed, bool setup_o
 // the same padded sizes as the forward eigensolver's buckets (cone.cu)
 #define HSDE_REV_BUCKETS(X)                                                                     \
     X(4, 4) X(8, 8) X(12, 16) X(16, 32) X(20, 64) X(24, 64) X(28, 128) X(32, 128) X(36, 256)   \
-    X(40, 256) X(44, 512) X(48, 512) X(56, 512) X(64, 512)
+    X(40, 256) X(44, 512) X(48, 512) X(56, 512) X(64, 512) X(80, 512) X(96, 1024) X(112, 1024)
+
+// a size exists for a precision only if its CTA fits the opt-in shared memory
+template <typename T, int CP, int G>
+constexpr bool rev_fits() {
+    return RevCfg<T, CP, G>::smem <= 232448;
+}
 
 template <typename T, int CP, int G>
 static int rev_prepare_one() {
+    if constexpr (!rev_fits<T, CP, G>()) return HSDE_OK;
     using Cfg = RevCfg<T, CP, G>;
     if (Cfg::smem > 48 * 1024 &&
         cudaFuncSetAttribute(k_rev_clique<T, CP, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::smem) !=
@@ -426,21 +433,23 @@ int rev_prepare(bool mixed) {
     return rc == HSDE_OK ? HSDE_OK : HSDE_ECUDA;
 }
 
+template <typename T, int CP, int G>
+static int rev_launch_one(const DevView& V, const RevArgs& R, const Bucket& bk, void* st) {
+    if constexpr (!rev_fits<T, CP, G>()) {
+        return HSDE_ERANGE;
+    } else {
+        using C = RevCfg<T, CP, G>;
+        k_rev_clique<T, CP, G><<<(bk.count + C::GPB - 1) / C::GPB, C::NTH, C::smem, Su(st)>>>(V, R, bk.list,
+                                                                                             bk.count);
+        return HSDE_OK;
+    }
+}
+
 int launch_rev_clique(const DevView& V, const RevArgs& R, const Bucket& bk, bool mixed, void* st) {
     if (bk.count == 0) return HSDE_OK;
-#define X(cp, g)                                                                                        \
-    if (bk.cmax == cp) {                                                                                \
-        if (mixed) {                                                                                    \
-            using C = RevCfg<float, cp, g>;                                                             \
-            k_rev_clique<float, cp, g><<<(bk.count + C::GPB - 1) / C::GPB, C::NTH, C::smem, Su(st)>>>(  \
-                V, R, bk.list, bk.count);                                                               \
-        } else {                                                                                        \
-            using C = RevCfg<double, cp, g>;                                                            \
-            k_rev_clique<double, cp, g><<<(bk.count + C::GPB - 1) / C::GPB, C::NTH, C::smem, Su(st)>>>( \
-                V, R, bk.list, bk.count);                                                               \
-        }                                                                                               \
-        return HSDE_OK;                                                                                 \
-    }
+#define X(cp, g)                                                                  \
+    if (bk.cmax == cp) return mixed ? rev_launch_one<float, cp, g>(V, R, bk, st)   \
+                                    : rev_launch_one<double, cp, g>(V, R, bk, st);
     HSDE_REV_BUCKETS(X)
 #undef X
     return HSDE_ERANGE;

@@ -119,7 +119,7 @@ def test_invalid_options_rejected_before_any_device_call(hs, kw):
 def test_clique_beyond_the_largest_eigensolver_is_rejected(hs):
     """A clique larger than the library's eigensolvers take gives HSDE_ERANGE
     at setup, before any device call (so this needs no GPU)."""
-    big = 8 + max(64, int(hs.MAX_CLIQUE))
+    big = 8 + hs.MAX_CLIQUE[hs.MIXED]      # the default precision
     p = synth.block_arrow(2, big - 5, 5, 4, np.random.default_rng(3))
     assert hs.hsde_analyze(p)["c_max"] == big
     with pytest.raises(hs.HSDEError) as ei:
