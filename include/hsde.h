@@ -310,8 +310,16 @@ HSDE_API int  hsde_spd_inverse_noalloc(double* S, int32_t m, void* cuda_stream);
  * of instance i, keeping the pattern, the constraint matrices and the cached
  * factor S (which does not depend on c or b); the scaling factors sigma and
  * rho, M^{-1} zeta and 1 + zeta^T M^{-1} zeta (Eq. MatrixInverseResult) are
- * recomputed.  The iterate is left as it is.  Errors: HSDE_EINVAL (null or
- * non-finite). */
+ * recomputed.  The iterate is left as it is.  c and b are both host memory
+ * or both device memory of the handle's GPU (unified addressing tells them
+ * apart).  Device data never passes through the host: kernels check it and
+ * form the sums of the scaling, whose partials the host adds in a fixed
+ * order (the norms, sigma and rho can differ from the host path's in the
+ * last bit; unscaled handles upload c and b unchanged either way).  The
+ * caller's writes to device c and b must be complete (synchronise the
+ * producing stream) before the call; the call returns after its own work
+ * is done.  Errors: HSDE_EINVAL (null, non-finite, a mix of host and device
+ * pointers, or a pointer into another GPU). */
 HSDE_API int  hsde_set_data(hsde_handle* h, int32_t i, const double* c, const double* b);
 
 /* Unrolled differentiation (single-instance handles).  hsde_unrolled_forward
@@ -332,7 +340,10 @@ HSDE_API int  hsde_set_data(hsde_handle* h, int32_t i, const double* c, const do
  * as given (options alpha = 1 and scaling = 0): the scaling factors depend
  * on c and b.  Errors: HSDE_EINVAL (B != 1, K or ckpt < 1, alpha != 1 or
  * scaling on),
- * HSDE_ESTATE (backward without forward), HSDE_ENOMEM, HSDE_ECUDA. */
+ * HSDE_ESTATE (backward without forward), HSDE_ENOMEM, HSDE_ECUDA.
+ * Every array argument (x, y, xbar, ybar, gC, gb) may be host memory or
+ * device memory of the handle's GPU; device seeds must be complete before
+ * the call, and both calls return with their outputs written. */
 HSDE_API int  hsde_unrolled_forward(hsde_handle* h, int32_t K, int32_t ckpt, double* x, double* y,
                                     double* tau, double* kappa);
 HSDE_API int  hsde_unrolled_backward(hsde_handle* h, const double* xbar, const double* ybar,

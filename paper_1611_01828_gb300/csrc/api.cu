@@ -77,15 +77,10 @@ struct HostPrep {
 // Scaling factors of one instance from its ORIGINAL data (the practical form
 // of the cited ADMM; the paper applies it without saying how): sigma and rho
 // from max(||D b||, ||c||), where D b is the row-normalised b.
-void scale_factors(const HostPrep& H, const double* b, const double* c, const hsde_options& O, double& sigma,
-                   double& rho, double& bnorm, double& cnorm) {
-    double nb = 0.0, bb = 0.0, cc = 0.0;
-    for (int32_t i = 0; i < H.m; ++i) {
-        const double db = H.dscale[i] * b[i];
-        nb += db * db;
-        bb += b[i] * b[i];
-    }
-    for (size_t e = 0; e < H.diag.size(); ++e) cc += (H.diag[e] ? 1.0 : 2.0) * c[e] * c[e];
+// sigma, rho and the original norms from the sums sum (d_i b_i)^2, sum b_i^2
+// and the full-vec sum c_e^2 (reading P7).
+void scale_from_sums(double nb, double bb, double cc, const hsde_options& O, double& sigma, double& rho,
+                     double& bnorm, double& cnorm) {
     bnorm = std::sqrt(bb);
     cnorm = std::sqrt(cc);
     sigma = rho = 1.0;
@@ -95,6 +90,18 @@ void scale_factors(const HostPrep& H, const double* b, const double* c, const hs
         sigma = O.scale_norm / mx;
         rho = O.dual_weight * O.scale_norm / mx;
     }
+}
+
+void scale_factors(const HostPrep& H, const double* b, const double* c, const hsde_options& O, double& sigma,
+                   double& rho, double& bnorm, double& cnorm) {
+    double nb = 0.0, bb = 0.0, cc = 0.0;
+    for (int32_t i = 0; i < H.m; ++i) {
+        const double db = H.dscale[i] * b[i];
+        nb += db * db;
+        bb += b[i] * b[i];
+    }
+    for (size_t e = 0; e < H.diag.size(); ++e) cc += (H.diag[e] ? 1.0 : 2.0) * c[e] * c[e];
+    scale_from_sums(nb, bb, cc, O, sigma, rho, bnorm, cnorm);
 }
 
 int prepare(const hsde_problem* P, const hsde_options& O, HostPrep& H, std::string& err) {
@@ -279,6 +286,11 @@ struct hsde_handle {
     bool any_dense = false;
     bool need_rhs = true;      // f must be formed before the next iteration (after setup / set_state)
     UnrollWS uw;
+    // hsde_set_data from device memory: d_i of every instance and the
+    // per-CTA sums (allocated on first use)
+    double* dscale_dev = nullptr;
+    double* data_part = nullptr;
+    double* data_part_host = nullptr;   // pinned
 };
 
 namespace {
@@ -362,6 +374,9 @@ void free_handle(hsde_handle* h) {
     for (auto& e : h->ev_ce) if (e) cudaEventDestroy(e);
     if (h->arena) cudaFree(h->arena);
     if (h->uw.mem) cudaFree(h->uw.mem);
+    if (h->dscale_dev) cudaFree(h->dscale_dev);
+    if (h->data_part) cudaFree(h->data_part);
+    if (h->data_part_host) cudaFreeHost(h->data_part_host);
     if (h->host_inst) cudaFreeHost(h->host_inst);
     if (h->own_stream && h->st) cudaStreamDestroy(h->st);
     delete h;
@@ -863,6 +878,21 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
 int check_handle(const hsde_handle* h, int32_t i) {
     if (!h) return fail(HSDE_EINVAL, "null handle");
     if (i < 0 || i >= h->B) return fail(HSDE_EINVAL, "instance index out of range");
+    return HSDE_OK;
+}
+
+// kind = 1 for device (or managed) memory of the handle's GPU, 0 for host
+// memory; a pointer into another GPU's memory is refused.
+int pointer_kind(const hsde_handle* h, const void* p, int& kind) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        kind = 0;
+        return HSDE_OK;
+    }
+    kind = (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? 1 : 0;
+    if (a.type == cudaMemoryTypeDevice && a.device != h->device)
+        return fail(HSDE_EINVAL, "device pointer of another GPU");
     return HSDE_OK;
 }
 
@@ -1390,26 +1420,57 @@ int hsde_set_data(hsde_handle* h, int32_t i, const double* c, const double* b) {
     CK(cudaSetDevice(h->device));
     HostPrep& H = h->prep[i];
     const int64_t N = H.S.N();
-    for (int64_t e = 0; e < N; ++e)
-        if (!std::isfinite(c[e])) return fail(HSDE_EINVAL, "non-finite c");
-    for (int32_t j = 0; j < H.m; ++j)
-        if (!std::isfinite(b[j])) return fail(HSDE_EINVAL, "non-finite b");
-    // new scaling factors from the new data (D depends on A only)
-    scale_factors(H, b, c, h->opt, H.sigma, H.rho, H.bnorm, H.cnorm);
-    H.cvec.resize(N);
-    for (int64_t e = 0; e < N; ++e) H.cvec[e] = H.rho * c[e];
-    H.b.resize(H.m);
-    for (int32_t j = 0; j < H.m; ++j) H.b[j] = H.sigma * H.dscale[j] * b[j];
+    int kc, kb = 0;
+    if ((rc = pointer_kind(h, c, kc)) != HSDE_OK) return rc;
+    if (H.m && (rc = pointer_kind(h, b, kb)) != HSDE_OK) return rc;
+    if (H.m && kc != kb) return fail(HSDE_EINVAL, "c and b must both be host or both device pointers");
+    double* cdst = const_cast<double*>(h->V.c) + h->x_off[i];
+    double* bdst = const_cast<double*>(h->V.b) + h->m_off[i];
+    if (kc) {
+        // device data: sums and scaled copies by kernels, only 4 doubles per
+        // CTA come back to the host
+        if (!h->dscale_dev) {
+            std::vector<double> d;
+            for (const HostPrep& Hb : h->prep) d.insert(d.end(), Hb.dscale.begin(), Hb.dscale.end());
+            CK(cudaMalloc(&h->dscale_dev, sizeof(double) * std::max<size_t>(1, d.size())));
+            CK(cudaMalloc(&h->data_part, sizeof(double) * 4 * DATA_MAX_CTAS));
+            CK(cudaMallocHost(&h->data_part_host, sizeof(double) * 4 * DATA_MAX_CTAS));
+            if (!d.empty())
+                CK(cudaMemcpy(h->dscale_dev, d.data(), sizeof(double) * d.size(), cudaMemcpyHostToDevice));
+        }
+        const double* dsc = h->dscale_dev + h->m_off[i];
+        const uint8_t* dg = h->V.diag + h->x_off[i];
+        launch_data_sums(c, N, dg, b, H.m, dsc, h->data_part, h->st);
+        const int nb = data_grid(N, H.m);
+        CK(cudaMemcpyAsync(h->data_part_host, h->data_part, sizeof(double) * 4 * nb, cudaMemcpyDeviceToHost,
+                           h->st));
+        CK(cudaStreamSynchronize(h->st));
+        double sm[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int k = 0; k < nb; ++k)
+            for (int j = 0; j < 4; ++j) sm[j] += h->data_part_host[4 * k + j];
+        if (sm[0] != 0.0) return fail(HSDE_EINVAL, "non-finite c or b");
+        scale_from_sums(sm[1], sm[2], sm[3], h->opt, H.sigma, H.rho, H.bnorm, H.cnorm);
+        launch_data_apply(c, N, H.rho, b, H.m, H.sigma, dsc, cdst, bdst, h->st);
+        CK(cudaGetLastError());
+    } else {
+        for (int64_t e = 0; e < N; ++e)
+            if (!std::isfinite(c[e])) return fail(HSDE_EINVAL, "non-finite c");
+        for (int32_t j = 0; j < H.m; ++j)
+            if (!std::isfinite(b[j])) return fail(HSDE_EINVAL, "non-finite b");
+        // new scaling factors from the new data (D depends on A only)
+        scale_factors(H, b, c, h->opt, H.sigma, H.rho, H.bnorm, H.cnorm);
+        H.cvec.resize(N);
+        for (int64_t e = 0; e < N; ++e) H.cvec[e] = H.rho * c[e];
+        H.b.resize(H.m);
+        for (int32_t j = 0; j < H.m; ++j) H.b[j] = H.sigma * H.dscale[j] * b[j];
+        CK(cudaMemcpy(cdst, H.cvec.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+        if (H.m) CK(cudaMemcpy(bdst, H.b.data(), sizeof(double) * H.m, cudaMemcpyHostToDevice));
+    }
     if ((rc = sync_inst(h)) != HSDE_OK) return rc;
     InstDev I = h->host_inst[i];
     I.sigma = H.sigma; I.rho = H.rho; I.bnorm = H.bnorm; I.cnorm = H.cnorm;
     h->host_inst[i] = I;
     CK(cudaMemcpy(h->V.inst + i, &I, sizeof(InstDev), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(const_cast<double*>(h->V.c) + h->x_off[i], H.cvec.data(), sizeof(double) * N,
-                  cudaMemcpyHostToDevice));
-    if (H.m)
-        CK(cudaMemcpy(const_cast<double*>(h->V.b) + h->m_off[i], H.b.data(), sizeof(double) * H.m,
-                      cudaMemcpyHostToDevice));
     // S does not depend on (c, b); M^{-1} zeta and 1 + zeta^T M^{-1} zeta do
     launch_rhs(h->V, h->mixed, Mode::Setup, h->st);
     launch_spmv_A(h->V, Mode::Setup, h->st);
@@ -1447,8 +1508,9 @@ int hsde_unrolled_forward(hsde_handle* h, int32_t K, int32_t ckpt, double* x, do
     }
     if ((rc = sync_inst(h)) != HSDE_OK) return rc;
     const InstDev& I = h->host_inst[0];
-    if (x) CK(cudaMemcpy(x, h->V.x, sizeof(double) * h->V.Ntot, cudaMemcpyDeviceToHost));
-    if (y && h->V.Mtot) CK(cudaMemcpy(y, h->V.y, sizeof(double) * h->V.Mtot, cudaMemcpyDeviceToHost));
+    // caller buffers: host or device memory (unified addressing)
+    if (x) CK(cudaMemcpy(x, h->V.x, sizeof(double) * h->V.Ntot, cudaMemcpyDefault));
+    if (y && h->V.Mtot) CK(cudaMemcpy(y, h->V.y, sizeof(double) * h->V.Mtot, cudaMemcpyDefault));
     if (tau) *tau = I.tau;
     if (kappa) *kappa = I.kappa;
     w.forward_done = true;
@@ -1465,10 +1527,11 @@ int hsde_unrolled_backward(hsde_handle* h, const double* xbar, const double* yba
     const size_t T = h->mixed ? sizeof(float) : sizeof(double);
     cudaStream_t st = h->st;
     // seeds
-    if (xbar) CK(cudaMemcpyAsync(w.xbar, xbar, sizeof(double) * V.Ntot, cudaMemcpyHostToDevice, st));
+    // caller buffers: host or device memory (unified addressing)
+    if (xbar) CK(cudaMemcpyAsync(w.xbar, xbar, sizeof(double) * V.Ntot, cudaMemcpyDefault, st));
     else CK(cudaMemsetAsync(w.xbar, 0, sizeof(double) * V.Ntot, st));
     if (V.Mtot) {
-        if (ybar) CK(cudaMemcpyAsync(w.ybar, ybar, sizeof(double) * V.Mtot, cudaMemcpyHostToDevice, st));
+        if (ybar) CK(cudaMemcpyAsync(w.ybar, ybar, sizeof(double) * V.Mtot, cudaMemcpyDefault, st));
         else CK(cudaMemsetAsync(w.ybar, 0, sizeof(double) * V.Mtot, st));
     }
     const double sc[2] = {taubar, kappabar};
@@ -1523,8 +1586,8 @@ int hsde_unrolled_backward(hsde_handle* h, const double* xbar, const double* yba
     launch_rev_finish(V, R, st);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
-    if (gC) CK(cudaMemcpy(gC, w.gc, sizeof(double) * V.Ntot, cudaMemcpyDeviceToHost));
-    if (gb && V.Mtot) CK(cudaMemcpy(gb, w.gb, sizeof(double) * V.Mtot, cudaMemcpyDeviceToHost));
+    if (gC) CK(cudaMemcpy(gC, w.gc, sizeof(double) * V.Ntot, cudaMemcpyDefault));
+    if (gb && V.Mtot) CK(cudaMemcpy(gb, w.gb, sizeof(double) * V.Mtot, cudaMemcpyDefault));
     h->need_rhs = true;
     return HSDE_OK;
 }

@@ -237,6 +237,15 @@ void launch_post(const DevView& V, bool mixed, void* st);
 // H^T sums of the long entries (before k_post, and inside launch_rhs in Iter mode)
 void launch_long(const DevView& V, bool mixed, void* st);
 void launch_setup_den(const DevView& V, void* st);
+// New data from device memory: per-CTA sums (non-finite count, ||D b||^2,
+// ||b||^2, full-vec ||c||^2; 4 per CTA, data_grid(N, m) CTAs), then the
+// scaled copies c~ = rho c, b~ = sigma D b.
+constexpr int DATA_MAX_CTAS = 304;
+int data_grid(int64_t N, int32_t m);
+void launch_data_sums(const double* c, int64_t N, const uint8_t* diag, const double* b, int32_t m,
+                      const double* dscale, double* part, void* st);
+void launch_data_apply(const double* c, int64_t N, double rho, const double* b, int32_t m, double sigma,
+                       const double* dscale, double* cdst, double* bdst, void* st);
 // A x and A^T y of the stored iterate into V.ax, V.aty for the constraint
 // rows [r0, r1) and pattern entries [e0, e1) (after hsde_set_state)
 void launch_state_products(const DevView& V, int r0, int r1, int64_t e0, int64_t e1, void* st);

@@ -25,6 +25,7 @@
 // bitwise reproducible for a given launch configuration.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "internal.h"
@@ -770,6 +771,61 @@ void launch_post(const DevView& V, bool mixed, void* st) {
     if (V.ntiles == 0) return;
     if (mixed) k_post<float><<<V.ntiles, NT, 0, S_(st)>>>(V);
     else k_post<double><<<V.ntiles, NT, 0, S_(st)>>>(V);
+}
+
+// ---------------------------------------------------------------------------
+// New data (c, b) given in device memory (hsde_set_data).  k_data_sums forms,
+// per CTA, the count of non-finite values, sum (d_i b_i)^2, sum b_i^2 and the
+// full-vec sum of c_e^2 that the scaling of reading P7 needs; the host adds
+// the CTAs' partials in order.  k_data_apply writes c~ = rho c and
+// b~ = sigma D b into the instance's slices.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) k_data_sums(const double* c, int64_t N, const uint8_t* diag,
+                                                  const double* b, int32_t m, const double* dscale,
+                                                  double* part) {
+    __shared__ double sh[4 * (NT / 32)];
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    const int64_t stride = (int64_t)gridDim.x * NT;
+    for (int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x; e < N; e += stride) {
+        const double ce = c[e];
+        if (!isfinite(ce)) v[0] += 1.0;
+        else v[3] += (diag[e] ? 1.0 : 2.0) * ce * ce;
+    }
+    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < m; i += stride) {
+        const double bi = b[i];
+        if (!isfinite(bi)) {
+            v[0] += 1.0;
+        } else {
+            const double db = dscale[i] * bi;
+            v[1] += db * db;
+            v[2] += bi * bi;
+        }
+    }
+    block_sum_n<4>(v, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) part[4 * blockIdx.x + k] = v[k];
+}
+
+__global__ void __launch_bounds__(NT) k_data_apply(const double* c, int64_t N, double rho, const double* b,
+                                                   int32_t m, double sigma, const double* dscale, double* cdst,
+                                                   double* bdst) {
+    const int64_t stride = (int64_t)gridDim.x * NT;
+    for (int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x; e < N; e += stride) cdst[e] = rho * c[e];
+    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < m; i += stride)
+        bdst[i] = sigma * dscale[i] * b[i];
+}
+
+int data_grid(int64_t N, int32_t m) {
+    const int64_t n = std::max<int64_t>(N, m);
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + NT - 1) / NT, DATA_MAX_CTAS));
+}
+void launch_data_sums(const double* c, int64_t N, const uint8_t* diag, const double* b, int32_t m,
+                      const double* dscale, double* part, void* st) {
+    k_data_sums<<<data_grid(N, m), NT, 0, S_(st)>>>(c, N, diag, b, m, dscale, part);
+}
+void launch_data_apply(const double* c, int64_t N, double rho, const double* b, int32_t m, double sigma,
+                       const double* dscale, double* cdst, double* bdst, void* st) {
+    k_data_apply<<<data_grid(N, m), NT, 0, S_(st)>>>(c, N, rho, b, m, sigma, dscale, cdst, bdst);
 }
 
 void launch_gj_step(double* pool, const int64_t* offs, const int32_t* ms, const int64_t* tile_pre, int nact,

@@ -127,6 +127,19 @@ def _ptr(a, ct):
     return a.ctypes.data_as(C.POINTER(ct)) if a is not None else None
 
 
+def _dptr(a, n=None):
+    """(ctypes pointer, keep-alive) for an FP64 array argument that may be a
+    NumPy array (host memory) or an int (a device address of n values)."""
+    if a is None:
+        return None, None
+    if isinstance(a, int):
+        return C.cast(C.c_void_p(a), C.POINTER(C.c_double)), None
+    arr = np.ascontiguousarray(a, np.float64)
+    if n is not None and arr.shape[0] != n:
+        raise ValueError(f"expected {n} values, got {arr.shape[0]}")
+    return _ptr(arr, C.c_double), arr
+
+
 class _ProblemView:
     """Keeps the contiguous arrays alive while the C struct points at them."""
 
@@ -276,28 +289,36 @@ class Handle:
         return dict(kernels_per_iteration=pr.kernels_per_iteration, phases=phases,
                     sweeps_mean=pr.sweeps_mean, sweeps_max=pr.sweeps_max, phase_sweeps_max=phase_sweeps)
 
-    def hsde_set_data(self, i: int, c: np.ndarray, b: np.ndarray):
-        cc = np.ascontiguousarray(c, np.float64)
-        bb = np.ascontiguousarray(b, np.float64)
-        _ck(lib.hsde_set_data(self.h, i, _ptr(cc, C.c_double), _ptr(bb, C.c_double)), "hsde_set_data")
+    def hsde_set_data(self, i: int, c, b):
+        """c, b: NumPy arrays, or ints holding device addresses (both the same kind)."""
+        (pc, kc), (pb, kb) = _dptr(c), _dptr(b)
+        _ck(lib.hsde_set_data(self.h, i, pc, pb), "hsde_set_data")
 
-    def hsde_unrolled_forward(self, K: int, ckpt: int = 20):
+    def hsde_unrolled_forward(self, K: int, ckpt: int = 20, x=None, y=None):
+        """Returns (x, y, tau, kappa).  x, y: ints holding device addresses to
+        write into (then None is returned for them), or None for new NumPy arrays."""
         sz = self.sizes[0]
-        x, y = np.zeros(sz.N), np.zeros(sz.m)
+        xh = np.zeros(sz.N) if x is None else None
+        yh = np.zeros(sz.m) if y is None else None
+        px = _ptr(xh, C.c_double) if x is None else _dptr(x)[0]
+        py = _ptr(yh, C.c_double) if y is None else _dptr(y)[0]
         tau, kappa = C.c_double(), C.c_double()
-        _ck(lib.hsde_unrolled_forward(self.h, int(K), int(ckpt), _ptr(x, C.c_double), _ptr(y, C.c_double),
-                                      C.byref(tau), C.byref(kappa)), "hsde_unrolled_forward")
-        return x, y, tau.value, kappa.value
+        _ck(lib.hsde_unrolled_forward(self.h, int(K), int(ckpt), px, py, C.byref(tau), C.byref(kappa)),
+            "hsde_unrolled_forward")
+        return xh, yh, tau.value, kappa.value
 
-    def hsde_unrolled_backward(self, xbar, ybar, taubar: float, kappabar: float):
+    def hsde_unrolled_backward(self, xbar, ybar, taubar: float, kappabar: float, gC=None, gb=None):
+        """Returns (gC, gb).  xbar, ybar: NumPy arrays or device addresses (ints);
+        gC, gb: device addresses to write into (None is returned for them) or None."""
         sz = self.sizes[0]
-        xb = np.ascontiguousarray(xbar, np.float64)
-        yb = np.ascontiguousarray(ybar, np.float64)
-        gC, gb = np.zeros(sz.N), np.zeros(sz.m)
-        _ck(lib.hsde_unrolled_backward(self.h, _ptr(xb, C.c_double), _ptr(yb, C.c_double), float(taubar),
-                                       float(kappabar), _ptr(gC, C.c_double), _ptr(gb, C.c_double)),
+        (pxb, kx), (pyb, ky) = _dptr(xbar, sz.N), _dptr(ybar, sz.m)
+        gCh = np.zeros(sz.N) if gC is None else None
+        gbh = np.zeros(sz.m) if gb is None else None
+        pg = _ptr(gCh, C.c_double) if gC is None else _dptr(gC)[0]
+        pgb = _ptr(gbh, C.c_double) if gb is None else _dptr(gb)[0]
+        _ck(lib.hsde_unrolled_backward(self.h, pxb, pyb, float(taubar), float(kappabar), pg, pgb),
             "hsde_unrolled_backward")
-        return gC, gb
+        return gCh, gbh
 
     # ---- convenience: run to a verdict in chunks ----
     def solve(self, chunk: int = 20):

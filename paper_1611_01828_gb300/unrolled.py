@@ -43,29 +43,57 @@ def pattern_values(handle, rows, cols, vals) -> np.ndarray:
     return out
 
 
+def _f64(t):
+    return t.detach().to(torch.float64).contiguous()
+
+
 class UnrolledHSDE(torch.autograd.Function):
-    """(c, b) -> (x_K, y_K, tau_K, kappa_K) after K iterations from the standard start."""
+    """(c, b) -> (x_K, y_K, tau_K, kappa_K) after K iterations from the standard start.
+
+    CUDA tensors on the handle's GPU go to the library as device addresses
+    (no host copy of C, b, the outputs or the upstream gradients); CPU
+    tensors go as host arrays."""
 
     @staticmethod
     def forward(ctx, c, b, handle, K: int, ckpt: int):
-        handle.hsde_set_data(0, c.detach().to("cpu", torch.float64).numpy(),
-                             b.detach().to("cpu", torch.float64).numpy())
-        x, y, tau, kappa = handle.hsde_unrolled_forward(K, ckpt)
+        sz = handle.sizes[0]
         ctx.handle = handle
         ctx.meta = (c.device, c.dtype, b.device, b.dtype)
-        f = lambda a, d, t: torch.as_tensor(np.asarray(a), dtype=t, device=d)
-        return f(x, c.device, c.dtype), f(y, b.device, b.dtype), f(tau, c.device, c.dtype), f(kappa, c.device, c.dtype)
+        if c.is_cuda:
+            c64, b64 = _f64(c), _f64(b.to(c.device))
+            x = torch.empty(sz.N, dtype=torch.float64, device=c.device)
+            y = torch.empty(sz.m, dtype=torch.float64, device=c.device)
+            torch.cuda.current_stream(c.device).synchronize()
+            handle.hsde_set_data(0, c64.data_ptr(), b64.data_ptr())
+            _, _, tau, kappa = handle.hsde_unrolled_forward(K, ckpt, x=x.data_ptr(), y=y.data_ptr())
+        else:
+            handle.hsde_set_data(0, _f64(c).numpy(), _f64(b).numpy())
+            xh, yh, tau, kappa = handle.hsde_unrolled_forward(K, ckpt)
+            x, y = torch.from_numpy(xh), torch.from_numpy(yh)
+        sc = lambda v: torch.tensor(v, dtype=c.dtype, device=c.device)
+        return x.to(c.dtype), y.to(device=b.device, dtype=b.dtype), sc(tau), sc(kappa)
 
     @staticmethod
     def backward(ctx, gx, gy, gtau, gkappa):
         cdev, cdt, bdev, bdt = ctx.meta
         sz = ctx.handle.sizes[0]
-        np_ = lambda t, n: (t.detach().to("cpu", torch.float64).numpy() if t is not None else np.zeros(n))
-        gC, gb = ctx.handle.hsde_unrolled_backward(np_(gx, sz.N), np_(gy, sz.m),
-                                                   float(gtau) if gtau is not None else 0.0,
-                                                   float(gkappa) if gkappa is not None else 0.0)
-        return (torch.as_tensor(gC, dtype=cdt, device=cdev), torch.as_tensor(gb, dtype=bdt, device=bdev),
-                None, None, None)
+        taubar = float(gtau) if gtau is not None else 0.0
+        kappabar = float(gkappa) if gkappa is not None else 0.0
+        if cdev.type == "cuda":
+            xb = _f64(gx) if gx is not None else None
+            yb = _f64(gy.to(cdev)) if gy is not None else None
+            gC = torch.empty(sz.N, dtype=torch.float64, device=cdev)
+            gb = torch.empty(sz.m, dtype=torch.float64, device=cdev)
+            torch.cuda.current_stream(cdev).synchronize()
+            ctx.handle.hsde_unrolled_backward(xb.data_ptr() if xb is not None else None,
+                                              yb.data_ptr() if yb is not None else None,
+                                              taubar, kappabar, gC=gC.data_ptr(), gb=gb.data_ptr())
+        else:
+            xb = _f64(gx).numpy() if gx is not None else None
+            yb = _f64(gy).numpy() if gy is not None else None
+            gCh, gbh = ctx.handle.hsde_unrolled_backward(xb, yb, taubar, kappabar)
+            gC, gb = torch.from_numpy(gCh), torch.from_numpy(gbh)
+        return gC.to(cdt), gb.to(device=bdev, dtype=bdt), None, None, None
 
 
 def unrolled_objective(c, b, handle, K: int, ckpt: int = 20, weights=None):

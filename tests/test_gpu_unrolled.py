@@ -133,3 +133,68 @@ def test_diff_grid_mixed_gradient_close_to_fp64(env, diff_grid):
         _, gC32, gb32 = _grad(torch, hsde, unrolled, Hm, c0, p.b, K, ckpt)
     g64 = np.concatenate([gC64, gb64]); g32 = np.concatenate([gC32, gb32])
     assert np.linalg.norm(g32 - g64) <= 2e-2 * np.linalg.norm(g64)
+
+
+def test_device_tensors_match_host_path(env, diff_grid):
+    """CUDA tensors go to the library as device addresses; the C-ABI results
+    are bitwise those of host arrays, and the autograd gradient agrees up to
+    the order of the objective's sum."""
+    torch, hsde, unrolled = env
+    p, H, c0 = diff_grid
+    K, ckpt = 60, 20
+    H.hsde_set_data(0, c0, p.b)
+    xh, yh, th, kh = H.hsde_unrolled_forward(K, ckpt)
+    rng = np.random.default_rng(5)
+    xb, yb = rng.standard_normal(xh.shape[0]), rng.standard_normal(yh.shape[0])
+    gCh, gbh = H.hsde_unrolled_backward(xb, yb, 0.3, -0.7)
+
+    dev = torch.device("cuda")
+    cd = torch.tensor(c0, device=dev); bd = torch.tensor(p.b, device=dev)
+    xd = torch.empty(xh.shape[0], dtype=torch.float64, device=dev)
+    yd = torch.empty(yh.shape[0], dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    H.hsde_set_data(0, cd.data_ptr(), bd.data_ptr())
+    _, _, td, kd = H.hsde_unrolled_forward(K, ckpt, x=xd.data_ptr(), y=yd.data_ptr())
+    assert (td, kd) == (th, kh)
+    assert np.array_equal(xd.cpu().numpy(), xh) and np.array_equal(yd.cpu().numpy(), yh)
+    xbd, ybd = torch.tensor(xb, device=dev), torch.tensor(yb, device=dev)
+    gCd = torch.empty_like(xd); gbd = torch.empty_like(yd)
+    torch.cuda.synchronize()
+    H.hsde_unrolled_backward(xbd.data_ptr(), ybd.data_ptr(), 0.3, -0.7, gC=gCd.data_ptr(), gb=gbd.data_ptr())
+    assert np.array_equal(gCd.cpu().numpy(), gCh) and np.array_equal(gbd.cpu().numpy(), gbh)
+
+    f_h, gC_h, gb_h = _grad(torch, hsde, unrolled, H, c0, p.b, K, ckpt)
+    ct = torch.tensor(c0, device=dev, requires_grad=True)
+    bt = torch.tensor(p.b, device=dev, requires_grad=True)
+    f = unrolled.unrolled_objective(ct, bt, H, K, ckpt)
+    f.backward()
+    assert ct.grad.is_cuda and bt.grad.is_cuda
+    assert float(f) == pytest.approx(f_h, rel=1e-12)
+    assert np.linalg.norm(ct.grad.cpu().numpy() - gC_h) <= 1e-10 * np.linalg.norm(gC_h)
+    assert np.linalg.norm(bt.grad.cpu().numpy() - gb_h) <= 1e-10 * np.linalg.norm(gb_h)
+
+
+def test_set_data_from_device_memory_on_a_scaled_handle(env):
+    """New data from device memory: the scaling sums are formed by kernels
+    (another summation order), so the iterate after 30 iterations agrees
+    with the host path's to rounding; a mix of host and device pointers is
+    refused on the host."""
+    torch, hsde, unrolled = env
+    p = synth.maxcut_grid(4, 6, np.random.default_rng(3))
+    rng = np.random.default_rng(8)
+    with hsde.Handle(p, precision="fp64") as H:
+        c1 = unrolled.pattern_values(H, p.C_row, p.C_col, p.C_val * (1.0 + 0.1 * rng.standard_normal(p.C_val.shape[0])))
+        b1 = p.b * 1.3
+        s0 = H.hsde_get_state(0)
+        H.hsde_set_data(0, c1, b1)
+        H.hsde_iterate(30)
+        sh = H.hsde_get_state(0)
+        H.hsde_set_state(0, s0)
+        cd = torch.tensor(c1, device="cuda"); bd = torch.tensor(b1, device="cuda")
+        torch.cuda.synchronize()
+        H.hsde_set_data(0, cd.data_ptr(), bd.data_ptr())
+        H.hsde_iterate(30)
+        sd = H.hsde_get_state(0)
+        assert np.max(np.abs(sd - sh)) <= 1e-10 * (1.0 + np.max(np.abs(sh)))
+        with pytest.raises(hsde.HSDEError):
+            H.hsde_set_data(0, cd.data_ptr(), b1)
