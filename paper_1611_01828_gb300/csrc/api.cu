@@ -70,7 +70,6 @@ struct HostPrep {
     bool dense = false;                       // two constraints share an entry
     bool lowrank = false;                     // dense S kept as B + U U^T (factor.cu)
     LowRankHost lr;
-    std::vector<double> Sdense;               // m*m (dense case)
     std::vector<double> Sdiag_inv;            // m (diagonal case)
 };
 
@@ -141,6 +140,8 @@ int prepare(const hsde_problem* P, const hsde_options& O, HostPrep& H, std::stri
     H.dscale.assign(m, 1.0);
     const int64_t a0 = m > 0 ? P->A_ptr[0] : 0;
     std::vector<std::pair<int32_t, double>> row;
+    H.A_col.reserve(m > 0 ? (size_t)(P->A_ptr[m] - a0) : 0);
+    H.A_val.reserve(H.A_col.capacity());
     for (int32_t i = 0; i < m; ++i) {
         row.clear();
         double nrm = 0.0;
@@ -152,10 +153,11 @@ int prepare(const hsde_problem* P, const hsde_options& O, HostPrep& H, std::stri
         }
         if (O.scaling && nrm > 0.0) H.dscale[i] = 1.0 / std::sqrt(nrm);
         for (auto& pr : row) pr.second *= H.dscale[i];
-        std::sort(row.begin(), row.end(),
-                  [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
-                      return a.first < b.first;
-                  });
+        // entries given in (column, row) order are already in pattern order
+        const auto by_e = [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
+            return a.first < b.first;
+        };
+        if (!std::is_sorted(row.begin(), row.end(), by_e)) std::sort(row.begin(), row.end(), by_e);
         for (auto& pr : row) {
             H.A_col.push_back(pr.first);
             H.A_val.push_back(H.diag[pr.first] ? pr.second : 2.0 * pr.second);
@@ -202,22 +204,8 @@ int prepare(const hsde_problem* P, const hsde_options& O, HostPrep& H, std::stri
             }
         H.Sdiag_inv.resize(m);
         for (int32_t i = 0; i < m; ++i) H.Sdiag_inv[i] = 1.0 / d[i];
-    } else {
-        H.Sdense.assign((size_t)m * m, 0.0);
-        double* Sm = H.Sdense.data();
-        for (int32_t i = 0; i < m; ++i) Sm[(size_t)i * m + i] = 1.0;
-        for (int64_t e = 0; e < N; ++e) {
-            const int32_t j0 = H.At_ptr[e], j1 = H.At_ptr[e + 1];
-            const double w = (H.diag[e] ? 1.0 : 2.0) * H.inv_delta[e];
-            for (int32_t ja = j0; ja < j1; ++ja) {
-                const double wa = w * H.At_val[ja];
-                double* Srow = Sm + (size_t)H.At_col[ja] * m;
-                for (int32_t jb = j0; jb <= ja; ++jb) Srow[H.At_col[jb]] += wa * H.At_val[jb];
-            }
-        }
-        for (int32_t i = 0; i < m; ++i)
-            for (int32_t j = 0; j < i; ++j) Sm[(size_t)j * m + i] = Sm[(size_t)i * m + j];
     }
+    // otherwise S is dense: formed on the device (k_form_S) and inverted there
     return HSDE_OK;
 }
 
@@ -787,12 +775,11 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
             if (h->prep[b].dense && !h->prep[b].lowrank) ord.push_back(b);
         std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return h->prep[a].m > h->prep[b].m; });
         std::vector<int64_t> offs, boffs, tpre;
-        std::vector<int32_t> ms;
+        std::vector<int32_t> ms, rows;
         int64_t acc_tiles = 0;
         for (int32_t b : ord) {
             const HostPrep& H = h->prep[b];
-            CK(cudaMemcpyAsync(V.sinv + inst[b].sinv_off, H.Sdense.data(), sizeof(double) * H.Sdense.size(),
-                               cudaMemcpyHostToDevice, st));
+            for (int32_t i = 0; i < H.m; ++i) rows.push_back(inst[b].m_off + i);
             offs.push_back(inst[b].sinv_off);
             ms.push_back(H.m);
             boffs.push_back(inst[b].m_off);
@@ -801,6 +788,18 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         }
         tpre.push_back(acc_tiles);
         UP(o_gjoff, offs); UP(o_gjm, ms); UP(o_gjb, boffs); UP(o_gjtp, tpre);
+        {
+            // S = I + A Delta^{-1} A^T of every dense instance, in the pool
+            int32_t* drows = nullptr;
+            CK(cudaMalloc(&drows, sizeof(int32_t) * rows.size()));
+            const cudaError_t e1 =
+                cudaMemcpyAsync(drows, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice, st);
+            if (e1 == cudaSuccess) launch_form_S(V, drows, (int32_t)rows.size(), mmax, st);
+            const cudaError_t e2 = cudaGetLastError();
+            const cudaError_t e3 = cudaStreamSynchronize(st);
+            cudaFree(drows);
+            CK(e1); CK(e2); CK(e3);
+        }
         int nact = (int)ord.size();
         for (int32_t k = 0; k < mmax; ++k) {
             while (nact > 0 && ms[nact - 1] <= k) --nact;
@@ -810,7 +809,6 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         }
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(st));
-        for (auto& H : h->prep) { std::vector<double>().swap(H.Sdense); }
     }
 #undef UP
     // ---- cached M^{-1} zeta = (x_p, ., y_p, .) and 1 + zeta^T M^{-1} zeta ----

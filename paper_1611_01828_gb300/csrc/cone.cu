@@ -307,8 +307,10 @@ __device__ __forceinline__ int packed_column(int e, int c) {
     return b;
 }
 
-template <typename T, int CP, int G>
-__global__ void __launch_bounds__(ConeCfg<T, CP, G>::NTH, ConeCfg<T, CP, G>::MINB)
+// MB: resident CTAs the registers are sized for (ConeCfg::MINB, or 1 for a
+// bucket whose CTAs each have an SM to themselves).
+template <typename T, int CP, int G, int MB>
+__global__ void __launch_bounds__(ConeCfg<T, CP, G>::NTH, MB)
 k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T tol2, int warm, int refresh) {
     using Cfg = ConeCfg<T, CP, G>;
     using V2 = typename Vec2<T>::type;
@@ -703,8 +705,14 @@ static int prepare_one() {
         // launch asks for when the bucket has few cliques (a CTA alone on its SM)
         const int want = Cfg::GPB == 1 ? std::max<int>(g_smem_optin, (int)Cfg::smem) : (int)Cfg::smem;
         if (want > 48 * 1024 &&
-            cudaFuncSetAttribute(k_cone<T, CP, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, want) != cudaSuccess)
+            cudaFuncSetAttribute(k_cone<T, CP, G, Cfg::MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, want) !=
+                cudaSuccess)
             return HSDE_ECUDA;
+        if constexpr (Cfg::GPB == 1 && CP >= 32 && Cfg::MINB != 1) {
+            if (cudaFuncSetAttribute(k_cone<T, CP, G, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, want) !=
+                cudaSuccess)
+                return HSDE_ECUDA;
+        }
         return HSDE_OK;
     }
 }
@@ -731,9 +739,18 @@ static int launch_one(const DevView& V, const Bucket& bk, int max_sweeps, double
     } else {
         using Cfg = ConeCfg<T, CP, G>;
         const int grid = (bk.count + Cfg::GPB - 1) / Cfg::GPB;
+        const T tol2 = (T)(tol * tol);
+        if constexpr (Cfg::GPB == 1 && CP >= 32 && Cfg::MINB != 1) {
+            // a CTA alone on its SM: the variant with the full register budget
+            if (alone_one<T, CP, G>(bk)) {
+                k_cone<T, CP, G, 1><<<grid, Cfg::NTH, (size_t)g_smem_optin, st>>>(V, bk.list, bk.count, max_sweeps,
+                                                                                 tol2, warm, refresh);
+                return HSDE_OK;
+            }
+        }
         const size_t smem = alone_one<T, CP, G>(bk) ? (size_t)g_smem_optin : Cfg::smem;
-        k_cone<T, CP, G><<<grid, Cfg::NTH, smem, st>>>(V, bk.list, bk.count, max_sweeps, (T)(tol * tol), warm,
-                                                         refresh);
+        k_cone<T, CP, G, Cfg::MINB><<<grid, Cfg::NTH, smem, st>>>(V, bk.list, bk.count, max_sweeps, tol2, warm,
+                                                                    refresh);
         return HSDE_OK;
     }
 }

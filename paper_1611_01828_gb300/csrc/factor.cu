@@ -114,22 +114,93 @@ bool build_lowrank(int32_t m, int64_t N, const int32_t* At_ptr, const int32_t* A
         L.blk_off[k] = tot;
         tot += (int64_t)bsz[k] * bsz[k];
     }
-    // B = I + local terms, block by block (row-major, both triangles: the
-    // product a_i a_j is formed once per ordered pair, so B is exactly
-    // symmetric)
+    // B = I + local terms, block by block (row-major, both triangles).  The
+    // local entries of a block are gathered into a dense b x n_e matrix G
+    // (row p: constraint p's values times sqrt(w_e Delta_e^{-1})), and
+    // B = I + G G^T is formed by dot products over contiguous rows (the lower
+    // triangle, mirrored: B is exactly symmetric).  A block whose entries
+    // touch few of its constraints (G mostly zero) is scattered entry by
+    // entry instead.
     L.binv.assign(tot, 0.0);
     for (int32_t k = 0; k < nb; ++k)
         for (int32_t p = 0; p < bsz[k]; ++p) L.binv[L.blk_off[k] + (int64_t)p * bsz[k] + p] = 1.0;
+    std::vector<int64_t> bent_ptr(nb + 1, 0), pairs(nb, 0);
     for (int64_t e = 0; e < N; ++e) {
         const int32_t j0 = At_ptr[e], j1 = At_ptr[e + 1];
         if (j1 - j0 > LR_BMAX || j1 == j0) continue;
-        const double w = (diag[e] ? 1.0 : 2.0) * inv_delta[e];
-        const int32_t k = L.row_blk[At_col[j0]], b = bsz[k];
+        const int32_t k = L.row_blk[At_col[j0]];
+        bent_ptr[k + 1] += 1;
+        pairs[k] += (int64_t)(j1 - j0) * (j1 - j0);
+    }
+    for (int32_t k = 0; k < nb; ++k) bent_ptr[k + 1] += bent_ptr[k];
+    std::vector<int64_t> bent(bent_ptr[nb]);
+    {
+        std::vector<int64_t> fill(bent_ptr.begin(), bent_ptr.end() - 1);
+        for (int64_t e = 0; e < N; ++e) {
+            const int32_t j0 = At_ptr[e], j1 = At_ptr[e + 1];
+            if (j1 - j0 > LR_BMAX || j1 == j0) continue;
+            bent[fill[L.row_blk[At_col[j0]]]++] = e;
+        }
+    }
+    std::vector<double> G;
+    std::vector<int32_t> pos;
+    std::vector<double> val;
+    for (int32_t k = 0; k < nb; ++k) {
+        const int32_t b = bsz[k];
+        const int64_t ne = bent_ptr[k + 1] - bent_ptr[k];
         double* Bk = L.binv.data() + L.blk_off[k];
-        for (int32_t ja = j0; ja < j1; ++ja) {
-            const int32_t pa = L.row_pos[At_col[ja]];
-            for (int32_t jb = j0; jb < j1; ++jb)
-                Bk[(int64_t)pa * b + L.row_pos[At_col[jb]]] += w * (At_val[ja] * At_val[jb]);
+        if (ne == 0) continue;
+        if (4 * pairs[k] >= (int64_t)b * b * ne) {
+            G.assign((size_t)b * ne, 0.0);
+            for (int64_t q = 0; q < ne; ++q) {
+                const int64_t e = bent[bent_ptr[k] + q];
+                const double sw = std::sqrt((diag[e] ? 1.0 : 2.0) * inv_delta[e]);
+                for (int32_t j = At_ptr[e]; j < At_ptr[e + 1]; ++j)
+                    G[(size_t)L.row_pos[At_col[j]] * ne + q] = sw * At_val[j];
+            }
+            // lower triangle in 4 x 4 tiles of (pa, pb), 16 running sums each
+            for (int32_t pa0 = 0; pa0 < b; pa0 += 4)
+                for (int32_t pb0 = 0; pb0 <= pa0; pb0 += 4) {
+                    double acc[4][4] = {};
+                    const double* ga[4];
+                    const double* gb[4];
+                    for (int u = 0; u < 4; ++u) {
+                        ga[u] = G.data() + (size_t)std::min(pa0 + u, b - 1) * ne;
+                        gb[u] = G.data() + (size_t)std::min(pb0 + u, b - 1) * ne;
+                    }
+                    for (int64_t q = 0; q < ne; ++q) {
+                        const double a0 = ga[0][q], a1 = ga[1][q], a2 = ga[2][q], a3 = ga[3][q];
+                        const double b0 = gb[0][q], b1 = gb[1][q], b2 = gb[2][q], b3 = gb[3][q];
+                        acc[0][0] += a0 * b0; acc[0][1] += a0 * b1; acc[0][2] += a0 * b2; acc[0][3] += a0 * b3;
+                        acc[1][0] += a1 * b0; acc[1][1] += a1 * b1; acc[1][2] += a1 * b2; acc[1][3] += a1 * b3;
+                        acc[2][0] += a2 * b0; acc[2][1] += a2 * b1; acc[2][2] += a2 * b2; acc[2][3] += a2 * b3;
+                        acc[3][0] += a3 * b0; acc[3][1] += a3 * b1; acc[3][2] += a3 * b2; acc[3][3] += a3 * b3;
+                    }
+                    for (int u = 0; u < 4; ++u)
+                        for (int v = 0; v < 4; ++v) {
+                            const int32_t pa = pa0 + u, pb = pb0 + v;
+                            if (pa >= b || pb > pa) continue;
+                            Bk[(int64_t)pa * b + pb] += acc[u][v];
+                            if (pb != pa) Bk[(int64_t)pb * b + pa] += acc[u][v];
+                        }
+                }
+        } else {
+            for (int64_t q = 0; q < ne; ++q) {
+                const int64_t e = bent[bent_ptr[k] + q];
+                const int32_t j0 = At_ptr[e], j1 = At_ptr[e + 1];
+                const double w = (diag[e] ? 1.0 : 2.0) * inv_delta[e];
+                pos.resize(j1 - j0);
+                val.resize(j1 - j0);
+                for (int32_t j = j0; j < j1; ++j) {
+                    pos[j - j0] = L.row_pos[At_col[j]];
+                    val[j - j0] = At_val[j];
+                }
+                for (int32_t a = 0; a < j1 - j0; ++a) {
+                    double* Brow = Bk + (int64_t)pos[a] * b;
+                    const double wa = w * val[a];
+                    for (int32_t c = 0; c < j1 - j0; ++c) Brow[pos[c]] += wa * val[c];
+                }
+            }
         }
     }
     for (int32_t k = 0; k < nb; ++k) gj_inverse_host(L.binv.data() + L.blk_off[k], bsz[k]);

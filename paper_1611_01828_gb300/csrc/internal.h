@@ -237,6 +237,11 @@ void launch_post(const DevView& V, bool mixed, void* st);
 // H^T sums of the long entries (before k_post, and inside launch_rhs in Iter mode)
 void launch_long(const DevView& V, bool mixed, void* st);
 void launch_setup_den(const DevView& V, void* st);
+// Dense S = I + A Delta^{-1} A^T into the S^{-1} pool (before its in-place
+// inversion), one warp per listed constraint row (absolute indices, rows of
+// instances with dense == 1); mmax = the largest m among them.
+constexpr size_t FORM_S_SMEM = 200 * 1024;
+void launch_form_S(const DevView& V, const int32_t* rows, int32_t nrows, int32_t mmax, void* st);
 // New data from device memory: per-CTA sums (non-finite count, ||D b||^2,
 // ||b||^2, full-vec ||c||^2; 4 per CTA, data_grid(N, m) CTAs), then the
 // scaled copies c~ = rho c, b~ = sigma D b.

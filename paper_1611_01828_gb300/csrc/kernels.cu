@@ -719,6 +719,41 @@ __global__ void k_gj_update(double* pool, const int64_t* offs, const int32_t* ms
 }
 
 // ---------------------------------------------------------------------------
+// Dense S = I + A Delta^{-1} A^T (Section 4.3, the matrix of Eq.
+// FactorizationMatrix) formed on the device, one warp per constraint row i of
+// the dense instances:  S_ij = delta_ij + sum_{e in A_i} A_ie Delta_e^{-1}
+// a_je, with A_ie the weighted value of row i (off-diagonal entries count
+// twice) and a_je the raw values of column e of A^T.  The warp walks row i's
+// entries in order and its lanes spread over each entry's constraints, which
+// are distinct, so every S_ij receives its terms in a fixed order
+// (deterministic); the row is built in shared memory (SMEM) or in place in
+// the pool row, which the warp owns.
+// ---------------------------------------------------------------------------
+template <bool SMEM>
+__global__ void k_form_S(DevView V, const int32_t* rows, int32_t nrows, int warps) {
+    extern __shared__ double srow[];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int32_t r = blockIdx.x * warps + w;
+    if (r >= nrows) return;
+    const int32_t i = rows[r];
+    const InstDev& I = V.inst[V.row_inst[i]];
+    const int32_t m = I.m, mo = I.m_off;
+    double* out = V.sinv + I.sinv_off + (int64_t)(i - mo) * m;
+    double* acc = SMEM ? srow + (size_t)w * m : out;
+    for (int32_t j = l; j < m; j += 32) acc[j] = (j == i - mo) ? 1.0 : 0.0;
+    __syncwarp();
+    for (int32_t k = V.A_ptr[i]; k < V.A_ptr[i + 1]; ++k) {
+        const int32_t e = V.A_col[k];
+        const double we = V.A_val[k] * V.inv_delta[e];
+        for (int32_t t = V.At_ptr[e] + l; t < V.At_ptr[e + 1]; t += 32)
+            acc[V.At_col[t] - mo] += we * V.At_val[t];
+        __syncwarp();
+    }
+    if (SMEM)
+        for (int32_t j = l; j < m; j += 32) out[j] = acc[j];
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 static inline cudaStream_t S_(void* st) { return reinterpret_cast<cudaStream_t>(st); }
@@ -836,6 +871,19 @@ void launch_gj_step(double* pool, const int64_t* offs, const int32_t* ms, const 
     k_gj_copy<<<gc, 256, 0, S_(st)>>>(pool, offs, ms, nact, k, rowbuf, colbuf, boff);
     k_gj_update<<<(unsigned)ntiles, dim3(32, 8), 0, S_(st)>>>(pool, offs, ms, tile_pre, nact, k, rowbuf, colbuf,
                                                              boff);
+}
+
+void launch_form_S(const DevView& V, const int32_t* rows, int32_t nrows, int32_t mmax, void* st) {
+    if (nrows <= 0) return;
+    const size_t per_warp = sizeof(double) * (size_t)mmax;
+    if (per_warp <= FORM_S_SMEM / 2) {
+        const int warps = (int)std::min<size_t>(8, FORM_S_SMEM / per_warp);
+        const size_t sm = per_warp * warps;
+        cudaFuncSetAttribute(k_form_S<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_form_S<true><<<(nrows + warps - 1) / warps, 32 * warps, sm, S_(st)>>>(V, rows, nrows, warps);
+    } else {
+        k_form_S<false><<<(nrows + 7) / 8, 256, 0, S_(st)>>>(V, rows, nrows, 8);
+    }
 }
 
 }  // namespace hsde

@@ -107,8 +107,24 @@ static bool check_coo(int32_t n, int64_t nnz, const int32_t* r, const int32_t* c
         err = std::string(what) + ": null pointer or negative count";
         return false;
     }
+    // entries given in (column, row) order, the usual case, need no sort:
+    // strictly increasing keys have no duplicate
+    bool increasing = true;
+    int64_t prev = -1;
+    for (int64_t k = 0; k < nnz; ++k) {
+        if (r[k] < 0 || r[k] >= n || c[k] < 0 || c[k] >= n) {
+            err = std::string(what) + ": index out of range";
+            return false;
+        }
+        const int64_t key = (int64_t)c[k] * n + r[k];
+        if (key <= prev) {
+            increasing = false;
+            break;
+        }
+        prev = key;
+    }
     std::vector<int64_t> keys;
-    keys.reserve((size_t)nnz);
+    if (!increasing) keys.reserve((size_t)nnz);
     for (int64_t k = 0; k < nnz; ++k) {
         if (r[k] < 0 || r[k] >= n || c[k] < 0 || c[k] >= n) {
             err = std::string(what) + ": index out of range";
@@ -122,7 +138,7 @@ static bool check_coo(int32_t n, int64_t nnz, const int32_t* r, const int32_t* c
             err = std::string(what) + ": non-finite value";
             return false;
         }
-        keys.push_back((int64_t)c[k] * n + r[k]);
+        if (!increasing) keys.push_back((int64_t)c[k] * n + r[k]);
     }
     std::sort(keys.begin(), keys.end());
     if (std::adjacent_find(keys.begin(), keys.end()) != keys.end()) {
@@ -160,18 +176,40 @@ int build_symbolic(const hsde_problem* P, Symbolic& S, std::string& err) {
     }
 
     // ---- aggregate pattern: adjacency (off-diagonal) as sorted lists ----
-    std::vector<std::vector<int32_t>> adj(n);
-    auto add = [&](int32_t r, int32_t c) {
-        if (r != c) { adj[r].push_back(c); adj[c].push_back(r); }
+    // The constraint matrices of clique-local problems repeat the same
+    // entries many times (5M entries for 30k distinct ones on a block-arrow
+    // with d = 50), so the entries are bucketed by column (counting sort)
+    // and de-duplicated with a stamp per row, in time linear in the input.
+    const int64_t annz = m > 0 ? P->A_ptr[m] - P->A_ptr[0] : 0;
+    const int32_t* Ar = m > 0 ? P->A_row : nullptr;
+    const int32_t* Ac = m > 0 ? P->A_col : nullptr;
+    std::vector<int64_t> cptr(n + 1, 0);
+    auto each_entry = [&](auto&& fn) {
+        for (int64_t k = 0; k < P->C_nnz; ++k) fn(P->C_row[k], P->C_col[k]);
+        for (int64_t k = 0; k < annz; ++k) fn(Ar[k], Ac[k]);
+        for (int64_t k = 0; k < P->pattern_nnz; ++k) fn(P->pattern_row[k], P->pattern_col[k]);
     };
-    for (int64_t k = 0; k < P->C_nnz; ++k) add(P->C_row[k], P->C_col[k]);
-    const int64_t annz = m > 0 ? P->A_ptr[m] : 0;
-    for (int64_t k = 0; k < annz; ++k) add(P->A_row[k], P->A_col[k]);
-    for (int64_t k = 0; k < P->pattern_nnz; ++k) add(P->pattern_row[k], P->pattern_col[k]);
-    for (auto& a : adj) {
-        std::sort(a.begin(), a.end());
-        a.erase(std::unique(a.begin(), a.end()), a.end());
+    each_entry([&](int32_t r, int32_t c) { if (r != c) ++cptr[c + 1]; });
+    for (int32_t j = 0; j < n; ++j) cptr[j + 1] += cptr[j];
+    std::vector<int32_t> rows_by_col((size_t)cptr[n]);
+    {
+        std::vector<int64_t> fill(cptr.begin(), cptr.end() - 1);
+        each_entry([&](int32_t r, int32_t c) { if (r != c) rows_by_col[(size_t)fill[c]++] = r; });
     }
+    std::vector<std::vector<int32_t>> adj(n);
+    {
+        std::vector<int32_t> stamp(n, -1);
+        for (int32_t j = 0; j < n; ++j)
+            for (int64_t k = cptr[j]; k < cptr[j + 1]; ++k) {
+                const int32_t r = rows_by_col[(size_t)k];
+                if (stamp[r] == j) continue;
+                stamp[r] = j;
+                adj[r].push_back(j);
+                adj[j].push_back(r);
+            }
+    }
+    std::vector<int32_t>().swap(rows_by_col);
+    for (auto& a : adj) std::sort(a.begin(), a.end());
 
     // ---- exact minimum degree ----
     S.n = n;
