@@ -43,12 +43,60 @@
 
 namespace hsde {
 
+// Row stride of the CP x LD buffers: even (2-vector accesses stay aligned),
+// chosen per bucket size to spread a round's accesses over the 32 banks.  A
+// warp's items run along a row and then jump by two rows, so 2 LD mod 32
+// decides the conflicts between rows; the values below minimise the
+// wavefronts of a whole round (A loads and scattered stores, V loads and
+// stores) in a count over every warp's addresses.  Small buckets (several
+// cliques per warp) keep CP + 2.
+constexpr int cone_ld_spread(int cp) {
+    switch (cp) {
+        case 20: return 26;
+        case 24: return 28;
+        case 32: return 44;
+        case 36: return 50;
+        case 40: return 52;
+        case 44: return 54;
+        case 48: return 56;
+        case 56: return 60;
+        case 64: return 76;
+        case 80: return 88;
+        case 96: return 108;
+        case 112: return 120;
+        default: return cp + 2;
+    }
+}
+
+template <typename T>
+constexpr size_t cone_group_bytes(int cp, int ld) {
+    // per group: A0, A1, V0, V1 (CP x LD), rot (cs,sn) K, tan K, lambda CP, red
+    // (one double per warp of the group, whatever T is: 64 elements), and
+    // the list of slots with a positive eigenvalue (CP + 1 ints)
+    return ((4 * (size_t)cp * ld + 2 * (cp / 2) + cp / 2 + cp + 64 + (cp + 2)) * sizeof(T) + 15) / 16 * 16;
+}
+
+// Half the opt-in shared memory: two one-clique CTAs still share an SM.
+constexpr size_t CONE_SMEM_HALF = 232448 / 2;
+
+template <typename T, int CP, int G>
+constexpr int cone_ld() {
+    const int nth = (G > 32) ? G : 128;
+    const size_t base = (size_t)(nth / G) * cone_group_bytes<T>(CP, CP + 2);
+    const size_t spread = (size_t)(nth / G) * cone_group_bytes<T>(CP, cone_ld_spread(CP));
+    // keep CP + 2 where the wider rows would lose the bucket its second
+    // resident CTA or no longer fit
+    if (spread > 232448 || (base <= CONE_SMEM_HALF && spread > CONE_SMEM_HALF)) return CP + 2;
+    return cone_ld_spread(CP);
+}
+
 template <typename T, int CP_, int G_>
 struct ConeCfg {
     static constexpr int CP = CP_;
     static constexpr int G = G_;
     static constexpr int K = CP / 2;
-    static constexpr int LD = CP + 2;                 // even row stride: 2-vector loads stay aligned
+    static constexpr int LD = cone_ld<T, CP_, G_>();
+    static_assert(LD % 2 == 0 && LD >= CP + 2, "even row stride beyond the padded size");
     static constexpr int NTH = (G > 32) ? G : 128;    // threads per CTA
     static constexpr int GPB = NTH / G;               // groups (cliques) per CTA
     static constexpr int NBLK = K * (K + 1) / 2;      // lower 2x2 blocks (row pair >= column pair)
@@ -57,13 +105,9 @@ struct ConeCfg {
     static constexpr int VPL = (NVP + G - 1) / G;     // V items per thread per round
     static_assert(G <= 32 ? (32 % G == 0) : (G % 32 == 0), "group: a power of two <= 32 or whole warps");
     static_assert(BPL <= 32 && VPL <= 32, "per-thread masks are 32 bits");
-    // per group: A0, A1, V0, V1 (CP x LD), rot (cs,sn) K, tan K, lambda CP, red
-    // (one double per warp of the group, whatever T is: 64 elements), and
-    // the list of slots with a positive eigenvalue (CP + 1 ints)
-    static constexpr size_t t_elems = 4 * CP * LD + 2 * K + K + CP + 64 + (CP + 2);   // + positive-slot list
     static_assert((G + 31) / 32 * sizeof(double) <= 64 * sizeof(T), "red holds one double per warp");
     static_assert((4 * CP * LD + 3 * K + CP) % 2 == 0, "red is 8-byte aligned");
-    static constexpr size_t group_bytes = (t_elems * sizeof(T) + 15) / 16 * 16;
+    static constexpr size_t group_bytes = cone_group_bytes<T>(CP, LD);
     static constexpr size_t smem = GPB * group_bytes;
     // resident CTAs the register budget is sized for: many-clique CTAs 8;
     // one clique per CTA 2 where two fit the shared memory (the kernel waits

@@ -730,7 +730,7 @@ __global__ void k_gj_update(double* pool, const int64_t* offs, const int32_t* ms
 // the pool row, which the warp owns.
 // ---------------------------------------------------------------------------
 template <bool SMEM>
-__global__ void k_form_S(DevView V, const int32_t* rows, int32_t nrows, int warps) {
+__global__ void k_form_S(DevView V, const int32_t* rows, int32_t nrows, int warps, int32_t stride) {
     extern __shared__ double srow[];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int32_t r = blockIdx.x * warps + w;
@@ -739,7 +739,9 @@ __global__ void k_form_S(DevView V, const int32_t* rows, int32_t nrows, int warp
     const InstDev& I = V.inst[V.row_inst[i]];
     const int32_t m = I.m, mo = I.m_off;
     double* out = V.sinv + I.sinv_off + (int64_t)(i - mo) * m;
-    double* acc = SMEM ? srow + (size_t)w * m : out;
+    // each warp's row buffer: stride = the largest m of the launch (the
+    // warps of one CTA can serve instances of different m)
+    double* acc = SMEM ? srow + (size_t)w * stride : out;
     for (int32_t j = l; j < m; j += 32) acc[j] = (j == i - mo) ? 1.0 : 0.0;
     __syncwarp();
     for (int32_t k = V.A_ptr[i]; k < V.A_ptr[i + 1]; ++k) {
@@ -880,9 +882,9 @@ void launch_form_S(const DevView& V, const int32_t* rows, int32_t nrows, int32_t
         const int warps = (int)std::min<size_t>(8, FORM_S_SMEM / per_warp);
         const size_t sm = per_warp * warps;
         cudaFuncSetAttribute(k_form_S<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_form_S<true><<<(nrows + warps - 1) / warps, 32 * warps, sm, S_(st)>>>(V, rows, nrows, warps);
+        k_form_S<true><<<(nrows + warps - 1) / warps, 32 * warps, sm, S_(st)>>>(V, rows, nrows, warps, mmax);
     } else {
-        k_form_S<false><<<(nrows + 7) / 8, 256, 0, S_(st)>>>(V, rows, nrows, 8);
+        k_form_S<false><<<(nrows + 7) / 8, 256, 0, S_(st)>>>(V, rows, nrows, 8, mmax);
     }
 }
 
