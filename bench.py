@@ -86,6 +86,8 @@ def sweep_stats(phases):
         out["mean_per_clique"] = round(sw[0] / sw[2], 3)
     out["bucket_max"] = {k: round(a[3] / a[2], 2) for k, a in phases.items()
                          if k.startswith("cone_") and a[2]}
+    # eigensolver variant of each bucket (the setup autotuner's choice)
+    out["bucket_variant"] = {k: ("throughput" if v else "latency") for k, v in phases.get("_variants", {}).items()}
     return out
 
 
@@ -267,7 +269,7 @@ def phase_roofline(phases, sizes_list, nnzA_list, mixed, traffic_tag=None):
     against the FP32 ALU peak (algorithmic 11 c^3 per clique), the affine and
     post phases against HBM (algorithmic bytes of every instance)."""
     peaks, src = load_peaks()
-    avg = {k: (a[0] / a[2], a[1]) for k, a in phases.items() if k not in ("iteration", "_sweeps_mean") and a[2]}
+    avg = {k: (a[0] / a[2], a[1]) for k, a in phases.items() if k != "iteration" and not k.startswith("_") and a[2]}
     dom = max(avg, key=lambda k: avg[k][0])
     dom_ms, dom_units = avg[dom]
     if dom.startswith("cone_"):
@@ -376,6 +378,7 @@ class Runner:
                 sw = phases.setdefault("_sweeps_mean", [0.0, 0, 0, 0])
                 sw[0] += pr["sweeps_mean"]
                 sw[2] += 1
+                phases["_variants"] = dict(pr.get("phase_variant", {}))
         self.barrier()
         return sum(a.elapsed_time(b) for a, b in ev), phases
 

@@ -134,6 +134,17 @@ typedef struct hsde_options {
                              default 1.8; 1 is the literal Eqs. Step1-Step3   */
     double  scale_norm;   /* target norm of the scaled b~ and c~, default 10   */
     double  dual_weight;  /* extra factor of rho over sigma, default 1.5       */
+    int32_t autotune;     /* eigensolver variant of each clique bucket (the
+                             latency variant: about one 2x2 block per thread;
+                             the throughput variant: fewer threads a clique,
+                             more cliques per SM).  Both give bitwise the same
+                             results.  1 (default): time both once per
+                             (precision, bucket size, clique count, SM count)
+                             at setup and keep the faster (cached for the
+                             process); 0: throughput unless the bucket's CTAs
+                             each have an SM to themselves; 2: always latency;
+                             3: always throughput.  A bucket of few large
+                             cliques always runs the latency variant.        */
 } hsde_options;
 
 typedef struct hsde_sizes {
@@ -180,6 +191,10 @@ typedef struct hsde_profile {
                                                    clique of the bucket took
                                                    (it sets the phase's time); 0
                                                    for the other phases       */
+    int32_t phase_variant[HSDE_MAX_PHASES];  /* cone phases: the eigensolver
+                                                variant the bucket runs (0
+                                                latency, 1 throughput; see
+                                                options.autotune)           */
 } hsde_profile;
 
 typedef struct hsde_handle hsde_handle;

@@ -15,8 +15,11 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -415,6 +418,68 @@ void append_at_tiles(const HostPrep& H, int32_t b, int64_t xo, std::vector<int4>
     if (N > e0) close(N);
 }
 
+// ---- eigensolver variant per bucket (the autotuner) ----
+// A bucket of few large cliques (each CTA alone on its SM) runs the latency
+// variant.  Any other bucket with two variants gets the faster one for its
+// clique count on this GPU, timed once per (precision, size, count, SMs) in
+// dry runs (synthetic matrices, two sweeps, no writes) and cached for the
+// process.  Both variants give bitwise the same results, so the choice
+// changes only the time.  options.autotune: 1 time (default), 0 the rule
+// "throughput variant unless alone", 2 always latency, 3 always throughput.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tune_cache;
+
+int time_variant(hsde_handle* h, Bucket& bk, int variant, float& ms) {
+    bk.variant = variant;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    struct Ev { cudaEvent_t a, b; ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); } } ev{e0, e1};
+    constexpr int REPS = 3;
+    int rc = launch_cone(h->V, bk, h->mixed, 2, 1e-6, 0, 0, h->st, 1);   // warm-up
+    CK(cudaEventRecord(e0, h->st));
+    for (int r = 0; r < REPS && rc == HSDE_OK; ++r) rc = launch_cone(h->V, bk, h->mixed, 2, 1e-6, 0, 0, h->st, 1);
+    CK(cudaEventRecord(e1, h->st));
+    if (rc != HSDE_OK) return fail(rc, "eigensolver variant launch");
+    CK(cudaGetLastError());
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    ms /= REPS;
+    return HSDE_OK;
+}
+
+int choose_variants(hsde_handle* h) {
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    for (Bucket& bk : h->buckets) {
+        bk.variant = 0;
+        if (cone_variants(bk.cmax, h->mixed) < 2 || cone_bucket_alone(bk, h->mixed)) continue;
+        const int mode = h->opt.autotune;
+        if (mode == 2) continue;
+        if (mode == 0 || mode == 3) {
+            bk.variant = 1;
+            continue;
+        }
+        const auto key = std::make_tuple((int)h->mixed, (int)bk.cmax, (int)bk.count, nsm);
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) {
+                bk.variant = it->second;
+                continue;
+            }
+        }
+        float t0 = 0.f, t1 = 0.f;
+        int rc;
+        if ((rc = time_variant(h, bk, 0, t0)) != HSDE_OK) return rc;
+        if ((rc = time_variant(h, bk, 1, t1)) != HSDE_OK) return rc;
+        bk.variant = t1 < t0 ? 1 : 0;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = bk.variant;
+    }
+    return HSDE_OK;
+}
+
 int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_handle** out) {
     const double t0 = now_ms();
     if (!out) return fail(HSDE_EINVAL, "out is null");
@@ -428,7 +493,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         opt.jacobi_tol < 0 || opt.warm_start < -1 || opt.warm_start > 1 || opt.warm_refresh < 0 ||
         (opt.scaling != 0 && opt.scaling != 1) || (opt.structured_factor != 0 && opt.structured_factor != 1) || !(opt.alpha > 0.0 && opt.alpha < 2.0) ||
         !(opt.scale_norm > 0.0) || !(opt.dual_weight > 0.0) || !std::isfinite(opt.scale_norm) ||
-        !std::isfinite(opt.dual_weight))
+        !std::isfinite(opt.dual_weight) || opt.autotune < 0 || opt.autotune > 3)
         return fail(HSDE_EINVAL, "invalid options");
 
     auto* h = new hsde_handle();
@@ -842,7 +907,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
             if (lists[t].empty()) continue;
             CK(cudaMemcpyAsync(dl + used, lists[t].data(), sizeof(int32_t) * lists[t].size(),
                                cudaMemcpyHostToDevice, st));
-            h->buckets.push_back(Bucket{caps[t], (int32_t)lists[t].size(), dl + used});
+            h->buckets.push_back(Bucket{caps[t], (int32_t)lists[t].size(), 0, dl + used});
             h->bucket_c3.push_back(c3[t]);
             h->bucket_ids.push_back(lists[t]);
             used += lists[t].size();
@@ -851,6 +916,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     }
     if (cone_prepare(h->mixed) != HSDE_OK || rev_prepare(h->mixed) != HSDE_OK)
         return fail(HSDE_ECUDA, "cudaFuncSetAttribute failed");
+    if ((rc = choose_variants(h)) != HSDE_OK) return rc;
 
     // ---- capture one iteration into a graph ----
     h->kernels_per_iter = count_kernels(h);
@@ -918,6 +984,7 @@ void hsde_default_options(hsde_options* o) {
     o->alpha = 1.8;
     o->scale_norm = 10.0;
     o->dual_weight = 1.5;
+    o->autotune = 1;
 }
 
 const char* hsde_last_error(void) { return g_err.c_str(); }
@@ -1273,6 +1340,7 @@ int hsde_get_profile(hsde_handle* h, hsde_profile* out) {
         int32_t bm = 0;
         for (int32_t k : h->bucket_ids[i]) bm = std::max(bm, sw[k]);
         out->phase_sweeps_max[1 + i] = bm;
+        out->phase_variant[1 + i] = h->buckets[i].variant;
     }
     return HSDE_OK;
 }

@@ -139,25 +139,38 @@ __device__ __forceinline__ void gsync(int gid) {
     }
 }
 
-// Sum over the group; every thread of the group gets the same value, summed
-// in a fixed order.
-template <int G, typename T>
-__device__ __forceinline__ T gsum(T v, T* red, int gid) {
+// Lanes of the fixed-order sums: a bucket's variants (different group sizes
+// G) must give bitwise the same results, so the reductions whose rounding
+// reaches the output (the convergence test, the clique's residual partials)
+// run in an order set by the bucket size alone.
+template <int CP>
+struct FixedLanes {
+    static constexpr int value = CP >= 20 ? 32 : 4;
+};
+
+// Sum of vals[0..n) (shared memory) in an order independent of G: lane
+// l < RW adds vals[l], vals[l + RW], ... in turn, then the RW lanes combine
+// by a butterfly.  Every thread of the group gets the result.  RW <= G.
+template <int G, int RW, typename S>
+__device__ __forceinline__ S fixed_sum(const S* vals, int n, S* red, int gid) {
+    static_assert(RW <= 32 && (RW & (RW - 1)) == 0, "RW: a power of two <= 32");
+    static_assert(G >= RW, "the group has the RW lanes");
+    const int lane = threadIdx.x % G;
+    const int base = (G >= 32) ? 0 : ((threadIdx.x & 31) & ~(G - 1));
+    S v = S(0);
+    if (lane < RW) {
+        for (int i = lane; i < n; i += RW) v += vals[i];
+        const unsigned m = (RW == 32) ? 0xffffffffu : (((1u << RW) - 1u) << base);
+#pragma unroll
+        for (int o = RW / 2; o > 0; o >>= 1) v += __shfl_xor_sync(m, v, o);
+    }
     if constexpr (G <= 32) {
-        const unsigned mask = gmask<G>();
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
-        return v;
+        return __shfl_sync(gmask<G>(), v, base);
     } else {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        const int w = (threadIdx.x % G) >> 5;
         gsync<G>(gid);
-        if ((threadIdx.x & 31) == 0) red[w] = v;
+        if (lane == 0) red[0] = v;
         gsync<G>(gid);
-        T t = 0;
-#pragma unroll
-        for (int i = 0; i < G / 32; ++i) t += red[i];
+        const S t = red[0];
         gsync<G>(gid);
         return t;
     }
@@ -351,11 +364,32 @@ __device__ __forceinline__ int packed_column(int e, int c) {
     return b;
 }
 
+// Entry (i, j), i >= j, of the synthetic symmetric matrix of clique k that
+// the autotuner's dry runs diagonalise: a hash of (k, i, j) mapped to
+// [-1, 1], the diagonal shifted by i / c so that the spectrum is spread.
+template <typename T>
+__device__ __forceinline__ T dry_entry(int k, int i, int j) {
+    uint32_t h = (uint32_t)k * 0x9E3779B1u ^ (uint32_t)(i * 0x85EBCA77u) ^ (uint32_t)(j * 0xC2B2AE3Du);
+    h ^= h >> 16;
+    h *= 0x7FEB352Du;
+    h ^= h >> 15;
+    h *= 0x846CA68Bu;
+    h ^= h >> 16;
+    const T u = T((double)(h >> 8) * (2.0 / 16777216.0) - 1.0);
+    return i == j ? u + T(i) * T(0.05) : u;
+}
+
 // MB: resident CTAs the registers are sized for (ConeCfg::MINB, or 1 for a
-// bucket whose CTAs each have an SM to themselves).
-template <typename T, int CP, int G, int MB>
+// bucket whose CTAs each have an SM to themselves); ST: one-clique CTAs may
+// keep the gathered values in registers until the rebuild (the latency
+// variants) instead of re-reading them (the throughput variants, whose
+// registers go to more resident CTAs).  dry != 0 (autotuning): a
+// deterministic synthetic matrix instead of the gather, a cold start,
+// exactly max_sweeps sweeps, and no global writes.
+template <typename T, int CP, int G, int MB, bool ST>
 __global__ void __launch_bounds__(ConeCfg<T, CP, G>::NTH, MB)
-k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T tol2, int warm, int refresh) {
+k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T tol2, int warm, int refresh,
+       int dry) {
     using Cfg = ConeCfg<T, CP, G>;
     using V2 = typename Vec2<T>::type;
     constexpr int LD = Cfg::LD, K = Cfg::K;
@@ -363,7 +397,8 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
     // One clique per CTA: the gathered values stay in registers until the
     // rebuild.  Groups of <= 32 lanes (many cliques per CTA) re-read them
     // instead, keeping registers, and so resident CTAs, as they were.
-    constexpr bool STASH = G > 32;
+    constexpr bool STASH = ST && G > 32;
+    constexpr int RW = FixedLanes<CP>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int gid = threadIdx.x / G, lane = threadIdx.x % G;
     const int li = blockIdx.x * Cfg::GPB + gid;
@@ -391,7 +426,7 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
     const double eta = I.eta;
     const double al = V.alpha;
     T* Vst = V.vstore ? reinterpret_cast<T*>(V.vstore) + V.vs_off[k] : nullptr;
-    const bool use_warm = warm && Vst != nullptr && !I.vcold;
+    const bool use_warm = !dry && warm && Vst != nullptr && !I.vcold;
     // every refresh-th iteration the stored basis, whose orthogonality
     // drifts by rounding from one iteration to the next, gets one
     // Newton-Schulz step V <- V (3I - V^T V) / 2 before use
@@ -457,8 +492,9 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
             avs[q] = av;
             vns[q] = (T)vn;
             const int arow = apos[q] / LD, b = apos[q] - (apos[q] / LD) * LD;
-            A0[apos[q]] = (T)av;
-            A0[b * LD + arow] = (T)av;
+            const T a = dry ? dry_entry<T>(k, arow, b) : (T)av;
+            A0[apos[q]] = a;
+            A0[b * LD + arow] = a;
         }
     } else {
         gsync<G>(gid);   // A0 zeroed
@@ -469,8 +505,9 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
             const double gx = V.xw[gi] - eta * V.xp[gi];
             double av, vn, hx;
             cone_inputs((double)s[off + e], (double)z[off + e], (double)v[off + e], gx, al, V.x, gi, av, vn, hx);
-            A0[arow * LD + b] = (T)av;
-            A0[b * LD + arow] = (T)av;
+            const T a = dry ? dry_entry<T>(k, arow, b) : (T)av;
+            A0[arow * LD + b] = a;
+            A0[b * LD + arow] = a;
         }
     }
     gsync<G>(gid);
@@ -579,25 +616,30 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
     bool converged = false;
     for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
         sweeps_done = sweep;
-        T offd = 0, dg = 0;
-        for (int idx = lane; idx < CP * CP; idx += G) {
-            const int i = idx / CP, j = idx - (idx / CP) * CP;
-            if (i < j) continue;
-            const T a = A[i * LD + j];
-            if (i == j) dg += a * a;
-            else offd += T(2) * a * a;
+        // per-row sums (row r: 2 sum_{j<r} a_rj^2 and a_rr^2) into the free
+        // buffer An, then fixed-order sums over the rows
+        for (int r = lane; r < CP; r += G) {
+            T o = T(0);
+            for (int j = 0; j < r; ++j) {
+                const T a = A[r * LD + j];
+                o += a * a;
+            }
+            const T d = A[r * LD + r];
+            An[r] = T(2) * o;
+            An[CP + r] = d * d;
         }
-        offd = gsum<G>(offd, red, gid);
-        const T tot = gsum<G>(dg, red, gid) + offd;
+        gsync<G>(gid);
+        const T offd = fixed_sum<G, RW>(An, CP, red, gid);
+        const T tot = fixed_sum<G, RW>(An + CP, CP, red, gid) + offd;
         converged = offd <= tol2 * tot;
-        if (converged || sweep == max_sweeps) break;
+        if ((converged && !dry) || sweep == max_sweeps) break;
         for (int r = 0; r < CP - 1; ++r) {
             jacobi_round<Cfg>(plan, A, An, Vc, Vn, rot, tan_, lane, gid);
             T* t1 = A; A = An; An = t1;
             T* t2 = Vc; Vc = Vn; Vn = t2;
         }
     }
-    if (V.tape_v) {
+    if (V.tape_v && !dry) {
         // reverse-mode tape: eigenvectors (original index x slot) and raw eigenvalues
         T* tv = reinterpret_cast<T*>(V.tape_v) + V.tv_off[k];
         for (int idx = lane; idx < CP * CP; idx += G) {
@@ -607,7 +649,7 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
         for (int i = lane; i < CP; i += G) tv[CP * CP + i] = A[i * LD + i];
     }
     for (int i = lane; i < CP; i += G) lam[i] = fmax(A[i * LD + i], T(0));
-    if (Vst != nullptr && warm) {
+    if (Vst != nullptr && warm && !dry) {
         for (int idx = lane; idx < CP * CP; idx += G) {
             const int i = idx / CP, j = idx - (idx / CP) * CP;
             Vst[idx] = Vc[i * LD + j];
@@ -668,20 +710,27 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
     }
     gsync<G>(gid);
 
-    double res = 0.0, sres = 0.0;
+    // each lower entry's contributions to ||H_k x - s_k||^2 and ||s_k||^2 go
+    // to the free buffers A and Vn (nlow doubles each fit: LD > c) and are
+    // summed in a fixed order
+    double* cres = reinterpret_cast<double*>(A);
+    double* csres = reinterpret_cast<double*>(Vn);
     if constexpr (STASH) {
 #pragma unroll
         for (int q = 0; q < EPT; ++q) {
             if (apos[q] < 0) continue;
-            const int64_t j = off + lane + q * G;
+            const int e = lane + q * G;
+            const int64_t j = off + e;
             const double sn = (double)An[apos[q]];
-            s[j] = (T)sn;
-            z[j] = (T)(sn - avs[q]);
-            v[j] = vns[q];
+            if (!dry) {
+                s[j] = (T)sn;
+                z[j] = (T)(sn - avs[q]);
+                v[j] = vns[q];
+            }
             const double d = gxs[q] - sn;
             const double w = (diag_bits >> q) & 1u ? 1.0 : 2.0;
-            res += w * d * d;
-            sres += w * sn * sn;
+            cres[e] = w * d * d;
+            csres[e] = w * sn * sn;
         }
     } else {
         for (int e = lane; e < nlow; e += G) {
@@ -693,18 +742,21 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
             const double gx = V.xw[gi] - eta * V.xp[gi];
             double av, vn, hx;
             cone_inputs((double)s[j], (double)z[j], (double)v[j], gx, al, V.x, gi, av, vn, hx);
-            s[j] = (T)sn;
-            z[j] = (T)(sn - av);
-            v[j] = (T)vn;
+            if (!dry) {
+                s[j] = (T)sn;
+                z[j] = (T)(sn - av);
+                v[j] = (T)vn;
+            }
             const double d = hx - sn;
             const double w = arow == b ? 1.0 : 2.0;
-            res += w * d * d;
-            sres += w * sn * sn;
+            cres[e] = w * d * d;
+            csres[e] = w * sn * sn;
         }
     }
-    res = gsum<G>(res, reinterpret_cast<double*>(red), gid);
-    sres = gsum<G>(sres, reinterpret_cast<double*>(red), gid);
-    if (lane == 0) {
+    gsync<G>(gid);
+    const double res = fixed_sum<G, RW>(cres, nlow, reinterpret_cast<double*>(red), gid);
+    const double sres = fixed_sum<G, RW>(csres, nlow, reinterpret_cast<double*>(red), gid);
+    if (lane == 0 && !dry) {
         V.cl_part[2 * k] = res;
         V.cl_part[2 * k + 1] = sres;
         V.cl_sweeps[k] = sweeps_done;
@@ -715,17 +767,24 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
 }
 
 // ---------------------------------------------------------------------------
-// buckets: padded size CP and threads per clique G
+// buckets: padded size CP; threads per clique G of the latency variant; GT of
+// the throughput variant (0: none)
 // ---------------------------------------------------------------------------
 // (padding a clique of c to CP costs about (CP/c)^3 of the work, so the
-// sizes are spaced by 4 above 16; G gives about one 2x2 block per thread and
-// round: K(K+1)/2 blocks, K = CP/2)
-// sizes above 64 hold one clique per CTA of up to 1024 threads; a size
-// exists for a precision only if its CTA fits the opt-in shared memory
-// (FP32 up to 112, FP64 up to 80)
-#define HSDE_CONE_BUCKETS(X)                                                                     \
-    X(4, 4) X(8, 8) X(12, 16) X(16, 32) X(20, 64) X(24, 96) X(28, 128) X(32, 160) X(36, 192)   \
-    X(40, 224) X(44, 256) X(48, 320) X(56, 416) X(64, 544) X(80, 832) X(96, 1024) X(112, 1024)
+// sizes are spaced by 4 above 16.)  The latency variant gives about one 2x2
+// block per thread and round (K(K+1)/2 blocks, K = CP/2) and keeps the
+// gathered values in registers: the fastest solve of one clique.  The
+// throughput variant gives about two blocks per thread, re-reads the
+// gathered values, and is compiled for as many resident CTAs as the shared
+// memory allows with ~72 registers a thread: more cliques per SM.  Both give
+// bitwise the same results (the same per-element arithmetic, and sums in a
+// fixed order).  Sizes above 64 hold one clique per CTA of up to 1024
+// threads; a size exists for a precision only if its CTA fits the opt-in
+// shared memory (FP32 up to 112, FP64 up to 80).
+#define HSDE_CONE_BUCKETS(X)                                                                          \
+    X(4, 4, 0) X(8, 8, 0) X(12, 16, 0) X(16, 32, 0) X(20, 64, 32) X(24, 96, 64) X(28, 128, 64)        \
+    X(32, 160, 96) X(36, 192, 96) X(40, 224, 128) X(44, 256, 128) X(48, 320, 160) X(56, 416, 224)     \
+    X(64, 544, 288) X(80, 832, 416) X(96, 1024, 0) X(112, 1024, 0)
 
 // Opt-in shared memory per CTA on this architecture (227 KB).
 constexpr size_t CONE_SMEM_MAX = 232448;
@@ -735,11 +794,29 @@ constexpr bool cone_fits() {
     return ConeCfg<T, CP, G>::smem <= CONE_SMEM_MAX;
 }
 
+// Resident CTAs of a throughput variant: as many as the shared memory holds,
+// at most 896 threads an SM (about 72 registers a thread).
+template <typename T, int CP, int G>
+constexpr int thr_minb() {
+    using Cfg = ConeCfg<T, CP, G>;
+    if (Cfg::GPB > 1) return 8;
+    const int by_smem = (int)(CONE_SMEM_MAX / Cfg::smem);
+    const int by_thr = 896 / Cfg::NTH;
+    const int m = by_smem < by_thr ? by_smem : by_thr;
+    return m < 1 ? 1 : (m > 16 ? 16 : m);
+}
+
 // Device limits read by cone_prepare: opt-in shared memory per CTA, SMs.
 static int g_smem_optin = 0;
 static int g_num_sms = 0;
 
-template <typename T, int CP, int G>
+template <typename T, int CP, int G, int MB, bool ST>
+static cudaError_t allow_smem(int bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(k_cone<T, CP, G, MB, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <typename T, int CP, int G, int GT>
 static int prepare_one() {
     if constexpr (!cone_fits<T, CP, G>()) {
         return HSDE_OK;                                          // never used in this precision
@@ -748,14 +825,16 @@ static int prepare_one() {
         // one clique per CTA: allowed the whole opt-in shared memory, which a
         // launch asks for when the bucket has few cliques (a CTA alone on its SM)
         const int want = Cfg::GPB == 1 ? std::max<int>(g_smem_optin, (int)Cfg::smem) : (int)Cfg::smem;
-        if (want > 48 * 1024 &&
-            cudaFuncSetAttribute(k_cone<T, CP, G, Cfg::MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, want) !=
-                cudaSuccess)
-            return HSDE_ECUDA;
+        if (allow_smem<T, CP, G, Cfg::MINB, true>(want) != cudaSuccess) return HSDE_ECUDA;
         if constexpr (Cfg::GPB == 1 && CP >= 32 && Cfg::MINB != 1) {
-            if (cudaFuncSetAttribute(k_cone<T, CP, G, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, want) !=
-                cudaSuccess)
-                return HSDE_ECUDA;
+            if (allow_smem<T, CP, G, 1, true>(want) != cudaSuccess) return HSDE_ECUDA;
+        }
+        if constexpr (GT > 0) {
+            if constexpr (cone_fits<T, CP, GT>()) {
+                if (allow_smem<T, CP, GT, thr_minb<T, CP, GT>(), false>((int)ConeCfg<T, CP, GT>::smem) !=
+                    cudaSuccess)
+                    return HSDE_ECUDA;
+            }
         }
         return HSDE_OK;
     }
@@ -775,32 +854,43 @@ static bool alone_one(const Bucket& bk) {
     }
 }
 
-template <typename T, int CP, int G>
+template <typename T, int CP, int G, int GT>
 static int launch_one(const DevView& V, const Bucket& bk, int max_sweeps, double tol, int warm, int refresh,
-                      cudaStream_t st) {
+                      int dry, cudaStream_t st) {
     if constexpr (!cone_fits<T, CP, G>()) {
         return HSDE_ERANGE;
     } else {
         using Cfg = ConeCfg<T, CP, G>;
-        const int grid = (bk.count + Cfg::GPB - 1) / Cfg::GPB;
         const T tol2 = (T)(tol * tol);
+        if constexpr (GT > 0) {
+            if constexpr (cone_fits<T, CP, GT>()) {
+                if (bk.variant == 1) {
+                    using CT = ConeCfg<T, CP, GT>;
+                    const int grid = (bk.count + CT::GPB - 1) / CT::GPB;
+                    k_cone<T, CP, GT, thr_minb<T, CP, GT>(), false><<<grid, CT::NTH, CT::smem, st>>>(
+                        V, bk.list, bk.count, max_sweeps, tol2, warm, refresh, dry);
+                    return HSDE_OK;
+                }
+            }
+        }
+        const int grid = (bk.count + Cfg::GPB - 1) / Cfg::GPB;
         if constexpr (Cfg::GPB == 1 && CP >= 32 && Cfg::MINB != 1) {
             // a CTA alone on its SM: the variant with the full register budget
             if (alone_one<T, CP, G>(bk)) {
-                k_cone<T, CP, G, 1><<<grid, Cfg::NTH, (size_t)g_smem_optin, st>>>(V, bk.list, bk.count, max_sweeps,
-                                                                                 tol2, warm, refresh);
+                k_cone<T, CP, G, 1, true><<<grid, Cfg::NTH, (size_t)g_smem_optin, st>>>(
+                    V, bk.list, bk.count, max_sweeps, tol2, warm, refresh, dry);
                 return HSDE_OK;
             }
         }
         const size_t smem = alone_one<T, CP, G>(bk) ? (size_t)g_smem_optin : Cfg::smem;
-        k_cone<T, CP, G, Cfg::MINB><<<grid, Cfg::NTH, smem, st>>>(V, bk.list, bk.count, max_sweeps, tol2, warm,
-                                                                    refresh);
+        k_cone<T, CP, G, Cfg::MINB, true><<<grid, Cfg::NTH, smem, st>>>(V, bk.list, bk.count, max_sweeps, tol2,
+                                                                         warm, refresh, dry);
         return HSDE_OK;
     }
 }
 
 int cone_bucket_of(int c, bool mixed) {
-#define X(cp, g) \
+#define X(cp, g, gt) \
     if (c <= cp && (mixed ? cone_fits<float, cp, g>() : cone_fits<double, cp, g>())) return cp;
     HSDE_CONE_BUCKETS(X)
 #undef X
@@ -809,7 +899,7 @@ int cone_bucket_of(int c, bool mixed) {
 
 int cone_max_clique(bool mixed) {
     int mx = 0;
-#define X(cp, g) \
+#define X(cp, g, gt) \
     if (mixed ? cone_fits<float, cp, g>() : cone_fits<double, cp, g>()) mx = cp;
     HSDE_CONE_BUCKETS(X)
 #undef X
@@ -818,10 +908,20 @@ int cone_max_clique(bool mixed) {
 
 void cone_bucket_sizes(std::vector<int>& out, bool mixed) {
     out.clear();
-#define X(cp, g) \
+#define X(cp, g, gt) \
     if (mixed ? cone_fits<float, cp, g>() : cone_fits<double, cp, g>()) out.push_back(cp);
     HSDE_CONE_BUCKETS(X)
 #undef X
+}
+
+int cone_variants(int cmax, bool mixed) {
+#define X(cp, g, gt)                                                                                  \
+    if (cmax == cp)                                                                                   \
+        return (gt > 0 && (mixed ? cone_fits<float, cp, (gt > 0 ? gt : g)>()                          \
+                                 : cone_fits<double, cp, (gt > 0 ? gt : g)>())) ? 2 : 1;
+    HSDE_CONE_BUCKETS(X)
+#undef X
+    return 0;
 }
 
 int cone_vstore_elems(int c, bool mixed) {
@@ -836,14 +936,15 @@ int cone_prepare(bool mixed) {
         cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return HSDE_ECUDA;
     int rc = HSDE_OK;
-#define X(cp, g) rc |= mixed ? prepare_one<float, cp, g>() : prepare_one<double, cp, g>();
+#define X(cp, g, gt) \
+    rc |= mixed ? prepare_one<float, cp, g, gt>() : prepare_one<double, cp, g, gt>();
     HSDE_CONE_BUCKETS(X)
 #undef X
     return rc == HSDE_OK ? HSDE_OK : HSDE_ECUDA;
 }
 
 int cone_smem_bytes(int cmax, bool mixed) {
-#define X(cp, g) \
+#define X(cp, g, gt) \
     if (cmax == cp) return mixed ? (int)ConeCfg<float, cp, g>::smem : (int)ConeCfg<double, cp, g>::smem;
     HSDE_CONE_BUCKETS(X)
 #undef X
@@ -851,7 +952,7 @@ int cone_smem_bytes(int cmax, bool mixed) {
 }
 
 bool cone_bucket_alone(const Bucket& bk, bool mixed) {
-#define X(cp, g) \
+#define X(cp, g, gt) \
     if (bk.cmax == cp) return mixed ? alone_one<float, cp, g>(bk) : alone_one<double, cp, g>(bk);
     HSDE_CONE_BUCKETS(X)
 #undef X
@@ -859,13 +960,13 @@ bool cone_bucket_alone(const Bucket& bk, bool mixed) {
 }
 
 int launch_cone(const DevView& V, const Bucket& bk, bool mixed, int max_sweeps, double tol, int warm, int refresh,
-                void* stp) {
+                void* stp, int dry) {
     if (bk.count == 0) return HSDE_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stp);
-#define X(cp, g)                                                                                \
-    if (bk.cmax == cp) {                                                                        \
-        return mixed ? launch_one<float, cp, g>(V, bk, max_sweeps, tol, warm, refresh, st)     \
-                     : launch_one<double, cp, g>(V, bk, max_sweeps, tol, warm, refresh, st);   \
+#define X(cp, g, gt)                                                                                   \
+    if (bk.cmax == cp) {                                                                               \
+        return mixed ? launch_one<float, cp, g, gt>(V, bk, max_sweeps, tol, warm, refresh, dry, st)   \
+                     : launch_one<double, cp, g, gt>(V, bk, max_sweeps, tol, warm, refresh, dry, st); \
     }
     HSDE_CONE_BUCKETS(X)
 #undef X

@@ -39,7 +39,7 @@ class hsde_options(C.Structure):
                 ("jacobi_max_sweeps", C.c_int32), ("use_graph", C.c_int32), ("jacobi_tol", C.c_double),
                 ("profile", C.c_int32), ("warm_start", C.c_int32), ("warm_refresh", C.c_int32),
                 ("scaling", C.c_int32), ("structured_factor", C.c_int32), ("alpha", C.c_double), ("scale_norm", C.c_double),
-                ("dual_weight", C.c_double)]
+                ("dual_weight", C.c_double), ("autotune", C.c_int32)]
 
 
 class hsde_sizes(C.Structure):
@@ -64,7 +64,7 @@ class hsde_profile(C.Structure):
                 ("phase_ms", C.c_double * MAX_PHASES), ("phase_name", (C.c_char * 24) * MAX_PHASES),
                 ("phase_units", C.c_int64 * MAX_PHASES), ("sweeps_mean", C.c_double),
                 ("sweeps_max", C.c_int32), ("_pad", C.c_int32),
-                ("phase_sweeps_max", C.c_int32 * MAX_PHASES)]
+                ("phase_sweeps_max", C.c_int32 * MAX_PHASES), ("phase_variant", C.c_int32 * MAX_PHASES)]
 
 
 # Every function declared in include/hsde.h: name -> (restype, argtypes)
@@ -286,8 +286,11 @@ class Handle:
                   for i in range(pr.nphases)}
         phase_sweeps = {pr.phase_name[i].value.decode(): int(pr.phase_sweeps_max[i])
                         for i in range(pr.nphases) if pr.phase_name[i].value.startswith(b"cone_")}
+        phase_variant = {pr.phase_name[i].value.decode(): int(pr.phase_variant[i])
+                         for i in range(pr.nphases) if pr.phase_name[i].value.startswith(b"cone_")}
         return dict(kernels_per_iteration=pr.kernels_per_iteration, phases=phases,
-                    sweeps_mean=pr.sweeps_mean, sweeps_max=pr.sweeps_max, phase_sweeps_max=phase_sweeps)
+                    sweeps_mean=pr.sweeps_mean, sweeps_max=pr.sweeps_max, phase_sweeps_max=phase_sweeps,
+                    phase_variant=phase_variant)
 
     def hsde_set_data(self, i: int, c, b):
         """c, b: NumPy arrays, or ints holding device addresses (both the same kind)."""

@@ -397,3 +397,22 @@ def test_large_cliques_one_step_from_random_state(hs, prec, c):
     with pytest.raises(hs.HSDEError) as ei:
         hs.Handle(q, precision=prec)
     assert ei.value.code == hs.HSDE_ERANGE
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_eigensolver_variants_give_bitwise_equal_iterates(hs, prec):
+    """Every bucket with two eigensolver variants (options.autotune 2: latency,
+    3: throughput) gives bitwise the same iterates: the per-element
+    arithmetic is the same and the sums run in an order set by the bucket
+    size.  So the setup autotuner's timing-based choice changes no result."""
+    probs = [synth.block_arrow_sweep(100, 25), synth.maxcut_grid(12, 30, np.random.default_rng(2))]
+    for p in probs:
+        states, variants = [], []
+        for mode in (2, 3):
+            with hs.Handle(p, precision=prec, autotune=mode, profile=1) as H:
+                H.hsde_iterate(25)
+                states.append(H.hsde_get_state(0))
+                variants.append(H.hsde_get_profile()["phase_variant"])
+        assert set(variants[0].values()) == {0}
+        assert 1 in variants[1].values()        # some bucket ran the other variant
+        assert np.array_equal(states[0], states[1]), p.name
