@@ -395,8 +395,9 @@ int upload(void* dst, const std::vector<T>& v, cudaStream_t st) {
 // entries) with at most TILE_N rows and AT_TILE_NNZ nonzeros, so that every
 // CTA gets about the same number of nonzeros whatever the row lengths.  Each
 // row of a tile is reduced by a group of lanes, the power of two (1 ... 32)
-// nearest above the tile's mean row length; a row longer than AT_TILE_NNZ is
-// a tile alone, reduced by the whole CTA (lanes = TILE_N).
+// that gives each lane at most AT_LANE_NNZ of the tile's mean row; a row
+// longer than AT_TILE_NNZ is a tile alone, reduced by the whole CTA
+// (lanes = TILE_N).
 void append_at_tiles(const HostPrep& H, int32_t b, int64_t xo, std::vector<int4>& out) {
     const int64_t N = H.S.N();
     int64_t e0 = 0, nnz = 0;
@@ -405,7 +406,7 @@ void append_at_tiles(const HostPrep& H, int32_t b, int64_t xo, std::vector<int4>
         int lanes = 1;
         if (rows == 1 && nnz > AT_TILE_NNZ) lanes = TILE_N;
         else
-            while (lanes < 32 && lanes * rows < nnz) lanes *= 2;
+            while (lanes < 32 && (int64_t)lanes * AT_LANE_NNZ * rows < nnz) lanes *= 2;
         out.push_back(make_int4(b, (int)(xo + e0), (int)(xo + e1), lanes));
         e0 = e1;
         nnz = 0;

@@ -88,6 +88,8 @@ constexpr int TILE_N = 256;
 constexpr int LONG_COPIES = 32;
 // Nonzeros of A^T per A^T tile (whole rows; a longer row is a tile alone).
 constexpr int AT_TILE_NNZ = 4096;
+// Nonzeros of one A^T row per lane of its reducing group (k_bwd_eta).
+constexpr int AT_LANE_NNZ = 12;
 
 // Device view of the whole batch (plain pointers into one arena).
 struct DevView {

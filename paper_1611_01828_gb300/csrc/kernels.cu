@@ -35,7 +35,8 @@ namespace hsde {
 static constexpr int NT = 256;   // threads per CTA for N-space tiles and m rows
 static_assert(TILE_N == NT, "one pattern entry per thread in the N-space kernels");
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename S>
+__device__ __forceinline__ S warp_sum(S v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -110,15 +111,15 @@ __device__ __forceinline__ double copy_szv(const DevView& V, int64_t p) {
 // summed by one warp in a fixed order (strided lanes, then a butterfly), so
 // each double is added about 12 times per warp instead of 5 times by every
 // thread.  buf holds NV * NT doubles; the result is valid in every thread.
-template <int NV>
-__device__ __forceinline__ void block_sum_t(double (&v)[NV], double* buf) {
+template <int NV, typename S>
+__device__ __forceinline__ void block_sum_t(S (&v)[NV], S* buf) {
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < NV; ++i) buf[i * NT + threadIdx.x] = v[i];
     __syncthreads();
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     for (int i = w; i < NV; i += NT / 32) {
-        double s = 0.0;
+        S s = S(0);
 #pragma unroll
         for (int k = 0; k < NT / 32; ++k) s += buf[i * NT + l + 32 * k];
         s = warp_sum(s);
@@ -335,67 +336,47 @@ __global__ void __launch_bounds__(NT) k_bwd_eta(DevView V) {
             part = (V.diag[e] ? 1.0 : 2.0) * V.c[e] * xv;
         }
     } else {
-        // The tile's products A_ji y_w,i (at most AT_TILE_NNZ, one contiguous
-        // range) are formed by the whole CTA with independent coalesced loads
-        // and kept in shared memory.  Groups of G lanes (a power of two <= 32,
-        // aligned in the warp) then reduce one row each at a time (the loop
-        // bound is uniform over the CTA, so every lane of a warp reaches each
-        // shuffle), and one thread per row finishes it.  Everything a row
-        // needs besides its sum is loaded up front.
-        __shared__ double prod[AT_TILE_NNZ];
-        __shared__ double rowacc[NT];
-        __shared__ int rowptr[NT + 1];
+        // Groups of G lanes (a power of two <= 32, aligned in the warp) take
+        // one row at a time: each lane accumulates its strided share of the
+        // row with FMAs (four independent loads and gathers in flight), then
+        // the group combines by a butterfly and its first lane finishes the
+        // row.  One FP64 operation per nonzero plus G log2 G per row: on this
+        // GPU the FP64 pipe, not DRAM, sets the time of this kernel, so the
+        // tiles give each lane about a dozen nonzeros of a row (the butterfly
+        // of a 32-lane group per row cost more than the products).  The loop
+        // bound is uniform over the CTA, so every lane reaches each shuffle.
         const int nrow = t.z - t.y;      // <= TILE_N == NT
-        const int er = t.y + threadIdx.x;
-        const bool hasr = (int)threadIdx.x < nrow;
-        double fr = 0.0, idr = 0.0, cr = 0.0;
-        bool dr = false;
-        if (hasr) {
-            fr = V.f[er];
-            idr = V.inv_delta[er];
-            cr = V.c[er];
-            dr = V.diag[er] != 0;
-        }
-        for (int r = threadIdx.x; r <= nrow; r += NT) rowptr[r] = V.At_ptr[t.y + r];
-        const int jt0 = V.At_ptr[t.y], jt1 = V.At_ptr[t.z];
-        // eight nonzeros per thread at a time: their index/value loads, then
-        // their gathers, are issued together
-        constexpr int U = 8;
-        for (int jb = jt0 + threadIdx.x; jb < jt1; jb += U * NT) {
-            int col[U];
-            double val[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int j = jb + u * NT;
-                col[u] = j < jt1 ? V.At_col[j] : 0;
-                val[u] = j < jt1 ? V.At_val[j] : 0.0;
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int j = jb + u * NT;
-                if (j < jt1) prod[j - jt0] = val[u] * V.yw[col[u]];
-            }
-        }
-        __syncthreads();
         const int grp = threadIdx.x / G, lane = threadIdx.x & (G - 1), ngrp = NT / G;
         for (int base = 0; base < nrow; base += ngrp) {
             const int r = base + grp;
             const bool valid = r < nrow;
+            const int e = t.y + r;
             double acc = 0.0;
             if (valid) {
-                const int j1 = rowptr[r + 1] - jt0;
-                for (int j = rowptr[r] - jt0 + lane; j < j1; j += G) acc += prod[j];
+                const int j0 = V.At_ptr[e], j1 = V.At_ptr[e + 1];
+                int j = j0 + lane;
+                double a0 = 0.0, a1 = 0.0;
+                for (; j + 3 * G < j1; j += 4 * G) {
+                    const int c0 = V.At_col[j], c1 = V.At_col[j + G], c2 = V.At_col[j + 2 * G],
+                              c3 = V.At_col[j + 3 * G];
+                    const double v0 = V.At_val[j], v1 = V.At_val[j + G], v2 = V.At_val[j + 2 * G],
+                                 v3 = V.At_val[j + 3 * G];
+                    const double y0 = V.yw[c0], y1 = V.yw[c1], y2 = V.yw[c2], y3 = V.yw[c3];
+                    a0 = fma(v0, y0, a0);
+                    a1 = fma(v1, y1, a1);
+                    a0 = fma(v2, y2, a0);
+                    a1 = fma(v3, y3, a1);
+                }
+                for (; j < j1; j += G) a0 = fma(V.At_val[j], V.yw[V.At_col[j]], a0);
+                acc = a0 + a1;
             }
             for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (valid && lane == 0) rowacc[r] = acc;
-        }
-        __syncthreads();
-        if (hasr) {
-            const double acc = rowacc[threadIdx.x];
-            const double xv = fr + idr * acc;
-            V.xw[er] = xv;
-            V.atyw[er] = acc;
-            part = (dr ? 1.0 : 2.0) * cr * xv;
+            if (valid && lane == 0) {
+                const double xv = V.f[e] + V.inv_delta[e] * acc;
+                V.xw[e] = xv;
+                V.atyw[e] = acc;
+                part += (V.diag[e] ? 1.0 : 2.0) * V.c[e] * xv;
+            }
         }
     }
     part = block_sum(part, sh);
@@ -533,9 +514,11 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
     //   A x_p = -b - y_p  (the same identity on the setup solve),
     // so A x_hat = A x_w - eta A x_p from values this step already has.
     double b1 = 0.0, b2 = 0.0, b3 = 0.0;
+    bool has_rows;
     {
         const int nt = I.tile_end - I.tile_begin, ti = blockIdx.x - I.tile_begin;
         const int i0 = (int)((int64_t)I.m * ti / nt), i1 = (int)((int64_t)I.m * (ti + 1) / nt);
+        has_rows = i1 > i0;
         const double otp = I.ot_prev;
         for (int i = i0 + threadIdx.x; i < i1; i += NT) {
             const int row = I.m_off + i;
@@ -563,12 +546,21 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
         }
     }
     if (check) {
-        double v9[9] = {a1, a2, a3, b1, b2, b3, (double)a4, (double)a5, (double)a6};
-        block_sum_t<9>(v9, stage);
+        // FP64 pipe time is what this kernel spends: the three N-space sums
+        // in FP64, the cancellation sums (compared with 1e-2 only) in FP32,
+        // and the constraint-space sums only in tiles that hold constraints
+        double v3[3] = {a1, a2, a3};
+        block_sum_t<3>(v3, stage);
+        float f3[3] = {a4, a5, a6};
+        block_sum_t<3>(f3, reinterpret_cast<float*>(stage));
+        double w3[3] = {b1, b2, b3};
+        if (has_rows) block_sum_t<3>(w3, stage);
         if (threadIdx.x == 0) {
             double* pp = V.part + (int64_t)blockIdx.x * KPART;
+            const double out9[9] = {v3[0], v3[1], v3[2], w3[0], w3[1], w3[2],
+                                    (double)f3[0], (double)f3[1], (double)f3[2]};
 #pragma unroll
-            for (int i = 0; i < 9; ++i) pp[1 + i] = v9[i];
+            for (int i = 0; i < 9; ++i) pp[1 + i] = out9[i];
         }
     }
     if (!last_cta(V.counters + 2 * t.x + 1, I.tile_end - I.tile_begin, &flag)) return;
