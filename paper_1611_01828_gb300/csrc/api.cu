@@ -18,6 +18,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <numeric>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -66,6 +67,11 @@ struct HostPrep {
     std::vector<int32_t> At_ptr, At_col;      // local constraint indices
     std::vector<double> At_val;
     std::vector<double> b;
+    // internal constraint order: row i of A, b, y is the caller's row perm[i]
+    // (empty: the caller's order).  Constraints are ordered by the first
+    // pattern entry they touch, so that the constraints of one clique are
+    // neighbours and the gathers of A^T y read contiguous runs.
+    std::vector<int32_t> perm;
     // data scaling (hsde_options.scaling): A~ = D A, b~ = sigma D b, c~ = rho c
     std::vector<double> dscale;               // d_i (1 when not scaling)
     double sigma = 1.0, rho = 1.0;
@@ -167,6 +173,36 @@ int prepare(const hsde_problem* P, const hsde_options& O, HostPrep& H, std::stri
         }
         H.A_ptr[i + 1] = (int32_t)H.A_col.size();
     }
+    // internal order of the constraints: by the first pattern entry of each
+    // row (stable, so an already ordered problem keeps the identity)
+    std::vector<double> bp(P->b, P->b + m);
+    {
+        std::vector<int32_t> order(m);
+        std::iota(order.begin(), order.end(), 0);
+        auto first = [&](int32_t i) { return H.A_ptr[i + 1] > H.A_ptr[i] ? H.A_col[H.A_ptr[i]] : INT32_MAX; };
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return first(a) < first(b); });
+        bool ident = true;
+        for (int32_t i = 0; i < m; ++i) ident = ident && order[i] == i;
+        if (!ident) {
+            std::vector<int32_t> ptr(m + 1, 0), col;
+            std::vector<double> val, dsc(m);
+            col.reserve(H.A_col.size());
+            val.reserve(H.A_val.size());
+            for (int32_t i = 0; i < m; ++i) {
+                const int32_t o = order[i];
+                col.insert(col.end(), H.A_col.begin() + H.A_ptr[o], H.A_col.begin() + H.A_ptr[o + 1]);
+                val.insert(val.end(), H.A_val.begin() + H.A_ptr[o], H.A_val.begin() + H.A_ptr[o + 1]);
+                ptr[i + 1] = (int32_t)col.size();
+                dsc[i] = H.dscale[o];
+                bp[i] = P->b[o];
+            }
+            H.A_ptr.swap(ptr);
+            H.A_col.swap(col);
+            H.A_val.swap(val);
+            H.dscale.swap(dsc);
+            H.perm.swap(order);
+        }
+    }
     H.At_ptr.assign(N + 1, 0);
     for (int32_t e : H.A_col) H.At_ptr[e + 1] += 1;
     for (int64_t e = 0; e < N; ++e) H.At_ptr[e + 1] += H.At_ptr[e];
@@ -186,9 +222,9 @@ int prepare(const hsde_problem* P, const hsde_options& O, HostPrep& H, std::stri
         for (int64_t e = 0; e < N; ++e) max_at = std::max(max_at, H.At_ptr[e + 1] - H.At_ptr[e]);
     }
     // b~ = sigma D b, c~ = rho c (the factors from the original data)
-    scale_factors(H, P->b, H.cvec.data(), O, H.sigma, H.rho, H.bnorm, H.cnorm);
+    scale_factors(H, bp.data(), H.cvec.data(), O, H.sigma, H.rho, H.bnorm, H.cnorm);
     H.b.resize(m);
-    for (int32_t i = 0; i < m; ++i) H.b[i] = H.sigma * H.dscale[i] * P->b[i];
+    for (int32_t i = 0; i < m; ++i) H.b[i] = H.sigma * H.dscale[i] * bp[i];
     for (double& cv : H.cvec) cv *= H.rho;
     // S = I + A Delta^{-1} A^T (full-vec inner products); diagonal if no two
     // constraints share a pattern entry.
@@ -281,6 +317,7 @@ struct hsde_handle {
     // per-CTA sums (allocated on first use)
     double* dscale_dev = nullptr;
     double* data_part = nullptr;
+    int32_t* perm_dev = nullptr;        // [Mtot] caller index of each internal row (null: all identity)
     double* data_part_host = nullptr;   // pinned
 };
 
@@ -366,6 +403,7 @@ void free_handle(hsde_handle* h) {
     if (h->arena) cudaFree(h->arena);
     if (h->uw.mem) cudaFree(h->uw.mem);
     if (h->dscale_dev) cudaFree(h->dscale_dev);
+    if (h->perm_dev) cudaFree(h->perm_dev);
     if (h->data_part) cudaFree(h->data_part);
     if (h->data_part_host) cudaFreeHost(h->data_part_host);
     if (h->host_inst) cudaFreeHost(h->host_inst);
@@ -877,6 +915,20 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         CK(cudaStreamSynchronize(st));
     }
 #undef UP
+    // ---- the caller's index of every internal constraint row (device copy,
+    // for the device-pointer paths), when some instance was reordered ----
+    {
+        bool any = false;
+        for (const HostPrep& H : h->prep) any = any || !H.perm.empty();
+        if (any && Mtot > 0) {
+            std::vector<int32_t> pm;
+            pm.reserve(Mtot);
+            for (const HostPrep& H : h->prep)
+                for (int32_t j = 0; j < H.m; ++j) pm.push_back(H.perm.empty() ? j : H.perm[j]);
+            CK(cudaMalloc(&h->perm_dev, sizeof(int32_t) * pm.size()));
+            CK(cudaMemcpy(h->perm_dev, pm.data(), sizeof(int32_t) * pm.size(), cudaMemcpyHostToDevice));
+        }
+    }
     // ---- cached M^{-1} zeta = (x_p, ., y_p, .) and 1 + zeta^T M^{-1} zeta ----
     launch_rhs(V, h->mixed, Mode::Setup, st);
     launch_spmv_A(V, Mode::Setup, st);
@@ -946,6 +998,15 @@ int check_handle(const hsde_handle* h, int32_t i) {
     return HSDE_OK;
 }
 
+// An m-vector of one instance from the internal constraint order to the
+// caller's (out[perm[i]] = in[i]) and back (out[i] = in[perm[i]]).
+void to_caller(const HostPrep& H, const double* in, double* out) {
+    for (int32_t i = 0; i < H.m; ++i) out[H.perm[i]] = in[i];
+}
+void to_internal(const HostPrep& H, const double* in, double* out) {
+    for (int32_t i = 0; i < H.m; ++i) out[i] = in[H.perm[i]];
+}
+
 // kind = 1 for device (or managed) memory of the handle's GPU, 0 for host
 // memory; a pointer into another GPU's memory is refused.
 int pointer_kind(const hsde_handle* h, const void* p, int& kind) {
@@ -958,6 +1019,54 @@ int pointer_kind(const hsde_handle* h, const void* p, int& kind) {
     kind = (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? 1 : 0;
     if (a.type == cudaMemoryTypeDevice && a.device != h->device)
         return fail(HSDE_EINVAL, "device pointer of another GPU");
+    return HSDE_OK;
+}
+
+// The m-vector of a single-instance handle between the device (internal
+// constraint order) and a caller buffer (host or device memory, the
+// caller's order).  Both return with the copy done.
+int m_out(hsde_handle* h, double* dst, const double* src) {
+    const HostPrep& H = h->prep[0];
+    const int32_t m = H.m;
+    if (m == 0) return HSDE_OK;
+    if (H.perm.empty()) {
+        CK(cudaMemcpy(dst, src, sizeof(double) * m, cudaMemcpyDefault));
+        return HSDE_OK;
+    }
+    int kind = 0, rc;
+    if ((rc = pointer_kind(h, dst, kind)) != HSDE_OK) return rc;
+    if (kind) {
+        launch_perm_move(dst, src, h->perm_dev, m, true, h->st);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(h->st));
+    } else {
+        std::vector<double> t(m);
+        CK(cudaMemcpy(t.data(), src, sizeof(double) * m, cudaMemcpyDeviceToHost));
+        to_caller(H, t.data(), dst);
+    }
+    return HSDE_OK;
+}
+
+int m_in(hsde_handle* h, double* dst, const double* src) {
+    const HostPrep& H = h->prep[0];
+    const int32_t m = H.m;
+    if (m == 0) return HSDE_OK;
+    CK(cudaStreamSynchronize(h->st));
+    if (H.perm.empty()) {
+        CK(cudaMemcpy(dst, src, sizeof(double) * m, cudaMemcpyDefault));
+        return HSDE_OK;
+    }
+    int kind = 0, rc;
+    if ((rc = pointer_kind(h, src, kind)) != HSDE_OK) return rc;
+    if (kind) {
+        launch_perm_move(dst, src, h->perm_dev, m, false, h->st);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(h->st));
+    } else {
+        std::vector<double> t(m);
+        to_internal(H, src, t.data());
+        CK(cudaMemcpy(dst, t.data(), sizeof(double) * m, cudaMemcpyHostToDevice));
+    }
     return HSDE_OK;
 }
 
@@ -1189,7 +1298,13 @@ int hsde_get_state(hsde_handle* h, int32_t i, double* state) {
     double* p = state;
     CK(cudaMemcpy(p, h->V.x + h->x_off[i], sizeof(double) * N, cudaMemcpyDeviceToHost)); p += N;
     if ((rc = get_packed(h, h->V.s, i, p)) != HSDE_OK) return rc; p += P;
-    if (m) CK(cudaMemcpy(p, h->V.y + h->m_off[i], sizeof(double) * m, cudaMemcpyDeviceToHost));
+    if (m && H.perm.empty()) {
+        CK(cudaMemcpy(p, h->V.y + h->m_off[i], sizeof(double) * m, cudaMemcpyDeviceToHost));
+    } else if (m) {
+        std::vector<double> yi(m);
+        CK(cudaMemcpy(yi.data(), h->V.y + h->m_off[i], sizeof(double) * m, cudaMemcpyDeviceToHost));
+        to_caller(H, yi.data(), p);
+    }
     p += m;
     if ((rc = get_packed(h, h->V.v, i, p)) != HSDE_OK) return rc; p += P;
     *p++ = h->host_inst[i].tau;
@@ -1210,7 +1325,13 @@ int hsde_set_state(hsde_handle* h, int32_t i, const double* state, int32_t itera
     const double* p = state;
     CK(cudaMemcpy(h->V.x + h->x_off[i], p, sizeof(double) * N, cudaMemcpyHostToDevice)); p += N;
     if ((rc = set_packed(h, h->V.s, i, p)) != HSDE_OK) return rc; p += P;
-    if (m) CK(cudaMemcpy(h->V.y + h->m_off[i], p, sizeof(double) * m, cudaMemcpyHostToDevice));
+    if (m && H.perm.empty()) {
+        CK(cudaMemcpy(h->V.y + h->m_off[i], p, sizeof(double) * m, cudaMemcpyHostToDevice));
+    } else if (m) {
+        std::vector<double> yi(m);
+        to_internal(H, p, yi.data());
+        CK(cudaMemcpy(h->V.y + h->m_off[i], yi.data(), sizeof(double) * m, cudaMemcpyHostToDevice));
+    }
     p += m;
     if ((rc = set_packed(h, h->V.v, i, p)) != HSDE_OK) return rc; p += P;
     const double tau = *p++;
@@ -1249,8 +1370,11 @@ int hsde_get_solution(hsde_handle* h, int32_t i, double* X, double* y, double* Z
         for (int64_t e = 0; e < N; ++e) X[e] /= I.sigma * tau;
     }
     if (y && H.m) {
-        CK(cudaMemcpy(y, h->V.y + h->m_off[i], sizeof(double) * H.m, cudaMemcpyDeviceToHost));
-        for (int32_t j = 0; j < H.m; ++j) y[j] = H.dscale[j] * y[j] / (I.rho * tau);
+        std::vector<double> yi(H.m);
+        CK(cudaMemcpy(yi.data(), h->V.y + h->m_off[i], sizeof(double) * H.m, cudaMemcpyDeviceToHost));
+        for (int32_t j = 0; j < H.m; ++j) yi[j] = H.dscale[j] * yi[j] / (I.rho * tau);
+        if (H.perm.empty()) std::copy(yi.begin(), yi.end(), y);
+        else to_caller(H, yi.data(), y);
     }
     if (Z) {
         std::vector<double> zp(P);
@@ -1278,8 +1402,11 @@ int hsde_get_certificate(hsde_handle* h, int32_t i, int32_t kind, double* y, dou
     if (kind == HSDE_PRIMAL_INFEASIBLE) {
         const double bty = I.bty;
         if (y && H.m) {
-            CK(cudaMemcpy(y, h->V.y + h->m_off[i], sizeof(double) * H.m, cudaMemcpyDeviceToHost));
-            for (int32_t j = 0; j < H.m; ++j) y[j] = H.dscale[j] * y[j] / I.rho / bty;
+            std::vector<double> yi(H.m);
+            CK(cudaMemcpy(yi.data(), h->V.y + h->m_off[i], sizeof(double) * H.m, cudaMemcpyDeviceToHost));
+            for (int32_t j = 0; j < H.m; ++j) yi[j] = H.dscale[j] * yi[j] / I.rho / bty;
+            if (H.perm.empty()) std::copy(yi.begin(), yi.end(), y);
+            else to_caller(H, yi.data(), y);
         }
         if (Z) {
             std::vector<double> zp(P);
@@ -1507,7 +1634,8 @@ int hsde_set_data(hsde_handle* h, int32_t i, const double* c, const double* b) {
         }
         const double* dsc = h->dscale_dev + h->m_off[i];
         const uint8_t* dg = h->V.diag + h->x_off[i];
-        launch_data_sums(c, N, dg, b, H.m, dsc, h->data_part, h->st);
+        const int32_t* pm = H.perm.empty() ? nullptr : h->perm_dev + h->m_off[i];
+        launch_data_sums(c, N, dg, b, H.m, dsc, pm, h->data_part, h->st);
         const int nb = data_grid(N, H.m);
         CK(cudaMemcpyAsync(h->data_part_host, h->data_part, sizeof(double) * 4 * nb, cudaMemcpyDeviceToHost,
                            h->st));
@@ -1517,13 +1645,19 @@ int hsde_set_data(hsde_handle* h, int32_t i, const double* c, const double* b) {
             for (int j = 0; j < 4; ++j) sm[j] += h->data_part_host[4 * k + j];
         if (sm[0] != 0.0) return fail(HSDE_EINVAL, "non-finite c or b");
         scale_from_sums(sm[1], sm[2], sm[3], h->opt, H.sigma, H.rho, H.bnorm, H.cnorm);
-        launch_data_apply(c, N, H.rho, b, H.m, H.sigma, dsc, cdst, bdst, h->st);
+        launch_data_apply(c, N, H.rho, b, H.m, H.sigma, dsc, pm, cdst, bdst, h->st);
         CK(cudaGetLastError());
     } else {
         for (int64_t e = 0; e < N; ++e)
             if (!std::isfinite(c[e])) return fail(HSDE_EINVAL, "non-finite c");
         for (int32_t j = 0; j < H.m; ++j)
             if (!std::isfinite(b[j])) return fail(HSDE_EINVAL, "non-finite b");
+        std::vector<double> bi;
+        if (!H.perm.empty()) {
+            bi.resize(H.m);
+            to_internal(H, b, bi.data());
+            b = bi.data();
+        }
         // new scaling factors from the new data (D depends on A only)
         scale_factors(H, b, c, h->opt, H.sigma, H.rho, H.bnorm, H.cnorm);
         H.cvec.resize(N);
@@ -1577,7 +1711,7 @@ int hsde_unrolled_forward(hsde_handle* h, int32_t K, int32_t ckpt, double* x, do
     const InstDev& I = h->host_inst[0];
     // caller buffers: host or device memory (unified addressing)
     if (x) CK(cudaMemcpy(x, h->V.x, sizeof(double) * h->V.Ntot, cudaMemcpyDefault));
-    if (y && h->V.Mtot) CK(cudaMemcpy(y, h->V.y, sizeof(double) * h->V.Mtot, cudaMemcpyDefault));
+    if (y && (rc = m_out(h, y, h->V.y)) != HSDE_OK) return rc;
     if (tau) *tau = I.tau;
     if (kappa) *kappa = I.kappa;
     w.forward_done = true;
@@ -1598,7 +1732,10 @@ int hsde_unrolled_backward(hsde_handle* h, const double* xbar, const double* yba
     if (xbar) CK(cudaMemcpyAsync(w.xbar, xbar, sizeof(double) * V.Ntot, cudaMemcpyDefault, st));
     else CK(cudaMemsetAsync(w.xbar, 0, sizeof(double) * V.Ntot, st));
     if (V.Mtot) {
-        if (ybar) CK(cudaMemcpyAsync(w.ybar, ybar, sizeof(double) * V.Mtot, cudaMemcpyDefault, st));
+        if (ybar) {
+            int rc0;
+            if ((rc0 = m_in(h, w.ybar, ybar)) != HSDE_OK) return rc0;
+        }
         else CK(cudaMemsetAsync(w.ybar, 0, sizeof(double) * V.Mtot, st));
     }
     const double sc[2] = {taubar, kappabar};
@@ -1654,7 +1791,7 @@ int hsde_unrolled_backward(hsde_handle* h, const double* xbar, const double* yba
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
     if (gC) CK(cudaMemcpy(gC, w.gc, sizeof(double) * V.Ntot, cudaMemcpyDefault));
-    if (gb && V.Mtot) CK(cudaMemcpy(gb, w.gb, sizeof(double) * V.Mtot, cudaMemcpyDefault));
+    if (gb && V.Mtot && (rc = m_out(h, gb, w.gb)) != HSDE_OK) return rc;
     h->need_rhs = true;
     return HSDE_OK;
 }

@@ -251,9 +251,13 @@ void launch_form_S(const DevView& V, const int32_t* rows, int32_t nrows, int32_t
 constexpr int DATA_MAX_CTAS = 304;
 int data_grid(int64_t N, int32_t m);
 void launch_data_sums(const double* c, int64_t N, const uint8_t* diag, const double* b, int32_t m,
-                      const double* dscale, double* part, void* st);
+                      const double* dscale, const int32_t* perm, double* part, void* st);
 void launch_data_apply(const double* c, int64_t N, double rho, const double* b, int32_t m, double sigma,
-                       const double* dscale, double* cdst, double* bdst, void* st);
+                       const double* dscale, const int32_t* perm, double* cdst, double* bdst, void* st);
+// m-vector of one instance between the caller's constraint order and the
+// internal one (perm[i]: the caller's index of internal row i): scatter
+// dst[perm[i]] = src[i], else gather dst[i] = src[perm[i]]
+void launch_perm_move(double* dst, const double* src, const int32_t* perm, int32_t m, bool scatter, void* st);
 // A x and A^T y of the stored iterate into V.ax, V.aty for the constraint
 // rows [r0, r1) and pattern entries [e0, e1) (after hsde_set_state)
 void launch_state_products(const DevView& V, int r0, int r1, int64_t e0, int64_t e1, void* st);

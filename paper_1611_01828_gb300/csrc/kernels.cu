@@ -811,7 +811,7 @@ void launch_post(const DevView& V, bool mixed, void* st) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NT) k_data_sums(const double* c, int64_t N, const uint8_t* diag,
                                                   const double* b, int32_t m, const double* dscale,
-                                                  double* part) {
+                                                  const int32_t* perm, double* part) {
     __shared__ double sh[4 * (NT / 32)];
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     const int64_t stride = (int64_t)gridDim.x * NT;
@@ -821,7 +821,7 @@ __global__ void __launch_bounds__(NT) k_data_sums(const double* c, int64_t N, co
         else v[3] += (diag[e] ? 1.0 : 2.0) * ce * ce;
     }
     for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < m; i += stride) {
-        const double bi = b[i];
+        const double bi = b[perm ? perm[i] : i];
         if (!isfinite(bi)) {
             v[0] += 1.0;
         } else {
@@ -836,12 +836,22 @@ __global__ void __launch_bounds__(NT) k_data_sums(const double* c, int64_t N, co
 }
 
 __global__ void __launch_bounds__(NT) k_data_apply(const double* c, int64_t N, double rho, const double* b,
-                                                   int32_t m, double sigma, const double* dscale, double* cdst,
-                                                   double* bdst) {
+                                                   int32_t m, double sigma, const double* dscale,
+                                                   const int32_t* perm, double* cdst, double* bdst) {
     const int64_t stride = (int64_t)gridDim.x * NT;
     for (int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x; e < N; e += stride) cdst[e] = rho * c[e];
     for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < m; i += stride)
-        bdst[i] = sigma * dscale[i] * b[i];
+        bdst[i] = sigma * dscale[i] * b[perm ? perm[i] : i];
+}
+
+// m-vectors between the caller's constraint order and the internal one:
+// gather dst[i] = src[perm[i]], scatter dst[perm[i]] = src[i].
+__global__ void __launch_bounds__(NT) k_perm_move(double* dst, const double* src, const int32_t* perm, int32_t m,
+                                                  int scatter) {
+    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < m; i += (int64_t)gridDim.x * NT) {
+        if (scatter) dst[perm[i]] = src[i];
+        else dst[i] = src[perm[i]];
+    }
 }
 
 int data_grid(int64_t N, int32_t m) {
@@ -849,12 +859,16 @@ int data_grid(int64_t N, int32_t m) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + NT - 1) / NT, DATA_MAX_CTAS));
 }
 void launch_data_sums(const double* c, int64_t N, const uint8_t* diag, const double* b, int32_t m,
-                      const double* dscale, double* part, void* st) {
-    k_data_sums<<<data_grid(N, m), NT, 0, S_(st)>>>(c, N, diag, b, m, dscale, part);
+                      const double* dscale, const int32_t* perm, double* part, void* st) {
+    k_data_sums<<<data_grid(N, m), NT, 0, S_(st)>>>(c, N, diag, b, m, dscale, perm, part);
 }
 void launch_data_apply(const double* c, int64_t N, double rho, const double* b, int32_t m, double sigma,
-                       const double* dscale, double* cdst, double* bdst, void* st) {
-    k_data_apply<<<data_grid(N, m), NT, 0, S_(st)>>>(c, N, rho, b, m, sigma, dscale, cdst, bdst);
+                       const double* dscale, const int32_t* perm, double* cdst, double* bdst, void* st) {
+    k_data_apply<<<data_grid(N, m), NT, 0, S_(st)>>>(c, N, rho, b, m, sigma, dscale, perm, cdst, bdst);
+}
+void launch_perm_move(double* dst, const double* src, const int32_t* perm, int32_t m, bool scatter, void* st) {
+    if (m <= 0) return;
+    k_perm_move<<<data_grid(0, m), NT, 0, S_(st)>>>(dst, src, perm, m, scatter ? 1 : 0);
 }
 
 void launch_gj_step(double* pool, const int64_t* offs, const int32_t* ms, const int64_t* tile_pre, int nact,
