@@ -87,7 +87,8 @@ def sweep_stats(phases):
     out["bucket_max"] = {k: round(a[3] / a[2], 2) for k, a in phases.items()
                          if k.startswith("cone_") and a[2]}
     # eigensolver variant of each bucket (the setup autotuner's choice)
-    out["bucket_variant"] = {k: ("throughput" if v else "latency") for k, v in phases.get("_variants", {}).items()}
+    names = {0: "latency", 1: "throughput", 2: "register-V"}
+    out["bucket_variant"] = {k: names.get(v, str(v)) for k, v in phases.get("_variants", {}).items()}
     return out
 
 

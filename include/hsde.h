@@ -137,14 +137,17 @@ typedef struct hsde_options {
     int32_t autotune;     /* eigensolver variant of each clique bucket (the
                              latency variant: about one 2x2 block per thread;
                              the throughput variant: fewer threads a clique,
-                             more cliques per SM).  Both give bitwise the same
-                             results.  1 (default): time both once per
-                             (precision, bucket size, clique count, SM count)
-                             at setup and keep the faster (cached for the
-                             process); 0: throughput unless the bucket's CTAs
-                             each have an SM to themselves; 2: always latency;
-                             3: always throughput.  A bucket of few large
-                             cliques always runs the latency variant.        */
+                             more cliques per SM; the register-V variant,
+                             FP32 sizes 24-64: V held in registers through
+                             the sweeps).  All give bitwise the same results.
+                             1 (default): time them once per (precision,
+                             bucket size, clique count, SM count) at setup
+                             and keep the fastest (cached for the process);
+                             0: throughput unless the bucket's CTAs each have
+                             an SM to themselves; 2: always latency;
+                             3: always throughput; 4: register-V where the
+                             bucket has it.  A bucket of few large cliques
+                             always runs the latency variant.               */
 } hsde_options;
 
 typedef struct hsde_sizes {
@@ -193,7 +196,8 @@ typedef struct hsde_profile {
                                                    for the other phases       */
     int32_t phase_variant[HSDE_MAX_PHASES];  /* cone phases: the eigensolver
                                                 variant the bucket runs (0
-                                                latency, 1 throughput; see
+                                                latency, 1 throughput, 2
+                                                register-V; see
                                                 options.autotune)           */
 } hsde_profile;
 

@@ -459,12 +459,13 @@ void append_at_tiles(const HostPrep& H, int32_t b, int64_t xo, std::vector<int4>
 
 // ---- eigensolver variant per bucket (the autotuner) ----
 // A bucket of few large cliques (each CTA alone on its SM) runs the latency
-// variant.  Any other bucket with two variants gets the faster one for its
-// clique count on this GPU, timed once per (precision, size, count, SMs) in
-// dry runs (synthetic matrices, two sweeps, no writes) and cached for the
-// process.  Both variants give bitwise the same results, so the choice
-// changes only the time.  options.autotune: 1 time (default), 0 the rule
-// "throughput variant unless alone", 2 always latency, 3 always throughput.
+// variant.  Any other bucket with more than one variant gets the fastest for
+// its clique count on this GPU, timed once per (precision, size, count, SMs)
+// in dry runs (synthetic matrices, two sweeps, no writes) and cached for the
+// process.  All variants give bitwise the same results, so the choice
+// changes only the time.  options.autotune: 1 time them (default); 0 the
+// throughput variant unless alone; 2 always latency; 3 always throughput;
+// 4 register-V where a bucket has it (else throughput, else latency).
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, int> g_tune_cache;
 
@@ -492,11 +493,18 @@ int choose_variants(hsde_handle* h) {
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
     for (Bucket& bk : h->buckets) {
         bk.variant = 0;
-        if (cone_variants(bk.cmax, h->mixed) < 2 || cone_bucket_alone(bk, h->mixed)) continue;
+        bool has[3];
+        int nv = 0;
+        for (int v = 0; v < 3; ++v) nv += (has[v] = cone_has_variant(bk.cmax, h->mixed, v)) ? 1 : 0;
+        if (nv < 2 || cone_bucket_alone(bk, h->mixed)) continue;
         const int mode = h->opt.autotune;
         if (mode == 2) continue;
         if (mode == 0 || mode == 3) {
-            bk.variant = 1;
+            bk.variant = has[1] ? 1 : 0;
+            continue;
+        }
+        if (mode == 4) {
+            bk.variant = has[2] ? 2 : (has[1] ? 1 : 0);
             continue;
         }
         const auto key = std::make_tuple((int)h->mixed, (int)bk.cmax, (int)bk.count, nsm);
@@ -508,13 +516,18 @@ int choose_variants(hsde_handle* h) {
                 continue;
             }
         }
-        float t0 = 0.f, t1 = 0.f;
-        int rc;
-        if ((rc = time_variant(h, bk, 0, t0)) != HSDE_OK) return rc;
-        if ((rc = time_variant(h, bk, 1, t1)) != HSDE_OK) return rc;
-        bk.variant = t1 < t0 ? 1 : 0;
+        int best = 0;
+        float tbest = 0.f;
+        for (int v = 0; v < 3; ++v) {
+            if (!has[v]) continue;
+            float t = 0.f;
+            int rc;
+            if ((rc = time_variant(h, bk, v, t)) != HSDE_OK) return rc;
+            if (v == 0 || t < tbest) { best = v; tbest = t; }
+        }
+        bk.variant = best;
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = bk.variant;
+        g_tune_cache[key] = best;
     }
     return HSDE_OK;
 }
@@ -532,7 +545,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         opt.jacobi_tol < 0 || opt.warm_start < -1 || opt.warm_start > 1 || opt.warm_refresh < 0 ||
         (opt.scaling != 0 && opt.scaling != 1) || (opt.structured_factor != 0 && opt.structured_factor != 1) || !(opt.alpha > 0.0 && opt.alpha < 2.0) ||
         !(opt.scale_norm > 0.0) || !(opt.dual_weight > 0.0) || !std::isfinite(opt.scale_norm) ||
-        !std::isfinite(opt.dual_weight) || opt.autotune < 0 || opt.autotune > 3)
+        !std::isfinite(opt.dual_weight) || opt.autotune < 0 || opt.autotune > 4)
         return fail(HSDE_EINVAL, "invalid options");
 
     auto* h = new hsde_handle();

@@ -219,6 +219,22 @@ __device__ __forceinline__ void rotation(double app, double aqq, double apq, dou
     }
 }
 
+// Products and FMAs with the rounding fixed by the source (no contraction
+// left to the compiler), so that the register-V and shared-memory variants
+// of a bucket update V with bitwise the same arithmetic.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// The rotation (c, s) of one slot pair applied to the pair's entries (v0, v1)
+// of one column of V: (c v0 - s v1, s v0 + c v1).
+template <typename T>
+__device__ __forceinline__ void rot_pair(T c, T s, T v0, T v1, T& n0, T& n1) {
+    n0 = fma_rn(-s, v1, mul_rn(c, v0));
+    n1 = fma_rn(s, v0, mul_rn(c, v1));
+}
+
 // Offsets (in elements of one CP x LD buffer) a thread uses in every round.
 // The thread-to-block assignment does not change between rounds, so the
 // tournament map is evaluated once per solve, not once per round.
@@ -271,6 +287,39 @@ struct RoundPlan {
     }
 };
 
+// Block i of a thread's round plan: J_r^T X J_c of the 2 x 2 block X (rows
+// 2kr, 2kr+1; columns 2kc, 2kc+1), written to its slots of the next round.
+// A diagonal block keeps its lower triangle: a_pp - t a_pq, 0, a_qq + t a_pq.
+template <typename Cfg, typename T>
+__device__ __forceinline__ void update_block(const RoundPlan<Cfg>& pl, int i, const T* __restrict__ A,
+                                             T* __restrict__ An, const T* __restrict__ rot,
+                                             const T* __restrict__ tan_) {
+    constexpr int LD = Cfg::LD;
+    using V2 = typename Vec2<T>::type;
+    const V2 top = *reinterpret_cast<const V2*>(A + pl.a_src[i]);
+    const V2 bot = *reinterpret_cast<const V2*>(A + pl.a_src[i] + LD);
+    if (pl.diag_mask & (1u << i)) {
+        // top.y lies above the diagonal (not kept); a_pq = bot.x
+        const T t = tan_[pl.rot_r[i] >> 1];
+        const T apq = bot.x;
+        An[pl.a_dst[i][0]] = fma_rn(-t, apq, top.x);
+        An[pl.a_dst[i][1]] = (t == T(0)) ? apq : T(0);
+        An[pl.a_dst[i][3]] = fma_rn(t, apq, bot.y);
+    } else {
+        const V2 rr = *reinterpret_cast<const V2*>(rot + pl.rot_r[i]);
+        const V2 rc = *reinterpret_cast<const V2*>(rot + pl.rot_c[i]);
+        T y00, y01, y10, y11, d0, d1, d2, d3;
+        rot_pair(rr.x, rr.y, top.x, bot.x, y00, y10);    // J_r^T X, first column
+        rot_pair(rr.x, rr.y, top.y, bot.y, y01, y11);    // second column
+        rot_pair(rc.x, rc.y, y00, y01, d0, d1);          // (.) J_c, first row
+        rot_pair(rc.x, rc.y, y10, y11, d2, d3);          // second row
+        An[pl.a_dst[i][0]] = d0;
+        An[pl.a_dst[i][1]] = d1;
+        An[pl.a_dst[i][2]] = d2;
+        An[pl.a_dst[i][3]] = d3;
+    }
+}
+
 template <typename Cfg, typename T>
 __device__ __forceinline__ void jacobi_round(const RoundPlan<Cfg>& pl, const T* __restrict__ A,
                                              T* __restrict__ An, const T* __restrict__ Vc, T* __restrict__ Vn,
@@ -294,27 +343,7 @@ __device__ __forceinline__ void jacobi_round(const RoundPlan<Cfg>& pl, const T* 
 #pragma unroll
     for (int i = 0; i < Cfg::BPL; ++i) {
         if ((Cfg::NBLK % G != 0) && !(pl.a_valid & (1u << i))) continue;
-        const V2 top = *reinterpret_cast<const V2*>(A + pl.a_src[i]);
-        const V2 bot = *reinterpret_cast<const V2*>(A + pl.a_src[i] + LD);
-        if (pl.diag_mask & (1u << i)) {
-            // top.y lies above the diagonal (not kept); a_pq = bot.x
-            const T t = tan_[pl.rot_r[i] >> 1];
-            const T apq = bot.x;
-            An[pl.a_dst[i][0]] = top.x - t * apq;
-            An[pl.a_dst[i][1]] = (t == T(0)) ? apq : T(0);
-            An[pl.a_dst[i][3]] = bot.y + t * apq;
-        } else {
-            const V2 rr = *reinterpret_cast<const V2*>(rot + pl.rot_r[i]);
-            const V2 rc = *reinterpret_cast<const V2*>(rot + pl.rot_c[i]);
-            // J_r^T X
-            const T y00 = rr.x * top.x - rr.y * bot.x, y01 = rr.x * top.y - rr.y * bot.y;
-            const T y10 = rr.y * top.x + rr.x * bot.x, y11 = rr.y * top.y + rr.x * bot.y;
-            // (.) J_c
-            An[pl.a_dst[i][0]] = rc.x * y00 - rc.y * y01;
-            An[pl.a_dst[i][1]] = rc.y * y00 + rc.x * y01;
-            An[pl.a_dst[i][2]] = rc.x * y10 - rc.y * y11;
-            An[pl.a_dst[i][3]] = rc.y * y10 + rc.x * y11;
-        }
+        update_block(pl, i, A, An, rot, tan_);
     }
 #pragma unroll
     for (int i = 0; i < Cfg::VPL; ++i) {
@@ -323,14 +352,67 @@ __device__ __forceinline__ void jacobi_round(const RoundPlan<Cfg>& pl, const T* 
         const V2 v0 = *reinterpret_cast<const V2*>(Vc + pl.v_src[i]);
         const V2 v1 = *reinterpret_cast<const V2*>(Vc + pl.v_src[i] + LD);
         V2 n0, n1;
-        n0.x = rc.x * v0.x - rc.y * v1.x;
-        n0.y = rc.x * v0.y - rc.y * v1.y;
-        n1.x = rc.y * v0.x + rc.x * v1.x;
-        n1.y = rc.y * v0.y + rc.x * v1.y;
+        rot_pair(rc.x, rc.y, v0.x, v1.x, n0.x, n1.x);
+        rot_pair(rc.x, rc.y, v0.y, v1.y, n0.y, n1.y);
         *reinterpret_cast<V2*>(Vn + pl.v_dst0[i]) = n0;
         *reinterpret_cast<V2*>(Vn + pl.v_dst1[i]) = n1;
     }
     gsync<G>(gid);
+}
+
+// Slot c_i of the circle-tournament cycle: 1 -> 2 -> 4 -> ... -> CP-2 ->
+// CP-1 -> CP-3 -> ... -> 3 -> 1 (slot 0 stays), so sigma(c_i) = c_(i+1).
+template <int CP>
+__device__ __forceinline__ int cycle_slot(int i) {
+    constexpr int K = CP / 2;
+    return i == 0 ? 1 : (i < K ? 2 * i : 4 * K - 1 - 2 * i);
+}
+
+// One round of the register-V variant.  The A-threads (is_a; the plan is
+// theirs) compute the rotations and update A as in jacobi_round; each
+// V-thread holds one column of V (all CP slots) in registers, applies the
+// round's K rotations and then the slot permutation sigma, moving values
+// along the one cycle of sigma (register moves, no shared memory).
+template <typename PCfg, int GT, typename T>
+__device__ __forceinline__ void jacobi_round_rv(const RoundPlan<PCfg>& pl, const T* __restrict__ A,
+                                                T* __restrict__ An, T* __restrict__ rot, T* __restrict__ tan_,
+                                                int alane, bool is_a, T (&vr)[PCfg::CP], int gid) {
+    constexpr int CP = PCfg::CP, K = PCfg::K, LD = PCfg::LD, G = PCfg::G;
+    using V2 = typename Vec2<T>::type;
+    if (is_a && alane < K) {
+        const int k = alane;
+        const T app = A[(2 * k) * LD + 2 * k];
+        const V2 qrow = *reinterpret_cast<const V2*>(A + (2 * k + 1) * LD + 2 * k);
+        T cs, sn, t;
+        rotation(app, qrow.y, qrow.x, cs, sn, t);
+        V2 cssn;
+        cssn.x = cs;
+        cssn.y = sn;
+        *reinterpret_cast<V2*>(rot + 2 * k) = cssn;
+        tan_[k] = t;
+    }
+    gsync<GT>(gid);
+    if (is_a) {
+#pragma unroll
+        for (int i = 0; i < PCfg::BPL; ++i) {
+            if ((PCfg::NBLK % G != 0) && !(pl.a_valid & (1u << i))) continue;
+            update_block(pl, i, A, An, rot, tan_);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const V2 cs = *reinterpret_cast<const V2*>(rot + 2 * k);
+            T n0, n1;
+            rot_pair(cs.x, cs.y, vr[2 * k], vr[2 * k + 1], n0, n1);
+            vr[2 * k] = n0;
+            vr[2 * k + 1] = n1;
+        }
+        const T last = vr[cycle_slot<CP>(CP - 2)];
+#pragma unroll
+        for (int i = CP - 2; i >= 1; --i) vr[cycle_slot<CP>(i)] = vr[cycle_slot<CP>(i - 1)];
+        vr[cycle_slot<CP>(0)] = last;
+    }
+    gsync<GT>(gid);
 }
 
 // The point projected for one packed entry, from the previous s, z, v of
@@ -386,11 +468,25 @@ __device__ __forceinline__ T dry_entry(int k, int i, int j) {
 // registers go to more resident CTAs).  dry != 0 (autotuning): a
 // deterministic synthetic matrix instead of the gather, a cold start,
 // exactly max_sweeps sweeps, and no global writes.
-template <typename T, int CP, int G, int MB, bool ST>
+// Register-V variant (VR): of the G threads, the last GV = 32 ceil(CP / 32)
+// each hold one column of V in registers through the sweeps (no shared-
+// memory traffic for V), the first G - GV (the A-threads) update A; every
+// other phase runs on all G threads as in the other variants.
+template <int CP, int G, bool VR>
+struct RegV {
+    static constexpr int GV = VR ? (CP + 31) / 32 * 32 : 0;
+    static constexpr int GA = G - GV;
+};
+
+template <typename T, int CP, int G, int MB, bool ST, bool VR>
 __global__ void __launch_bounds__(ConeCfg<T, CP, G>::NTH, MB)
 k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T tol2, int warm, int refresh,
        int dry) {
     using Cfg = ConeCfg<T, CP, G>;
+    constexpr int GA = RegV<CP, G, VR>::GA;
+    static_assert(!VR || (G > 32 && GA >= 32 && GA % 32 == 0), "register-V: whole warps of each kind");
+    // the round plan's configuration: the A-threads' (all threads without VR)
+    using PCfg = ConeCfg<T, CP, VR ? GA : G>;
     using V2 = typename Vec2<T>::type;
     constexpr int LD = Cfg::LD, K = Cfg::K;
     constexpr int EPT = (CP * (CP + 1) / 2 + G - 1) / G;   // lower entries per thread
@@ -515,8 +611,9 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
     T* An = A1;
     T* Vc = V0;
     T* Vn = V1;
-    RoundPlan<Cfg> plan;
-    plan.build(lane);
+    const bool is_a = !VR || lane < GA;
+    RoundPlan<PCfg> plan;
+    plan.build(is_a ? lane : 0);
     const int cq = (c + 1) & ~1;   // A and its products vanish beyond c
     if (reorth) {
         // Gram matrix G = V^T V (slot x slot) into An, 2 x 2 tiles over all CP
@@ -590,8 +687,8 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
         gsync<G>(gid);
         // lower triangle of A = An V, 2 x 2 tiles (the round plan's blocks)
 #pragma unroll
-        for (int i = 0; i < Cfg::BPL; ++i) {
-            if ((Cfg::NBLK % G != 0) && !(plan.a_valid & (1u << i))) continue;
+        for (int i = 0; i < PCfg::BPL; ++i) {
+            if (!is_a || ((PCfg::NBLK % PCfg::G != 0) && !(plan.a_valid & (1u << i)))) continue;
             const int r = plan.rot_r[i], cl = plan.rot_c[i];
             T a00 = 0, a01 = 0, a10 = 0, a11 = 0;
             for (int q = 0; q < cq; q += 2) {
@@ -612,6 +709,13 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
         gsync<G>(gid);
     }
 
+    // register-V: each V-thread takes its column of V (slot-major in Vc)
+    T vr[VR ? CP : 1];
+    if constexpr (VR) {
+        const int col = lane - GA;
+#pragma unroll
+        for (int q = 0; q < CP; ++q) vr[q] = (!is_a && col < CP) ? Vc[q * LD + col] : T(0);
+    }
     int sweeps_done = 0;
     bool converged = false;
     for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
@@ -634,10 +738,23 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
         converged = offd <= tol2 * tot;
         if ((converged && !dry) || sweep == max_sweeps) break;
         for (int r = 0; r < CP - 1; ++r) {
-            jacobi_round<Cfg>(plan, A, An, Vc, Vn, rot, tan_, lane, gid);
+            if constexpr (VR) {
+                jacobi_round_rv<PCfg, G>(plan, A, An, rot, tan_, lane, is_a, vr, gid);
+            } else {
+                jacobi_round<Cfg>(plan, A, An, Vc, Vn, rot, tan_, lane, gid);
+                T* t2 = Vc; Vc = Vn; Vn = t2;
+            }
             T* t1 = A; A = An; An = t1;
-            T* t2 = Vc; Vc = Vn; Vn = t2;
         }
+    }
+    if constexpr (VR) {
+        // the V columns back to shared memory (slot-major) for what follows
+        const int col = lane - GA;
+        if (!is_a && col < CP) {
+#pragma unroll
+            for (int q = 0; q < CP; ++q) Vc[q * LD + col] = vr[q];
+        }
+        gsync<G>(gid);
     }
     if (V.tape_v && !dry) {
         // reverse-mode tape: eigenvectors (original index x slot) and raw eigenvalues
@@ -687,8 +804,8 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
     // eigenvalues only), into the free buffer An
     const int npos = pos[CP];
 #pragma unroll
-    for (int i = 0; i < Cfg::BPL; ++i) {
-        if ((Cfg::NBLK % G != 0) && !(plan.a_valid & (1u << i))) continue;
+    for (int i = 0; i < PCfg::BPL; ++i) {
+        if (!is_a || ((PCfg::NBLK % PCfg::G != 0) && !(plan.a_valid & (1u << i)))) continue;
         const int r = plan.rot_r[i], cl = plan.rot_c[i];
         if (cl >= c) continue;
         T a00 = 0, a01 = 0, a10 = 0, a11 = 0;
@@ -767,8 +884,8 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
 }
 
 // ---------------------------------------------------------------------------
-// buckets: padded size CP; threads per clique G of the latency variant; GT of
-// the throughput variant (0: none)
+// buckets: padded size CP; threads per clique G of the latency variant, GT of
+// the throughput variant and GR of the register-V variant (0: none)
 // ---------------------------------------------------------------------------
 // (padding a clique of c to CP costs about (CP/c)^3 of the work, so the
 // sizes are spaced by 4 above 16.)  The latency variant gives about one 2x2
@@ -776,15 +893,18 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
 // gathered values in registers: the fastest solve of one clique.  The
 // throughput variant gives about two blocks per thread, re-reads the
 // gathered values, and is compiled for as many resident CTAs as the shared
-// memory allows with ~72 registers a thread: more cliques per SM.  Both give
-// bitwise the same results (the same per-element arithmetic, and sums in a
-// fixed order).  Sizes above 64 hold one clique per CTA of up to 1024
-// threads; a size exists for a precision only if its CTA fits the opt-in
-// shared memory (FP32 up to 112, FP64 up to 80).
+// memory allows with ~72 registers a thread: more cliques per SM.  The
+// register-V variant (FP32) adds a warp or two that hold V in registers
+// through the sweeps, about three blocks per A-thread.  All give bitwise the
+// same results (the same per-element arithmetic with its rounding fixed in
+// the source, and sums in a fixed order).  Sizes above 64 hold one clique per
+// CTA of up to 1024 threads; a size exists for a precision only if its CTA
+// fits the opt-in shared memory (FP32 up to 112, FP64 up to 80).
 #define HSDE_CONE_BUCKETS(X)                                                                          \
-    X(4, 4, 0) X(8, 8, 0) X(12, 16, 0) X(16, 32, 0) X(20, 64, 32) X(24, 96, 64) X(28, 128, 64)        \
-    X(32, 160, 96) X(36, 192, 96) X(40, 224, 128) X(44, 256, 128) X(48, 320, 160) X(56, 416, 224)     \
-    X(64, 544, 288) X(80, 832, 416) X(96, 1024, 0) X(112, 1024, 0)
+    X(4, 4, 0, 0) X(8, 8, 0, 0) X(12, 16, 0, 0) X(16, 32, 0, 0) X(20, 64, 32, 0) X(24, 96, 64, 64)   \
+    X(28, 128, 64, 96) X(32, 160, 96, 96) X(36, 192, 96, 128) X(40, 224, 128, 160)                  \
+    X(44, 256, 128, 160) X(48, 320, 160, 192) X(56, 416, 224, 224) X(64, 544, 288, 256)             \
+    X(80, 832, 416, 0) X(96, 1024, 0, 0) X(112, 1024, 0, 0)
 
 // Opt-in shared memory per CTA on this architecture (227 KB).
 constexpr size_t CONE_SMEM_MAX = 232448;
@@ -806,17 +926,37 @@ constexpr int thr_minb() {
     return m < 1 ? 1 : (m > 16 ? 16 : m);
 }
 
+// Resident CTAs of a register-V variant: as many as the shared memory holds
+// while every thread keeps CP + 48 registers (the V column or the A-thread's
+// round plan, both live through the sweeps).  Each of the four SM
+// sub-partitions has 16384 registers for the warps it holds.
+template <typename T, int CP, int G>
+constexpr int rv_minb() {
+    using Cfg = ConeCfg<T, CP, G>;
+    const int regs = (CP + 48 + 7) / 8 * 8;
+    const int warps_per_smsp = 16384 / (32 * regs);
+    const int by_regs = 4 * warps_per_smsp / (Cfg::NTH / 32);
+    const int by_smem = (int)(CONE_SMEM_MAX / Cfg::smem);
+    const int m = by_smem < by_regs ? by_smem : by_regs;
+    return m < 1 ? 1 : (m > 16 ? 16 : m);
+}
+
+template <typename T, int GR>
+constexpr bool has_rv() {
+    return GR > 0 && sizeof(T) == 4;
+}
+
 // Device limits read by cone_prepare: opt-in shared memory per CTA, SMs.
 static int g_smem_optin = 0;
 static int g_num_sms = 0;
 
-template <typename T, int CP, int G, int MB, bool ST>
+template <typename T, int CP, int G, int MB, bool ST, bool VR>
 static cudaError_t allow_smem(int bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(k_cone<T, CP, G, MB, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return cudaFuncSetAttribute(k_cone<T, CP, G, MB, ST, VR>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-template <typename T, int CP, int G, int GT>
+template <typename T, int CP, int G, int GT, int GR>
 static int prepare_one() {
     if constexpr (!cone_fits<T, CP, G>()) {
         return HSDE_OK;                                          // never used in this precision
@@ -825,13 +965,20 @@ static int prepare_one() {
         // one clique per CTA: allowed the whole opt-in shared memory, which a
         // launch asks for when the bucket has few cliques (a CTA alone on its SM)
         const int want = Cfg::GPB == 1 ? std::max<int>(g_smem_optin, (int)Cfg::smem) : (int)Cfg::smem;
-        if (allow_smem<T, CP, G, Cfg::MINB, true>(want) != cudaSuccess) return HSDE_ECUDA;
+        if (allow_smem<T, CP, G, Cfg::MINB, true, false>(want) != cudaSuccess) return HSDE_ECUDA;
         if constexpr (Cfg::GPB == 1 && CP >= 32 && Cfg::MINB != 1) {
-            if (allow_smem<T, CP, G, 1, true>(want) != cudaSuccess) return HSDE_ECUDA;
+            if (allow_smem<T, CP, G, 1, true, false>(want) != cudaSuccess) return HSDE_ECUDA;
         }
         if constexpr (GT > 0) {
             if constexpr (cone_fits<T, CP, GT>()) {
-                if (allow_smem<T, CP, GT, thr_minb<T, CP, GT>(), false>((int)ConeCfg<T, CP, GT>::smem) !=
+                if (allow_smem<T, CP, GT, thr_minb<T, CP, GT>(), false, false>((int)ConeCfg<T, CP, GT>::smem) !=
+                    cudaSuccess)
+                    return HSDE_ECUDA;
+            }
+        }
+        if constexpr (has_rv<T, GR>()) {
+            if constexpr (cone_fits<T, CP, GR>()) {
+                if (allow_smem<T, CP, GR, rv_minb<T, CP, GR>(), false, true>((int)ConeCfg<T, CP, GR>::smem) !=
                     cudaSuccess)
                     return HSDE_ECUDA;
             }
@@ -854,7 +1001,19 @@ static bool alone_one(const Bucket& bk) {
     }
 }
 
-template <typename T, int CP, int G, int GT>
+template <typename T, int CP, int G, int GT, int GR>
+static bool has_variant(int v) {
+    if constexpr (!cone_fits<T, CP, G>()) {
+        return false;
+    } else {
+        if (v == 0) return true;
+        if (v == 1) return GT > 0 && cone_fits<T, CP, (GT > 0 ? GT : G)>();
+        if (v == 2) return has_rv<T, GR>() && cone_fits<T, CP, (GR > 0 ? GR : G)>();
+        return false;
+    }
+}
+
+template <typename T, int CP, int G, int GT, int GR>
 static int launch_one(const DevView& V, const Bucket& bk, int max_sweeps, double tol, int warm, int refresh,
                       int dry, cudaStream_t st) {
     if constexpr (!cone_fits<T, CP, G>()) {
@@ -867,7 +1026,17 @@ static int launch_one(const DevView& V, const Bucket& bk, int max_sweeps, double
                 if (bk.variant == 1) {
                     using CT = ConeCfg<T, CP, GT>;
                     const int grid = (bk.count + CT::GPB - 1) / CT::GPB;
-                    k_cone<T, CP, GT, thr_minb<T, CP, GT>(), false><<<grid, CT::NTH, CT::smem, st>>>(
+                    k_cone<T, CP, GT, thr_minb<T, CP, GT>(), false, false><<<grid, CT::NTH, CT::smem, st>>>(
+                        V, bk.list, bk.count, max_sweeps, tol2, warm, refresh, dry);
+                    return HSDE_OK;
+                }
+            }
+        }
+        if constexpr (has_rv<T, GR>()) {
+            if constexpr (cone_fits<T, CP, GR>()) {
+                if (bk.variant == 2) {
+                    using CR = ConeCfg<T, CP, GR>;
+                    k_cone<T, CP, GR, rv_minb<T, CP, GR>(), false, true><<<bk.count, CR::NTH, CR::smem, st>>>(
                         V, bk.list, bk.count, max_sweeps, tol2, warm, refresh, dry);
                     return HSDE_OK;
                 }
@@ -877,20 +1046,20 @@ static int launch_one(const DevView& V, const Bucket& bk, int max_sweeps, double
         if constexpr (Cfg::GPB == 1 && CP >= 32 && Cfg::MINB != 1) {
             // a CTA alone on its SM: the variant with the full register budget
             if (alone_one<T, CP, G>(bk)) {
-                k_cone<T, CP, G, 1, true><<<grid, Cfg::NTH, (size_t)g_smem_optin, st>>>(
+                k_cone<T, CP, G, 1, true, false><<<grid, Cfg::NTH, (size_t)g_smem_optin, st>>>(
                     V, bk.list, bk.count, max_sweeps, tol2, warm, refresh, dry);
                 return HSDE_OK;
             }
         }
         const size_t smem = alone_one<T, CP, G>(bk) ? (size_t)g_smem_optin : Cfg::smem;
-        k_cone<T, CP, G, Cfg::MINB, true><<<grid, Cfg::NTH, smem, st>>>(V, bk.list, bk.count, max_sweeps, tol2,
-                                                                         warm, refresh, dry);
+        k_cone<T, CP, G, Cfg::MINB, true, false><<<grid, Cfg::NTH, smem, st>>>(V, bk.list, bk.count, max_sweeps,
+                                                                                tol2, warm, refresh, dry);
         return HSDE_OK;
     }
 }
 
 int cone_bucket_of(int c, bool mixed) {
-#define X(cp, g, gt) \
+#define X(cp, g, gt, gr) \
     if (c <= cp && (mixed ? cone_fits<float, cp, g>() : cone_fits<double, cp, g>())) return cp;
     HSDE_CONE_BUCKETS(X)
 #undef X
@@ -899,7 +1068,7 @@ int cone_bucket_of(int c, bool mixed) {
 
 int cone_max_clique(bool mixed) {
     int mx = 0;
-#define X(cp, g, gt) \
+#define X(cp, g, gt, gr) \
     if (mixed ? cone_fits<float, cp, g>() : cone_fits<double, cp, g>()) mx = cp;
     HSDE_CONE_BUCKETS(X)
 #undef X
@@ -908,20 +1077,19 @@ int cone_max_clique(bool mixed) {
 
 void cone_bucket_sizes(std::vector<int>& out, bool mixed) {
     out.clear();
-#define X(cp, g, gt) \
+#define X(cp, g, gt, gr) \
     if (mixed ? cone_fits<float, cp, g>() : cone_fits<double, cp, g>()) out.push_back(cp);
     HSDE_CONE_BUCKETS(X)
 #undef X
 }
 
-int cone_variants(int cmax, bool mixed) {
-#define X(cp, g, gt)                                                                                  \
-    if (cmax == cp)                                                                                   \
-        return (gt > 0 && (mixed ? cone_fits<float, cp, (gt > 0 ? gt : g)>()                          \
-                                 : cone_fits<double, cp, (gt > 0 ? gt : g)>())) ? 2 : 1;
+bool cone_has_variant(int cmax, bool mixed, int variant) {
+#define X(cp, g, gt, gr)                                                                            \
+    if (cmax == cp)                                                                                 \
+        return mixed ? has_variant<float, cp, g, gt, gr>(variant) : has_variant<double, cp, g, gt, gr>(variant);
     HSDE_CONE_BUCKETS(X)
 #undef X
-    return 0;
+    return false;
 }
 
 int cone_vstore_elems(int c, bool mixed) {
@@ -936,15 +1104,15 @@ int cone_prepare(bool mixed) {
         cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return HSDE_ECUDA;
     int rc = HSDE_OK;
-#define X(cp, g, gt) \
-    rc |= mixed ? prepare_one<float, cp, g, gt>() : prepare_one<double, cp, g, gt>();
+#define X(cp, g, gt, gr) \
+    rc |= mixed ? prepare_one<float, cp, g, gt, gr>() : prepare_one<double, cp, g, gt, gr>();
     HSDE_CONE_BUCKETS(X)
 #undef X
     return rc == HSDE_OK ? HSDE_OK : HSDE_ECUDA;
 }
 
 int cone_smem_bytes(int cmax, bool mixed) {
-#define X(cp, g, gt) \
+#define X(cp, g, gt, gr) \
     if (cmax == cp) return mixed ? (int)ConeCfg<float, cp, g>::smem : (int)ConeCfg<double, cp, g>::smem;
     HSDE_CONE_BUCKETS(X)
 #undef X
@@ -952,7 +1120,7 @@ int cone_smem_bytes(int cmax, bool mixed) {
 }
 
 bool cone_bucket_alone(const Bucket& bk, bool mixed) {
-#define X(cp, g, gt) \
+#define X(cp, g, gt, gr) \
     if (bk.cmax == cp) return mixed ? alone_one<float, cp, g>(bk) : alone_one<double, cp, g>(bk);
     HSDE_CONE_BUCKETS(X)
 #undef X
@@ -963,10 +1131,10 @@ int launch_cone(const DevView& V, const Bucket& bk, bool mixed, int max_sweeps, 
                 void* stp, int dry) {
     if (bk.count == 0) return HSDE_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stp);
-#define X(cp, g, gt)                                                                                   \
-    if (bk.cmax == cp) {                                                                               \
-        return mixed ? launch_one<float, cp, g, gt>(V, bk, max_sweeps, tol, warm, refresh, dry, st)   \
-                     : launch_one<double, cp, g, gt>(V, bk, max_sweeps, tol, warm, refresh, dry, st); \
+#define X(cp, g, gt, gr)                                                                                   \
+    if (bk.cmax == cp) {                                                                                   \
+        return mixed ? launch_one<float, cp, g, gt, gr>(V, bk, max_sweeps, tol, warm, refresh, dry, st)   \
+                     : launch_one<double, cp, g, gt, gr>(V, bk, max_sweeps, tol, warm, refresh, dry, st); \
     }
     HSDE_CONE_BUCKETS(X)
 #undef X

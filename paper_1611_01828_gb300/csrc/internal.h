@@ -220,7 +220,7 @@ constexpr int MAX_BUCKETS = 20;
 struct Bucket {
     int32_t cmax;            // padded size CP of the bucket (4 ... 112)
     int32_t count;
-    int32_t variant;         // 0: latency variant, 1: throughput variant (cone.cu)
+    int32_t variant;         // 0 latency, 1 throughput, 2 register-V variant (cone.cu)
     int32_t* list;           // device array of clique ids (largest first)
 };
 
@@ -267,8 +267,9 @@ void launch_state_products(const DevView& V, int r0, int r1, int64_t e0, int64_t
 // max_sweeps sweeps, no global writes)
 int  launch_cone(const DevView& V, const Bucket& bk, bool mixed, int max_sweeps, double tol,
                  int warm, int refresh, void* st, int dry = 0);
-// variants of a bucket size in a precision (1 or 2)
-int  cone_variants(int cmax, bool mixed);
+// whether a bucket size has eigensolver variant 0 (latency), 1 (throughput)
+// or 2 (register-V) in a precision
+bool cone_has_variant(int cmax, bool mixed, int variant);
 int  cone_smem_bytes(int cmax, bool mixed);
 // padded size of the bucket of a clique of size c in a precision, -1 if none
 int  cone_bucket_of(int c, bool mixed);
