@@ -487,6 +487,7 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
     static_assert(!VR || (G > 32 && GA >= 32 && GA % 32 == 0), "register-V: whole warps of each kind");
     // the round plan's configuration: the A-threads' (all threads without VR)
     using PCfg = ConeCfg<T, CP, VR ? GA : G>;
+    static_assert(PCfg::LD == Cfg::LD, "the plan indexes the buffers with their row stride");
     using V2 = typename Vec2<T>::type;
     constexpr int LD = Cfg::LD, K = Cfg::K;
     constexpr int EPT = (CP * (CP + 1) / 2 + G - 1) / G;   // lower entries per thread
