@@ -419,19 +419,22 @@ __device__ __forceinline__ void jacobi_round_rv(const RoundPlan<PCfg>& pl, const
 // the entry and gx = (H_k x_hat) of it: a = alpha s_hat + (1-alpha) s - z,
 // the new v = alpha v_hat + (1-alpha) v, and hx = (H_k x_new) of it.  alpha
 // is uniform over the launch, so the branch does not diverge; alpha = 1
-// reads nothing more.
-__device__ __forceinline__ void cone_inputs(double so, double zo, double vo, double gx, double al,
-                                            const double* __restrict__ x, int gi, double& av, double& vn,
-                                            double& hx) {
-    if (al == 1.0) {
-        av = 0.5 * (so - zo - vo + gx);
-        vn = 0.5 * (so + zo + vo - gx);
+// reads nothing more.  In the clique's precision C: s, z, v are stored in
+// it and a is projected in it; gx is formed in FP64 by the caller (x_w and
+// eta x_p can nearly cancel).  On this GPU FP64 runs at 1/64 of the FP32
+// rate, so the mixed form keeps these per-entry terms off the FP64 pipe.
+template <typename C>
+__device__ __forceinline__ void cone_inputs(C so, C zo, C vo, C gx, C al, const double* __restrict__ x, int gi,
+                                            C& av, C& vn, C& hx) {
+    if (al == C(1)) {
+        av = C(0.5) * (so - zo - vo + gx);
+        vn = C(0.5) * (so + zo + vo - gx);
         hx = gx;
     } else {
-        const double sh = 0.5 * (so + zo - vo + gx);
-        av = al * sh + (1.0 - al) * so - zo;
-        vn = al * 0.5 * (so + zo + vo - gx) + (1.0 - al) * vo;
-        hx = al * gx + (1.0 - al) * x[gi];
+        const C sh = C(0.5) * (so + zo - vo + gx);
+        av = al * sh + (C(1) - al) * so - zo;
+        vn = al * C(0.5) * (so + zo + vo - gx) + (C(1) - al) * vo;
+        hx = al * gx + (C(1) - al) * (C)x[gi];
     }
 }
 
@@ -544,7 +547,7 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
     // issued here too.
     int apos[STASH ? EPT : 1];   // arow * LD + bcol; -1: no entry
     unsigned diag_bits = 0u;
-    double avs[STASH ? EPT : 1], gxs[STASH ? EPT : 1];
+    T avs[STASH ? EPT : 1], gxs[STASH ? EPT : 1];
     T vns[STASH ? EPT : 1];
     int gi[STASH ? EPT : 1];
     T so[STASH ? EPT : 1], zo[STASH ? EPT : 1], vo[STASH ? EPT : 1];
@@ -582,12 +585,11 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
         for (int q = 0; q < EPT; ++q) {
             if (apos[q] < 0) continue;
             const double gx = V.xw[gi[q]] - eta * V.xp[gi[q]];
-            const double so_ = so[q], zo_ = zo[q], vo_ = vo[q];
-            double av, vn, hx;
-            cone_inputs(so_, zo_, vo_, gx, al, V.x, gi[q], av, vn, hx);
+            T av, vn, hx;
+            cone_inputs<T>(so[q], zo[q], vo[q], (T)gx, (T)al, V.x, gi[q], av, vn, hx);
             gxs[q] = hx;
             avs[q] = av;
-            vns[q] = (T)vn;
+            vns[q] = vn;
             const int arow = apos[q] / LD, b = apos[q] - (apos[q] / LD) * LD;
             const T a = dry ? dry_entry<T>(k, arow, b) : (T)av;
             A0[apos[q]] = a;
@@ -600,8 +602,8 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
             const int arow = b + (e - (b * c - b * (b - 1) / 2));
             const int gi = V.gmap[off + e];
             const double gx = V.xw[gi] - eta * V.xp[gi];
-            double av, vn, hx;
-            cone_inputs((double)s[off + e], (double)z[off + e], (double)v[off + e], gx, al, V.x, gi, av, vn, hx);
+            T av, vn, hx;
+            cone_inputs<T>(s[off + e], z[off + e], v[off + e], (T)gx, (T)al, V.x, gi, av, vn, hx);
             const T a = dry ? dry_entry<T>(k, arow, b) : (T)av;
             A0[arow * LD + b] = a;
             A0[b * LD + arow] = a;
@@ -829,24 +831,24 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
     gsync<G>(gid);
 
     // each lower entry's contributions to ||H_k x - s_k||^2 and ||s_k||^2 go
-    // to the free buffers A and Vn (nlow doubles each fit: LD > c) and are
+    // to the free buffers A and Vn (nlow values each fit: LD > c) and are
     // summed in a fixed order
-    double* cres = reinterpret_cast<double*>(A);
-    double* csres = reinterpret_cast<double*>(Vn);
+    T* cres = A;
+    T* csres = Vn;
     if constexpr (STASH) {
 #pragma unroll
         for (int q = 0; q < EPT; ++q) {
             if (apos[q] < 0) continue;
             const int e = lane + q * G;
             const int64_t j = off + e;
-            const double sn = (double)An[apos[q]];
+            const T sn = An[apos[q]];
             if (!dry) {
-                s[j] = (T)sn;
-                z[j] = (T)(sn - avs[q]);
+                s[j] = sn;
+                z[j] = sn - avs[q];
                 v[j] = vns[q];
             }
-            const double d = gxs[q] - sn;
-            const double w = (diag_bits >> q) & 1u ? 1.0 : 2.0;
+            const T d = gxs[q] - sn;
+            const T w = (diag_bits >> q) & 1u ? T(1) : T(2);
             cres[e] = w * d * d;
             csres[e] = w * sn * sn;
         }
@@ -855,25 +857,25 @@ k_cone(DevView V, const int32_t* __restrict__ list, int nlist, int max_sweeps, T
             const int b = packed_column(e, c);
             const int arow = b + (e - (b * c - b * (b - 1) / 2));
             const int64_t j = off + e;
-            const double sn = (double)An[arow * LD + b];
+            const T sn = An[arow * LD + b];
             const int gi = V.gmap[j];
             const double gx = V.xw[gi] - eta * V.xp[gi];
-            double av, vn, hx;
-            cone_inputs((double)s[j], (double)z[j], (double)v[j], gx, al, V.x, gi, av, vn, hx);
+            T av, vn, hx;
+            cone_inputs<T>(s[j], z[j], v[j], (T)gx, (T)al, V.x, gi, av, vn, hx);
             if (!dry) {
-                s[j] = (T)sn;
-                z[j] = (T)(sn - av);
-                v[j] = (T)vn;
+                s[j] = sn;
+                z[j] = sn - av;
+                v[j] = vn;
             }
-            const double d = hx - sn;
-            const double w = arow == b ? 1.0 : 2.0;
+            const T d = hx - sn;
+            const T w = arow == b ? T(1) : T(2);
             cres[e] = w * d * d;
             csres[e] = w * sn * sn;
         }
     }
     gsync<G>(gid);
-    const double res = fixed_sum<G, RW>(cres, nlow, reinterpret_cast<double*>(red), gid);
-    const double sres = fixed_sum<G, RW>(csres, nlow, reinterpret_cast<double*>(red), gid);
+    const double res = (double)fixed_sum<G, RW>(cres, nlow, red, gid);
+    const double sres = (double)fixed_sum<G, RW>(csres, nlow, red, gid);
     if (lane == 0 && !dry) {
         V.cl_part[2 * k] = res;
         V.cl_part[2 * k + 1] = sres;

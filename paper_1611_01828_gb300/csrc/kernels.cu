@@ -443,7 +443,12 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
     const double ot = I.tau + I.kappa;            // omega_tau of the next iteration
     const double al = V.alpha;
     const bool relax = al != 1.0;
-    double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    // Stopping-rule partial sums of this tile in PS: FP32 in the mixed form
+    // (each is tested to ~1e-4 and the differences inside them, r - tau c and
+    // A x - tau b, are formed in FP64 first), FP64 in the FP64 form; the
+    // tiles' partials are added in FP64 by the last CTA.
+    using PS = T;
+    PS a1 = PS(0), a2 = PS(0), a3 = PS(0);
     // ||A^T y||^2, ||H^T z||^2, ||H x||^2 for the certificate cancellation
     // test, which compares them with 1e-2 only: accumulated in FP32
     float a4 = 0.f, a5 = 0.f, a6 = 0.f;
@@ -497,11 +502,12 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
         }
         if (check) {
             const double r = hz + aty;
-            const double w = V.diag[e] ? 1.0 : 2.0;
             const double d = r - tau * ce;
-            a1 += w * d * d;
-            a2 += w * r * r;
-            a3 += w * ce * x;
+            const PS w = V.diag[e] ? PS(1) : PS(2);
+            const PS pd = (PS)d, pr = (PS)r;
+            a1 += w * pd * pd;
+            a2 += w * pr * pr;
+            a3 += w * (PS)ce * (PS)x;
             const float fw = (float)w, fa = (float)aty, fh = (float)hz, fx = (float)x;
             a4 += fw * fa * fa;
             a5 += fw * fh * fh;
@@ -513,7 +519,7 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
     //   A x_w = A f + A Delta^{-1} A^T y_w = A f + (S - I) y_w = A f + q - y_w,
     //   A x_p = -b - y_p  (the same identity on the setup solve),
     // so A x_hat = A x_w - eta A x_p from values this step already has.
-    double b1 = 0.0, b2 = 0.0, b3 = 0.0;
+    PS b1 = PS(0), b2 = PS(0), b3 = PS(0);
     bool has_rows;
     {
         const int nt = I.tile_end - I.tile_begin, ti = blockIdx.x - I.tile_begin;
@@ -535,32 +541,43 @@ __global__ void __launch_bounds__(NT) k_post(DevView V) {
                     V.ax[row] = ax;
                 }
                 if (check) {
-                    const double w2 = V.dinv2[row];
-                    const double d = ax - tau * bi;
-                    b1 += w2 * d * d;
-                    b2 += w2 * ax * ax;
-                    b3 += bi * ynew;
+                    const PS w2 = (PS)V.dinv2[row];
+                    const PS pd = (PS)(ax - tau * bi), pa = (PS)ax;
+                    b1 += w2 * pd * pd;
+                    b2 += w2 * pa * pa;
+                    b3 += (PS)bi * (PS)ynew;
                 }
             }
             V.y[row] = ynew;
         }
     }
     if (check) {
-        // FP64 pipe time is what this kernel spends: the three N-space sums
-        // in FP64, the cancellation sums (compared with 1e-2 only) in FP32,
-        // and the constraint-space sums only in tiles that hold constraints
-        double v3[3] = {a1, a2, a3};
-        block_sum_t<3>(v3, stage);
-        float f3[3] = {a4, a5, a6};
-        block_sum_t<3>(f3, reinterpret_cast<float*>(stage));
-        double w3[3] = {b1, b2, b3};
-        if (has_rows) block_sum_t<3>(w3, stage);
-        if (threadIdx.x == 0) {
-            double* pp = V.part + (int64_t)blockIdx.x * KPART;
-            const double out9[9] = {v3[0], v3[1], v3[2], w3[0], w3[1], w3[2],
-                                    (double)f3[0], (double)f3[1], (double)f3[2]};
+        double* pp = V.part + (int64_t)blockIdx.x * KPART;
+        if constexpr (sizeof(PS) == 4) {
+            // the mixed form: one FP32 reduction of all nine
+            float v9[9] = {a1, a2, a3, b1, b2, b3, a4, a5, a6};
+            block_sum_t<9>(v9, reinterpret_cast<float*>(stage));
+            if (threadIdx.x == 0) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) pp[1 + i] = out9[i];
+                for (int i = 0; i < 9; ++i) pp[1 + i] = (double)v9[i];
+            }
+        } else {
+            // FP64 pipe time is what this kernel spends: the three N-space
+            // sums in FP64, the cancellation sums (compared with 1e-2 only)
+            // in FP32, and the constraint-space sums only in tiles that hold
+            // constraints
+            double v3[3] = {a1, a2, a3};
+            block_sum_t<3>(v3, stage);
+            float f3[3] = {a4, a5, a6};
+            block_sum_t<3>(f3, reinterpret_cast<float*>(stage));
+            double w3[3] = {b1, b2, b3};
+            if (has_rows) block_sum_t<3>(w3, stage);
+            if (threadIdx.x == 0) {
+                const double out9[9] = {v3[0], v3[1], v3[2], w3[0], w3[1], w3[2],
+                                        (double)f3[0], (double)f3[1], (double)f3[2]};
+#pragma unroll
+                for (int i = 0; i < 9; ++i) pp[1 + i] = out9[i];
+            }
         }
     }
     if (!last_cta(V.counters + 2 * t.x + 1, I.tile_end - I.tile_begin, &flag)) return;
