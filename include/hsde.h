@@ -58,8 +58,10 @@ extern "C" {
 #define HSDE_ECUDA    (-3)   /* CUDA runtime error (no device, launch, ...)  */
 #define HSDE_ESTATE   (-4)   /* query does not match the instance's verdict */
 #define HSDE_ERANGE   (-5)   /* size beyond what this build supports (cliques
-                                larger than 112 in HSDE_MIXED or 80 in HSDE_FP64,
-                                totals beyond int32 indexing) */
+                                larger than 1024; cliques above 112 in
+                                HSDE_MIXED or 80 in HSDE_FP64 in
+                                hsde_unrolled_forward; totals beyond int32
+                                indexing) */
 
 /* per-instance iteration status (readings of the paper's stopping rule) */
 #define HSDE_RUNNING            0
@@ -187,7 +189,8 @@ typedef struct hsde_profile {
     int64_t phase_units[HSDE_MAX_PHASES];  /* work units of the phase: pattern
                                               entries (affine, check) or
                                               sum_k c_k^3 (cone buckets)        */
-    double  sweeps_mean;  /* Jacobi sweeps per clique in the last iteration      */
+    double  sweeps_mean;  /* Jacobi sweeps per clique in the last iteration (QR
+                             path: QR steps per eigenvalue, rounded up)        */
     int32_t sweeps_max;
     int32_t _pad;
     int32_t phase_sweeps_max[HSDE_MAX_PHASES];  /* cone phases: most sweeps any
@@ -291,8 +294,12 @@ HSDE_API int  hsde_get_certificate(hsde_handle* h, int32_t i, int32_t kind, doub
  * profile = 1, the device time of each phase of the last iteration (waits
  * for the handle's stream).  Phases: "affine" (A f, S^{-1}, A^T y_w, eta),
  * one "cone_cK" per clique bucket (cliques of size <= K, each on its own
- * graph branch), "post" (x update, stopping rule, verdict and the next
- * right-hand side) and "iteration" (all of it). */
+ * graph branch), "cone_qr" for the cliques above the Jacobi sizes (112 in
+ * HSDE_MIXED, 80 in HSDE_FP64; up to 1024): Householder tridiagonalisation,
+ * implicit QR with the Wilkinson shift and a split-precision TF32
+ * tensor-core rebuild in HSDE_MIXED, one CTA per clique; its sweeps count
+ * QR steps per eigenvalue, rounded up), "post" (x update, stopping rule,
+ * verdict and the next right-hand side) and "iteration" (all of it). */
 HSDE_API int  hsde_get_profile(hsde_handle* h, hsde_profile* out);
 
 /* In-place inverse of a dense m x m symmetric positive definite matrix held

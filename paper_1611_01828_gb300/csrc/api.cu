@@ -669,6 +669,21 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
             }
         }
     }
+    // workspaces of the cliques on the tridiagonal QR path (cone_large.cu)
+    std::vector<int64_t> hbigo;
+    int64_t bign = 0;
+    for (int32_t b = 0; b < B; ++b) {
+        const Symbolic& S = h->prep[b].S;
+        for (int32_t k = 0; k < S.p(); ++k) {
+            const int c = S.clique_ptr[k + 1] - S.clique_ptr[k];
+            if (cone_bucket_of(c, h->mixed) == CONE_BIG) {
+                hbigo.push_back(bign);
+                bign += cone_big_ws_elems(c);
+            } else {
+                hbigo.push_back(-1);
+            }
+        }
+    }
     const int64_t LIM = (int64_t)1 << 31;
     if (Ntot >= LIM || Ptot >= LIM || nnzA >= LIM || Mtot >= LIM || scn >= LIM)
         return fail(HSDE_ERANGE, "problem totals exceed int32 indexing");
@@ -707,6 +722,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
                  o_sd = cv.take<double>(Mtot), o_sinv = cv.take<double>(sinv);
     size_t o_s = cv.take<char>(Ptot * Tsz), o_z = cv.take<char>(Ptot * Tsz), o_v = cv.take<char>(Ptot * Tsz);
     const size_t o_vst = cv.take<char>(vsn * Tsz), o_vso = cv.take<int64_t>(hvso.size());
+    const size_t o_bigws = cv.take<char>(bign * Tsz), o_bigo = cv.take<int64_t>(hbigo.size());
     const size_t o_g = cv.take<int32_t>(Ptot), o_clo = cv.take<int32_t>(ncl), o_cls = cv.take<int32_t>(ncl),
                  o_cli = cv.take<int32_t>(ncl), o_inst = cv.take<InstDev>(B), o_tiles = cv.take<int4>(ntiles),
                  o_part = cv.take<double>(ntiles * KPART), o_clp = cv.take<double>(2 * ncl),
@@ -754,6 +770,8 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     V.s = ar + o_s; V.z = ar + o_z; V.v = ar + o_v;
     V.vstore = h->warm ? (void*)(ar + o_vst) : nullptr;
     V.vs_off = (const int64_t*)(ar + o_vso);
+    V.big_ws = bign > 0 ? (void*)(ar + o_bigws) : nullptr;
+    V.big_off = (const int64_t*)(ar + o_bigo);
     V.gmap = (const int32_t*)(ar + o_g); V.cl_off = (const int32_t*)(ar + o_clo);
     V.cl_size = (const int32_t*)(ar + o_cls); V.cl_inst = (const int32_t*)(ar + o_cli);
     V.inst = (InstDev*)(ar + o_inst); V.tiles = (const int4*)(ar + o_tiles);
@@ -849,7 +867,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
     UP(o_sscp, hsscp); UP(o_ssci, hssci); UP(o_lid, hlid); UP(o_le, hle); UP(o_linst, hlinst);
     UP(o_atp, hatp); UP(o_atc, hatc); UP(o_atv, hAtv); UP(o_b, hb); UP(o_ap, hap); UP(o_ac, hac);
     UP(o_av, hAv); UP(o_ri, hri); UP(o_sd, hsd); UP(o_g, hg); UP(o_clo, hclo); UP(o_cls, hcls);
-    UP(o_cli, hcli); UP(o_vso, hvso); UP(o_dinv2, hdinv2);
+    UP(o_cli, hcli); UP(o_vso, hvso); UP(o_bigo, hbigo); UP(o_dinv2, hdinv2);
     {
         // structured factors: per-row block data with absolute indices, pools
         std::vector<int64_t> hbr(Mtot, 0);
@@ -1473,7 +1491,8 @@ int hsde_get_profile(hsde_handle* h, hsde_profile* out) {
     if ((rc = put("affine", h->ev_it0, h->ev_aff, h->V.Ntot)) != HSDE_OK) return rc;
     for (size_t i = 0; i < h->buckets.size(); ++i) {
         char nm[24];
-        std::snprintf(nm, sizeof(nm), "cone_c%d", h->buckets[i].cmax);
+        if (h->buckets[i].cmax == CONE_BIG) std::snprintf(nm, sizeof(nm), "cone_qr");
+        else std::snprintf(nm, sizeof(nm), "cone_c%d", h->buckets[i].cmax);
         if ((rc = put(nm, h->ev_cs[i], h->ev_ce[i], h->bucket_c3[i])) != HSDE_OK) return rc;
     }
     if ((rc = put("post", h->ev_chk, h->ev_it1, h->V.Ntot)) != HSDE_OK) return rc;
@@ -1709,6 +1728,11 @@ int hsde_unrolled_forward(hsde_handle* h, int32_t K, int32_t ckpt, double* x, do
     if (K < 1 || ckpt < 1) return fail(HSDE_EINVAL, "K and ckpt must be positive");
     if (h->opt.alpha != 1.0 || h->opt.scaling != 0)
         return fail(HSDE_EINVAL, "unrolled differentiation needs options alpha = 1 and scaling = 0");
+    for (const auto& bk : h->buckets)
+        if (bk.cmax == CONE_BIG)
+            return fail(HSDE_ERANGE, "unrolled differentiation takes cliques up to " +
+                                         std::to_string(cone_jacobi_max(h->mixed)) +
+                                         " (the Jacobi eigensolvers); this problem has larger ones");
     CK(cudaSetDevice(h->device));
     int rc;
     if ((rc = ensure_unroll_ws(h, K, ckpt)) != HSDE_OK) return rc;

@@ -39,6 +39,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "cone_common.cuh"
 #include "internal.h"
 
 namespace hsde {
@@ -413,40 +414,6 @@ __device__ __forceinline__ void jacobi_round_rv(const RoundPlan<PCfg>& pl, const
         vr[cycle_slot<CP>(0)] = last;
     }
     gsync<GT>(gid);
-}
-
-// The point projected for one packed entry, from the previous s, z, v of
-// the entry and gx = (H_k x_hat) of it: a = alpha s_hat + (1-alpha) s - z,
-// the new v = alpha v_hat + (1-alpha) v, and hx = (H_k x_new) of it.  alpha
-// is uniform over the launch, so the branch does not diverge; alpha = 1
-// reads nothing more.  In the clique's precision C: s, z, v are stored in
-// it and a is projected in it; gx is formed in FP64 by the caller (x_w and
-// eta x_p can nearly cancel).  On this GPU FP64 runs at 1/64 of the FP32
-// rate, so the mixed form keeps these per-entry terms off the FP64 pipe.
-template <typename C>
-__device__ __forceinline__ void cone_inputs(C so, C zo, C vo, C gx, C al, const double* __restrict__ x, int gi,
-                                            C& av, C& vn, C& hx) {
-    if (al == C(1)) {
-        av = C(0.5) * (so - zo - vo + gx);
-        vn = C(0.5) * (so + zo + vo - gx);
-        hx = gx;
-    } else {
-        const C sh = C(0.5) * (so + zo - vo + gx);
-        av = al * sh + (C(1) - al) * so - zo;
-        vn = al * C(0.5) * (so + zo + vo - gx) + (C(1) - al) * vo;
-        hx = al * gx + (C(1) - al) * (C)x[gi];
-    }
-}
-
-// Column of entry e in a packed lower column-major c x c block (column b
-// starts at b c - b (b - 1) / 2).
-__device__ __forceinline__ int packed_column(int e, int c) {
-    const float cc = 2.f * c + 1.f;
-    int b = (int)((cc - sqrtf(fmaxf(cc * cc - 8.f * e, 0.f))) * 0.5f);
-    b = max(0, min(b, c - 1));
-    while (b > 0 && b * c - b * (b - 1) / 2 > e) --b;
-    while (b + 1 < c && (b + 1) * c - (b + 1) * b / 2 <= e) ++b;
-    return b;
 }
 
 // Entry (i, j), i >= j, of the synthetic symmetric matrix of clique k that
@@ -1061,15 +1028,19 @@ static int launch_one(const DevView& V, const Bucket& bk, int max_sweeps, double
     }
 }
 
+// Cliques above the largest Jacobi bucket of a precision (and up to
+// CONE_BIG) go to the tridiagonal QR path of cone_large.cu.
 int cone_bucket_of(int c, bool mixed) {
 #define X(cp, g, gt, gr) \
     if (c <= cp && (mixed ? cone_fits<float, cp, g>() : cone_fits<double, cp, g>())) return cp;
     HSDE_CONE_BUCKETS(X)
 #undef X
-    return -1;
+    return c <= CONE_BIG ? CONE_BIG : -1;
 }
 
-int cone_max_clique(bool mixed) {
+int cone_max_clique(bool) { return CONE_BIG; }
+
+int cone_jacobi_max(bool mixed) {
     int mx = 0;
 #define X(cp, g, gt, gr) \
     if (mixed ? cone_fits<float, cp, g>() : cone_fits<double, cp, g>()) mx = cp;
@@ -1084,9 +1055,11 @@ void cone_bucket_sizes(std::vector<int>& out, bool mixed) {
     if (mixed ? cone_fits<float, cp, g>() : cone_fits<double, cp, g>()) out.push_back(cp);
     HSDE_CONE_BUCKETS(X)
 #undef X
+    out.push_back(CONE_BIG);
 }
 
 bool cone_has_variant(int cmax, bool mixed, int variant) {
+    if (cmax == CONE_BIG) return variant == 0;
 #define X(cp, g, gt, gr)                                                                            \
     if (cmax == cp)                                                                                 \
         return mixed ? has_variant<float, cp, g, gt, gr>(variant) : has_variant<double, cp, g, gt, gr>(variant);
@@ -1097,6 +1070,7 @@ bool cone_has_variant(int cmax, bool mixed, int variant) {
 
 int cone_vstore_elems(int c, bool mixed) {
     const int cp = cone_bucket_of(c, mixed);
+    if (cp == CONE_BIG) return 0;   // the QR path keeps no basis from one iteration to the next
     return cp < 0 ? -1 : cp * cp;
 }
 
@@ -1111,6 +1085,7 @@ int cone_prepare(bool mixed) {
     rc |= mixed ? prepare_one<float, cp, g, gt, gr>() : prepare_one<double, cp, g, gt, gr>();
     HSDE_CONE_BUCKETS(X)
 #undef X
+    rc |= cone_big_prepare(mixed);
     return rc == HSDE_OK ? HSDE_OK : HSDE_ECUDA;
 }
 
@@ -1123,6 +1098,7 @@ int cone_smem_bytes(int cmax, bool mixed) {
 }
 
 bool cone_bucket_alone(const Bucket& bk, bool mixed) {
+    if (bk.cmax == CONE_BIG) return true;   // one CTA per clique, launched first
 #define X(cp, g, gt, gr) \
     if (bk.cmax == cp) return mixed ? alone_one<float, cp, g>(bk) : alone_one<double, cp, g>(bk);
     HSDE_CONE_BUCKETS(X)
@@ -1133,6 +1109,7 @@ bool cone_bucket_alone(const Bucket& bk, bool mixed) {
 int launch_cone(const DevView& V, const Bucket& bk, bool mixed, int max_sweeps, double tol, int warm, int refresh,
                 void* stp, int dry) {
     if (bk.count == 0) return HSDE_OK;
+    if (bk.cmax == CONE_BIG) return dry ? HSDE_OK : launch_cone_big(V, bk, mixed, stp);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stp);
 #define X(cp, g, gt, gr)                                                                                   \
     if (bk.cmax == cp) {                                                                                   \

@@ -122,6 +122,8 @@ struct DevView {
     void* s; void* z; void* v;
     const int32_t* gmap;     // absolute x index per packed entry
     void* vstore;            // per-clique eigenbasis of the last solve (warm start), or null
+    void* big_ws;            // workspaces of the cliques on the tridiagonal QR path (cone_large.cu)
+    const int64_t* big_off;  // [ncl] offset of each such clique's workspace (elements), -1 otherwise
     const int64_t* vs_off;   // [ncl] offset of each clique's CP x CP basis in vstore
     const int32_t* cl_off; const int32_t* cl_size; const int32_t* cl_inst;
     // instances and tiles
@@ -215,10 +217,13 @@ void launch_lr_solve(const DevView& V, const double* qin, double* yout, double* 
 
 // Most eigensolver buckets (graph branches, side streams) of one handle.
 constexpr int MAX_BUCKETS = 20;
+// Bucket id (and largest clique) of the tridiagonal QR path that takes the
+// cliques above the Jacobi bucket sizes (cone_large.cu).
+constexpr int CONE_BIG = 1024;
 
 // Bucket of cliques handled by one eigensolver variant.
 struct Bucket {
-    int32_t cmax;            // padded size CP of the bucket (4 ... 112)
+    int32_t cmax;            // padded size CP of the bucket (4 ... 112), CONE_BIG for the QR path
     int32_t count;
     int32_t variant;         // 0 latency, 1 throughput, 2 register-V variant (cone.cu)
     int32_t* list;           // device array of clique ids (largest first)
@@ -274,10 +279,16 @@ int  cone_smem_bytes(int cmax, bool mixed);
 // padded size of the bucket of a clique of size c in a precision, -1 if none
 int  cone_bucket_of(int c, bool mixed);
 int  cone_max_clique(bool mixed);    // largest clique the eigensolvers of a precision take
+int  cone_jacobi_max(bool mixed);    // largest clique of the Jacobi buckets (above: the QR path)
 void cone_bucket_sizes(std::vector<int>& out, bool mixed);   // the precision's buckets, ascending
 int  cone_vstore_elems(int c, bool mixed);   // stored basis size for a clique of size c
 bool cone_bucket_alone(const Bucket& bk, bool mixed);   // its CTAs each take a whole SM (launched first)
 int  cone_prepare(bool mixed);
+// tridiagonal QR path (cone_large.cu): workspace elements of a clique of
+// size c, kernel attributes, and the launch of a CONE_BIG bucket
+int64_t cone_big_ws_elems(int c);
+int  cone_big_prepare(bool mixed);
+int  launch_cone_big(const DevView& V, const Bucket& bk, bool mixed, void* st);
 // reverse mode (unrolled.cu)
 void launch_apply(const DevView& V, const ApplyArgs& A, bool mixed, bool setup_only, void* st);
 int  rev_prepare(bool mixed);

@@ -19,7 +19,8 @@ RUNNING, SOLVED, PRIMAL_INFEASIBLE, DUAL_INFEASIBLE, MAX_ITER, NUMERICAL_ERROR =
 STATUS_NAMES = {0: "running", 1: "solved", 2: "primal_infeasible", 3: "dual_infeasible", 4: "max_iter",
                 5: "numerical_error"}
 FP64, MIXED = 0, 1
-MAX_CLIQUE = {FP64: 80, MIXED: 112}   # largest clique of each precision's eigensolvers (HSDE_ERANGE above)
+MAX_CLIQUE = {FP64: 1024, MIXED: 1024}   # largest clique of the eigensolvers (HSDE_ERANGE above)
+JACOBI_MAX = {FP64: 80, MIXED: 112}     # above: the tridiagonal QR path ("cone_qr")
 
 _i32p = C.POINTER(C.c_int32)
 _i64p = C.POINTER(C.c_int64)

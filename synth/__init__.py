@@ -16,6 +16,11 @@ and clique-size range):
 * ``maxcut_grid``     -- max-cut relaxation on an open R x K grid graph with
                          +-1 edge weights: C = weighted Laplacian, A_i = e_i e_i^T,
                          b = 1 (the maxG-type rows of Table 1).
+* ``box_qp``          -- SDP relaxation of a box-constrained QP on a random
+                         graph: X = diag(X1, S) with X1_ii + S_ii = 1 and
+                         C = [[L_w, 0], [0, 0]] (the qpG-type rows of Table 1:
+                         n = 2 n1, m = n1, singleton slack cliques plus the
+                         graph's chordal cliques, up to ~300 vertices).
 * ``make_primal_infeasible`` -- appends tr(X) = -1 (the infp-type row).
 * ``make_dual_infeasible``   -- tilts C along a PSD direction in the null
                          space of A (the infd-type row).
@@ -33,7 +38,7 @@ import numpy as np
 __all__ = [
     "Problem", "block_arrow", "maxcut_grid", "make_primal_infeasible",
     "make_dual_infeasible", "trace_one", "block_arrow_n50", "maxcut_grid_instance", "block_arrow_sweep",
-    "serving_batch", "differentiation_maxcut_grid", "rng_for",
+    "serving_batch", "differentiation_maxcut_grid", "rng_for", "box_qp", "box_qp_large_clique",
 ]
 
 
@@ -256,6 +261,43 @@ def maxcut_grid(R, K, rng, name=None):
                    dict(family="maxcut_grid", R=R, K=K))
 
 
+def box_qp(n1, E, rng, name=None):
+    """SDP relaxation of min x^T L_w x over x in [-1, 1]^n1 on a uniform random
+    graph with E edges (+-1 weights), the box written with slacks:
+    X = [[X1, .], [., S]] of size n = 2 n1, constraints X1_ii + S_ii = 1
+    (m = n1, b = 1), C = [[L_w, 0], [0, 0]].  X = I/2 is feasible and
+    X1_ii <= 1 bounds the objective.  The slack diagonal gives n1 singleton
+    cliques; the graph part gives the chordal cliques."""
+    n = 2 * n1
+    seen = set()
+    er, ec = [], []
+    while len(er) < E:
+        a, b = (int(t) for t in rng.integers(0, n1, 2))
+        if a == b:
+            continue
+        r, c = max(a, b), min(a, b)
+        if (r, c) in seen:
+            continue
+        seen.add((r, c))
+        er.append(r)
+        ec.append(c)
+    er = np.asarray(er, np.int32)
+    ec = np.asarray(ec, np.int32)
+    w = rng.choice(np.array([-1.0, 1.0]), size=E)
+    deg = np.zeros(n1)
+    np.add.at(deg, er, w)
+    np.add.at(deg, ec, w)
+    Cr = np.concatenate([np.arange(n1, dtype=np.int32), er])
+    Cc = np.concatenate([np.arange(n1, dtype=np.int32), ec])
+    Cv = np.concatenate([deg, -w])
+    C_row, C_col, C_val = _dedup_sum(Cr, Cc, Cv, n)
+    i = np.arange(n1, dtype=np.int32)
+    A_ptr = np.arange(0, 2 * n1 + 1, 2, dtype=np.int64)
+    A_row = np.stack([i, i + n1], 1).ravel().astype(np.int32)
+    return Problem(name or f"box_qp_n{n}_E{E}", n, n1, C_row, C_col, C_val, A_ptr, A_row, A_row.copy(),
+                   np.ones(2 * n1), np.ones(n1), "feasible", dict(family="box_qp", n1=n1, E=E))
+
+
 def trace_one(C_row, C_col, C_val, n, name="trace_one"):
     """min <C,X> s.t. tr X = 1, X psd; optimum lambda_min(C)."""
     idx = np.arange(n, dtype=np.int32)
@@ -396,3 +438,11 @@ def serving_batch(B=256, n_lo=100, n_hi=1500, seed_instance=0, select=None):
 def differentiation_maxcut_grid():
     """Differentiation workload: max-cut on the open 10 x 100 grid (n=1000)."""
     return maxcut_grid(10, 100, rng_for(4), name="maxcut_grid10x100_diff")
+
+
+def box_qp_large_clique(instance=0):
+    """qpG51-shaped large-clique workload (Table 1: n = 2000, m = 1000,
+    p = 1675, cliques 1-304): the box-QP relaxation on a random graph with
+    1000 vertices and 2700 edges, whose minimum-degree chordal extension has
+    cliques up to ~300."""
+    return box_qp(1000, 2700, rng_for(5, instance), name="box_qp_n2000_E2700")

@@ -377,12 +377,13 @@ def test_structured_factor_matches_dense_factor(hs, prec, tol):
 
 @pytest.mark.parametrize("prec,c", [("mixed", 100), ("mixed", 75), ("fp64", 75)])
 def test_large_cliques_one_step_from_random_state(hs, prec, c):
-    """Cliques above 64 (the FP32 buckets go to 112, the FP64 ones to 80):
-    one iteration from a random state against the oracle, element by element,
-    and the next clique size up is refused with HSDE_ERANGE."""
+    """Cliques above 64 on the Jacobi buckets (the FP32 buckets go to 112, the
+    FP64 ones to 80): one iteration from a random state against the oracle,
+    element by element."""
     p = synth.block_arrow(3, c - 5, 5, 6, np.random.default_rng(c))
     ref = ohsde.HSDE(p)
     assert max(len(k) for k in ref.V.st.cliques) == c
+    assert c <= hs.JACOBI_MAX[hs.FP64 if prec == "fp64" else hs.MIXED]
     state = random_state(ref, np.random.default_rng(9), f32=(prec == "mixed"))
     with hs.Handle(p, precision=prec) as H:
         H.hsde_set_state(0, state, 0)
@@ -392,11 +393,6 @@ def test_large_cliques_one_step_from_random_state(hs, prec, c):
     u0, nu0 = from_state(ref, state, sz)
     u1, nu1, _ = ref.step(u0, nu0)
     close(ref, got, to_state(ref, u1, nu1), 1e-8 if prec == "fp64" else 1e-4, f"c = {c}, {prec}")
-    mx = hs.MAX_CLIQUE[hs.FP64 if prec == "fp64" else hs.MIXED]
-    q = synth.block_arrow(2, mx + 1 - 5, 5, 4, np.random.default_rng(1))
-    with pytest.raises(hs.HSDEError) as ei:
-        hs.Handle(q, precision=prec)
-    assert ei.value.code == hs.HSDE_ERANGE
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
