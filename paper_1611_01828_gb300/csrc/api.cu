@@ -994,7 +994,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
             if (lists[t].empty()) continue;
             CK(cudaMemcpyAsync(dl + used, lists[t].data(), sizeof(int32_t) * lists[t].size(),
                                cudaMemcpyHostToDevice, st));
-            h->buckets.push_back(Bucket{caps[t], (int32_t)lists[t].size(), 0, dl + used});
+            h->buckets.push_back(Bucket{caps[t], (int32_t)lists[t].size(), 0, dl + used, hcls[lists[t][0]]});
             h->bucket_c3.push_back(c3[t]);
             h->bucket_ids.push_back(lists[t]);
             used += lists[t].size();

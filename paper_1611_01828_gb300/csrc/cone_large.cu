@@ -33,6 +33,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "cone_common.cuh"
 #include "internal.h"
@@ -44,25 +45,33 @@ namespace {
 constexpr int BIG_NT = 512;
 constexpr int BIG_WARPS = BIG_NT / 32;
 constexpr int BIG_CHASERS = 32;   // warp 0 chases; the other warps apply rotations
+constexpr int QR_SLOTS = 4;       // QR steps the chase may run ahead of their application
 
 template <typename T> struct QrEps;
 template <> struct QrEps<float> { static constexpr float value = 1.1920929e-7f; };     // 2^-23
 template <> struct QrEps<double> { static constexpr double value = 2.220446049250313e-16; };   // 2^-52
 
 // Sum over the CTA, in an order fixed by the thread count: a shuffle tree in
-// each warp, then the warp sums in warp order.  Every thread gets the result.
+// each warp, then warp 0 combines the warp sums by a shuffle tree and
+// publishes the total.  Every thread gets the result.  red holds
+// BIG_WARPS + 1 values of S.
 template <typename S>
 __device__ __forceinline__ S block_sum(S v, S* red) {
+    static_assert(BIG_WARPS <= 32, "one warp combines the warp sums");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     __syncthreads();   // red is free (an earlier block_sum has been read)
     if (lane == 0) red[warp] = v;
     __syncthreads();
-    S t = S(0);
+    if (warp == 0) {
+        S t = lane < BIG_WARPS ? red[lane] : S(0);
 #pragma unroll
-    for (int w = 0; w < BIG_WARPS; ++w) t += red[w];
-    return t;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) red[BIG_WARPS] = t;
+    }
+    __syncthreads();
+    return red[BIG_WARPS];
 }
 
 template <typename T>
@@ -97,76 +106,114 @@ __device__ __forceinline__ void givens(float x, float z, float& cs, float& sn, f
     }
 }
 __device__ __forceinline__ void givens(double x, double z, double& cs, double& sn, double& r) {
-    r = hypot(x, z);
-    cs = 1.0;
-    sn = 0.0;
-    if (r != 0.0) {
-        cs = x / r;
-        sn = z / r;
+    const double q = fma(x, x, z * z);
+    if (q > 1e-290 && q < 1e290) {
+        const double iq = rsqrt(q);
+        cs = x * iq;
+        sn = z * iq;
+        r = q * iq;
+    } else {
+        r = hypot(x, z);
+        cs = 1.0;
+        sn = 0.0;
+        if (r != 0.0) {
+            cs = x / r;
+            sn = z / r;
+        }
     }
 }
 
+// mbarrier helpers (CTA scope) for the chase / apply pipeline.  A wait
+// polls at most QR_WAIT_LIMIT times and reports failure instead of
+// waiting on.
+constexpr int QR_WAIT_LIMIT = 1 << 22;
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(b)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(b))
+                 : "memory");
+}
+// true once the phase of the given parity has completed
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(b);
+    for (int it = 0; it < QR_WAIT_LIMIT; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // out[r] = scale * sum_i M[r][i] vec[i] for rows r < L of the block at M
-// (row stride ld), columns i < L: a warp per group of four rows, so that a
-// lane has the loads of four rows in flight.
+// (row stride ld), columns i < L: a warp per group of RG rows, so that a
+// lane has the loads of RG rows in flight.
+constexpr int RG = 8;
+
 template <typename T>
 __device__ __forceinline__ void rows_matvec(const T* __restrict__ M, int ld, int L, const T* __restrict__ vec,
                                             T scale, T* __restrict__ out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int r0 = 4 * warp; r0 < L; r0 += 4 * BIG_WARPS) {
-        const int nr = L - r0 < 4 ? L - r0 : 4;
-        const T* m0 = M + (size_t)r0 * ld;
-        const T* m1 = m0 + (nr > 1 ? ld : 0);
-        const T* m2 = m0 + (nr > 2 ? 2 * (size_t)ld : 0);
-        const T* m3 = m0 + (nr > 3 ? 3 * (size_t)ld : 0);
-        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-#pragma unroll 2
-        for (int i = lane; i < L; i += 32) {
-            const T x0 = m0[i], x1 = m1[i], x2 = m2[i], x3 = m3[i];
-            const T vi = vec[i];
-            a0 += x0 * vi;
-            a1 += x1 * vi;
-            a2 += x2 * vi;
-            a3 += x3 * vi;
+    for (int r0 = RG * warp; r0 < L; r0 += RG * BIG_WARPS) {
+        const int nr = L - r0 < RG ? L - r0 : RG;
+        const T* mr[RG];
+        T a[RG];
+#pragma unroll
+        for (int q = 0; q < RG; ++q) {
+            mr[q] = M + (size_t)(r0 + (q < nr ? q : 0)) * ld;
+            a[q] = T(0);
         }
-        a0 = warp_sum(a0);
-        a1 = warp_sum(a1);
-        a2 = warp_sum(a2);
-        a3 = warp_sum(a3);
-        if (lane == 0) {
-            out[r0] = scale * a0;
-            if (nr > 1) out[r0 + 1] = scale * a1;
-            if (nr > 2) out[r0 + 2] = scale * a2;
-            if (nr > 3) out[r0 + 3] = scale * a3;
+        for (int i = lane; i < L; i += 32) {
+            T x[RG];
+#pragma unroll
+            for (int q = 0; q < RG; ++q) x[q] = mr[q][i];
+            const T vi = vec[i];
+#pragma unroll
+            for (int q = 0; q < RG; ++q) a[q] += x[q] * vi;
+        }
+#pragma unroll
+        for (int q = 0; q < RG; ++q) a[q] = warp_sum(a[q]);
+        if (lane < nr) {
+            T o = a[0];
+#pragma unroll
+            for (int q = 1; q < RG; ++q) o = lane == q ? a[q] : o;
+            out[r0 + lane] = scale * o;
         }
     }
 }
 
-// M[r][i] -= u[r] v[i] + (w ? w[r] x[i] : 0) for r, i < L: four rows of a
+// M[r][i] -= u[r] v[i] + (w ? w[r] x[i] : 0) for r, i < L: RG rows of a
 // warp at a time, loads first.
 template <typename T>
 __device__ __forceinline__ void rows_update(T* __restrict__ M, int ld, int L, const T* __restrict__ u,
                                             const T* __restrict__ vv, const T* __restrict__ w,
                                             const T* __restrict__ xv) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int r0 = 4 * warp; r0 < L; r0 += 4 * BIG_WARPS) {
-        const int nr = L - r0 < 4 ? L - r0 : 4;
-        T* mr[4];
-        T ur[4], wr[4];
+    for (int r0 = RG * warp; r0 < L; r0 += RG * BIG_WARPS) {
+        const int nr = L - r0 < RG ? L - r0 : RG;
+        T* mr[RG];
+        T ur[RG], wr[RG];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < RG; ++q) {
             const int r = r0 + (q < nr ? q : 0);
             mr[q] = M + (size_t)r * ld;
             ur[q] = u[r];
             wr[q] = w ? w[r] : T(0);
         }
         for (int i = lane; i < L; i += 32) {
-            T x[4];
+            T x[RG];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) x[q] = mr[q][i];
+            for (int q = 0; q < RG; ++q) x[q] = mr[q][i];
             const T vi = vv[i], xi = w ? xv[i] : T(0);
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < RG; ++q)
                 if (q < nr) mr[q][i] = x[q] - (ur[q] * vi + wr[q] * xi);
         }
     }
@@ -257,9 +304,18 @@ __device__ void rebuild_fp64(const double* __restrict__ QT, const double* __rest
     }
 }
 
+// Bytes of the per-clique arrays in shared memory for cliques up to ld
+// (rounded up to 16), 16-byte aligned; the trailing-block buffer follows.
+template <typename T>
+__host__ __device__ constexpr size_t big_smem_base(int ld) {
+    return ((size_t)(6 + 2 * QR_SLOTS) * ld * sizeof(T) + (BIG_WARPS + 2) * sizeof(double) +
+            (size_t)ld * sizeof(int) + 15) /
+           16 * 16;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(BIG_NT, 1)
-k_cone_big(DevView V, const int32_t* __restrict__ list, int nlist) {
+k_cone_big(DevView V, const int32_t* __restrict__ list, int nlist, int ldmax, int cap) {
     static_assert(BIG_CHASERS == 32, "warp 0 is the chaser warp");
     const int li = blockIdx.x;
     if (li >= nlist) return;
@@ -278,12 +334,17 @@ k_cone_big(DevView V, const int32_t* __restrict__ list, int nlist) {
     T* hv = e + ld;                          // [ld] Householder vector of the current step
     T* pw = hv + ld;                         // [ld] p, then w; products QT_sub v
     T* beta = pw + ld;                       // [ld] beta_j of every reflection
-    T* rc = beta + ld;                       // [2 ld] rotation cosines (two steps in flight)
-    T* rs = rc + 2 * ld;                     // [2 ld] rotation sines
-    T* lam = rs + 2 * ld;                    // [ld] max(lambda, 0) (0 beyond c)
-    double* red = reinterpret_cast<double*>(lam + ld);   // [BIG_WARPS] (8-byte aligned: 9 ld T's)
-    int* pos = reinterpret_cast<int*>(red + BIG_WARPS);  // [ld] eigenvalues kept (FP64 rebuild)
-    __shared__ int s_lo[2], s_hi[2], s_more, s_steps, s_fail, s_npos;
+    T* lam = beta + ld;                      // [ld] max(lambda, 0) (0 beyond c)
+    T* ring = lam + ld;                      // [QR_SLOTS][2 ld] (cs, sn) of the QR steps in flight
+    double* red = reinterpret_cast<double*>(ring + QR_SLOTS * 2 * ld);   // [BIG_WARPS + 2]
+    T* redT = reinterpret_cast<T*>(red);                 // the same space, as T
+    int* pos = reinterpret_cast<int*>(red + BIG_WARPS + 2);  // [ld] eigenvalues kept (FP64 rebuild)
+    // the trailing blocks of the tridiagonalisation and of the accumulation
+    // of Q move here once they fit (cap elements; the layout above is sized
+    // for the bucket's largest clique, ldmax)
+    T* Sb = reinterpret_cast<T*>(smem_raw + big_smem_base<T>(ldmax));
+    __shared__ int s_lo[QR_SLOTS], s_hi[QR_SLOTS], s_steps, s_fail, s_npos;
+    __shared__ uint64_t full_bar[QR_SLOTS], empty_bar[QR_SLOTS];
 
     T* s = reinterpret_cast<T*>(V.s);
     T* z = reinterpret_cast<T*>(V.z);
@@ -314,100 +375,164 @@ k_cone_big(DevView V, const int32_t* __restrict__ list, int nlist) {
     __syncthreads();
 
     // ---- 1. Householder tridiagonalisation ----
+    // The active matrix is M(i, k) = Mb[(i - mo) ms + (k - mo)]: the
+    // workspace W, then, from the first step whose block (rows and columns
+    // j .. c-1) fits the shared-memory buffer, a copy of that block there.
+    // The Householder vectors also go to their rows of W (the accumulation
+    // reads them from there).
+    T* Mb = W;
+    int ms = ld, mo = 0;
     for (int j = 0; j + 2 < c; ++j) {
         const int L = c - j - 1;
-        T* rowj = W + (size_t)j * ld + j + 1;   // x = A(j, j+1 ..)
+        if (Mb == W && (L + 1) * (L + 1) <= cap) {
+            const int n = L + 1;
+            for (int idx = tid; idx < n * n; idx += BIG_NT) {
+                const int r = idx / n, k2 = idx - (idx / n) * n;
+                Sb[idx] = W[(size_t)(j + r) * ld + j + k2];
+            }
+            __syncthreads();
+            Mb = Sb;
+            ms = n;
+            mo = j;
+        }
+        T* rowj = Mb + (size_t)(j - mo) * ms + (j + 1 - mo);   // x = A(j, j+1 ..)
         T ss = T(0);
         for (int i = tid; i < L; i += BIG_NT) {
             const T xi = rowj[i];
             hv[i] = xi;
             ss += xi * xi;
         }
-        const double nx2 = block_sum<double>((double)ss, red);
-        if (nx2 == 0.0) {   // uniform: nothing to annihilate
-            if (tid == 0) { beta[j] = T(0); e[j] = T(0); d[j] = W[(size_t)j * ld + j]; }
+        const T nx2 = block_sum<T>(ss, redT);
+        if (nx2 == T(0)) {   // uniform: nothing to annihilate
+            if (tid == 0) { beta[j] = T(0); e[j] = T(0); d[j] = Mb[(size_t)(j - mo) * ms + (j - mo)]; }
             __syncthreads();
             continue;
         }
         const T x0 = hv[0];
-        const T nx = (T)sqrt(nx2);
+        const T nx = sqrt(nx2);
         const T alpha = x0 >= T(0) ? -nx : nx;           // H x = alpha e_1
         const T bj = T(1) / (nx * (nx + (x0 >= T(0) ? x0 : -x0)));   // 2 / v^T v
         __syncthreads();                                 // every thread has read hv[0]
         if (tid == 0) hv[0] = x0 - alpha;
         __syncthreads();
         // p = beta B v, B = A(j+1 .., j+1 ..)
-        T* B0 = W + (size_t)(j + 1) * ld + j + 1;
-        rows_matvec<T>(B0, ld, L, hv, bj, pw);
+        T* B0 = Mb + (size_t)(j + 1 - mo) * ms + (j + 1 - mo);
+        rows_matvec<T>(B0, ms, L, hv, bj, pw);
         __syncthreads();
         T pv = T(0);
         for (int i = tid; i < L; i += BIG_NT) pv += pw[i] * hv[i];
-        const T Kc = T(0.5) * bj * (T)block_sum<double>((double)pv, red);
+        const T Kc = T(0.5) * bj * block_sum<T>(pv, redT);
         for (int i = tid; i < L; i += BIG_NT) pw[i] -= Kc * hv[i];   // w
         __syncthreads();
         // B <- B - v w^T - w v^T; row j keeps v
-        rows_update<T>(B0, ld, L, hv, pw, pw, hv);
-        for (int i = tid; i < L; i += BIG_NT) rowj[i] = hv[i];
-        if (tid == 0) { beta[j] = bj; e[j] = alpha; d[j] = W[(size_t)j * ld + j]; }
+        rows_update<T>(B0, ms, L, hv, pw, pw, hv);
+        T* wj = W + (size_t)j * ld + j + 1;
+        for (int i = tid; i < L; i += BIG_NT) wj[i] = hv[i];
+        if (tid == 0) { beta[j] = bj; e[j] = alpha; d[j] = Mb[(size_t)(j - mo) * ms + (j - mo)]; }
         __syncthreads();
     }
     if (tid == 0) {
+        auto M = [&](int i, int k2) { return Mb[(size_t)(i - mo) * ms + (k2 - mo)]; };
         if (c >= 2) {
-            d[c - 2] = W[(size_t)(c - 2) * ld + c - 2];
-            e[c - 2] = W[(size_t)(c - 1) * ld + c - 2];
+            d[c - 2] = M(c - 2, c - 2);
+            e[c - 2] = M(c - 1, c - 2);
         }
-        d[c - 1] = W[(size_t)(c - 1) * ld + c - 1];
+        d[c - 1] = M(c - 1, c - 1);
     }
     __syncthreads();
 
     // ---- 2. QT <- QT H_j for j = c-3 .. 0 (rows and columns j+1 .. of QT) ----
+    // The block grows from the bottom-right corner: rows and columns
+    // qa .. c-1 (the largest block that fits, n = c - qa) are accumulated in
+    // shared memory, then written to QT before the first larger step.
+    int qn = 0;
+    while ((qn + 1) * (qn + 1) <= cap && qn + 1 <= c) ++qn;
+    const int qa = c - qn;
+    for (int idx = tid; idx < qn * qn; idx += BIG_NT) {
+        const int r = idx / qn, k2 = idx - (idx / qn) * qn;
+        Sb[idx] = r == k2 ? T(1) : T(0);
+    }
+    bool flushed = qn == 0;
+    __syncthreads();
     for (int j = c - 3; j >= 0; --j) {
         const T bj = beta[j];
         if (bj == T(0)) continue;   // uniform
         const int L = c - j - 1;
+        T* Q0;
+        int qs;
+        if (j + 1 >= qa) {
+            Q0 = Sb + (size_t)(j + 1 - qa) * qn + (j + 1 - qa);
+            qs = qn;
+        } else {
+            if (!flushed) {
+                for (int idx = tid; idx < qn * qn; idx += BIG_NT) {
+                    const int r = idx / qn, k2 = idx - (idx / qn) * qn;
+                    QT[(size_t)(qa + r) * ld + qa + k2] = Sb[idx];
+                }
+                flushed = true;
+                __syncthreads();
+            }
+            Q0 = QT + (size_t)(j + 1) * ld + j + 1;
+            qs = ld;
+        }
         const T* vj = W + (size_t)j * ld + j + 1;
         for (int i = tid; i < L; i += BIG_NT) hv[i] = vj[i];
         __syncthreads();
-        T* Q0 = QT + (size_t)(j + 1) * ld + j + 1;
-        rows_matvec<T>(Q0, ld, L, hv, bj, pw);
+        rows_matvec<T>(Q0, qs, L, hv, bj, pw);
         __syncthreads();
-        rows_update<T>(Q0, ld, L, pw, hv, (const T*)nullptr, (const T*)nullptr);
+        rows_update<T>(Q0, qs, L, pw, hv, (const T*)nullptr, (const T*)nullptr);
         __syncthreads();
     }
-
-    // ---- 3. implicit QR steps (Wilkinson shift) on (d, e) ----
-    // Phase p: lane 0 of warp 0 chases step p into buffer p & 1 while warps
-    // 1 .. apply step p - 1 from the other buffer to the rows of QT.
-    if (tid == 0) {
-        s_more = 1;
-        s_steps = 0;
-        s_fail = 0;
-        s_lo[0] = s_lo[1] = 0;
-        s_hi[0] = s_hi[1] = -1;   // nothing to apply
+    if (!flushed) {
+        for (int idx = tid; idx < qn * qn; idx += BIG_NT) {
+            const int r = idx / qn, k2 = idx - (idx / qn) * qn;
+            QT[(size_t)(qa + r) * ld + qa + k2] = Sb[idx];
+        }
     }
     __syncthreads();
-    const T eps = QrEps<T>::value;
-    T tnorm = T(0);   // max_k |d_k| + |e_k| + |e_{k-1}| (the absolute floor of the deflation test)
-    int hi = c - 1;        // chaser state (tid 0)
+
+    // ---- 3. implicit QR steps (Wilkinson shift) on (d, e) ----
+    // Lane 0 of warp 0 chases the bulge of each step and writes its
+    // rotations to a ring of QR_SLOTS slots; warps 1 .. apply them to the rows
+    // of QT as they come (each thread owns whole columns of QT, so the
+    // appliers never wait on each other).  full_bar[s]: the slot's step is
+    // written (one arrival, the chaser); empty_bar[s]: every applier warp is
+    // done with it.  Every wait is bounded; one that gives up marks the
+    // clique unconverged and leaves the loop.
     if (tid == 0) {
-        bool finite = true;
-        for (int q = 0; q < c; ++q) {
-            const T a = (d[q] < T(0) ? -d[q] : d[q]) + (q + 1 < c ? (e[q] < T(0) ? -e[q] : e[q]) : T(0)) +
-                        (q > 0 ? (e[q - 1] < T(0) ? -e[q - 1] : e[q - 1]) : T(0));
-            finite = finite && isfinite(a);
-            tnorm = a > tnorm ? a : tnorm;
-        }
-        if (!finite) {   // a non-finite input: no QR steps (the verdict reports it)
-            hi = 0;
-            s_fail = 1;
+        s_steps = 0;
+        s_fail = 0;
+        for (int q = 0; q < QR_SLOTS; ++q) {
+            mbar_init(&full_bar[q], 1);
+            mbar_init(&empty_bar[q], BIG_WARPS - 1);
         }
     }
-    int steps = 0;
-    const int max_steps = 30 * c;
-    for (int p = 0;; ++p) {
-        const int buf = p & 1;
-        if (warp == 0) {
-            if (tid == 0) {
+    __syncthreads();
+    if (warp == 0) {
+        if (tid == 0) {
+            const T eps = QrEps<T>::value;
+            T tnorm = T(0);   // max_k |d_k| + |e_k| + |e_{k-1}| (the absolute floor of the deflation test)
+            int hi = c - 1;
+            bool finite = true;
+            for (int q = 0; q < c; ++q) {
+                const T a = (d[q] < T(0) ? -d[q] : d[q]) + (q + 1 < c ? (e[q] < T(0) ? -e[q] : e[q]) : T(0)) +
+                            (q > 0 ? (e[q - 1] < T(0) ? -e[q - 1] : e[q - 1]) : T(0));
+                finite = finite && isfinite(a);
+                tnorm = a > tnorm ? a : tnorm;
+            }
+            if (!finite) {   // a non-finite input: no QR steps (the verdict reports it)
+                hi = 0;
+                s_fail = 1;
+            }
+            int steps = 0;
+            const int max_steps = 30 * c;
+            int lo_cur = -1;   // start of the unreduced block being reduced (-1: none yet)
+            for (int t = 0;; ++t) {
+                const int slot = t % QR_SLOTS, use = t / QR_SLOTS;
+                if (use > 0 && !mbar_wait(&empty_bar[slot], (use - 1) & 1)) {
+                    s_fail = 1;
+                    break;
+                }
                 int lo = 0;
                 bool step = false;
                 while (hi > 0) {
@@ -426,14 +551,23 @@ k_cone_big(DevView V, const int32_t* __restrict__ list, int nlist) {
                     s_fail = 1;
                 }
                 if (step) {
-                    lo = hi - 1;
-                    while (lo > 0) {
-                        const T ad = (d[lo - 1] < T(0) ? -d[lo - 1] : d[lo - 1]) + (d[lo] < T(0) ? -d[lo] : d[lo]);
-                        const T ae = e[lo - 1] < T(0) ? -e[lo - 1] : e[lo - 1];
-                        if (ae <= eps * ad || ae <= eps * tnorm) break;
-                        --lo;
+                    // the block's start: scanned when a new block begins; within
+                    // a block only the chase changes e, and it reports the
+                    // largest negligible e it leaves (split below)
+                    if (lo_cur < 0 || lo_cur >= hi) {
+                        lo = hi - 1;
+                        while (lo > 0) {
+                            const T ad = (d[lo - 1] < T(0) ? -d[lo - 1] : d[lo - 1]) + (d[lo] < T(0) ? -d[lo] : d[lo]);
+                            const T ae = e[lo - 1] < T(0) ? -e[lo - 1] : e[lo - 1];
+                            if (ae <= eps * ad || ae <= eps * tnorm) break;
+                            --lo;
+                        }
+                        if (lo > 0) e[lo - 1] = T(0);
+                        lo_cur = lo;
                     }
-                    if (lo > 0) e[lo - 1] = T(0);
+                    lo = lo_cur;
+                    int split = lo;   // largest q in (lo, hi) whose final e[q-1] is negligible
+                    T dprev = T(0);   // final d[q-1]
                     // Wilkinson shift: the eigenvalue of the trailing 2 x 2
                     // block closer to d[hi]
                     const T dl = (d[hi - 1] - d[hi]) * T(0.5);
@@ -441,8 +575,7 @@ k_cone_big(DevView V, const int32_t* __restrict__ list, int nlist) {
                     const T hy = qr_hypot(dl, eh);
                     const T mu = d[hi] - eh * (eh / (dl + (dl >= T(0) ? hy : -hy)));
                     T x = d[lo] - mu, zb = e[lo];
-                    T* cb = rc + buf * ld;
-                    T* sb = rs + buf * ld;
+                    T* rt = ring + (size_t)slot * 2 * ld;
                     // the rotated d[q], e[q] are carried in registers; d[q+1],
                     // e[q+1] are still the step's inputs and are loaded ahead
                     T dq = d[lo], eq = e[lo];
@@ -457,10 +590,16 @@ k_cone_big(DevView V, const int32_t* __restrict__ list, int nlist) {
                         const T nd0 = c2 * dq + csb + s2 * dn;
                         const T nd1 = s2 * dq - csb + c2 * dn;
                         const T ne = cs * sn * (dn - dq) + (c2 - s2) * eq;
+                        if (q > lo) {
+                            const T ar = r < T(0) ? -r : r;
+                            const T ad = (dprev < T(0) ? -dprev : dprev) + (nd0 < T(0) ? -nd0 : nd0);
+                            if (ar <= eps * ad || ar <= eps * tnorm) split = q;
+                        }
+                        dprev = nd0;
                         d[q] = nd0;
                         e[q] = ne;
-                        cb[q] = cs;
-                        sb[q] = sn;
+                        rt[2 * q] = cs;
+                        rt[2 * q + 1] = sn;
                         x = ne;
                         zb = sn * en;      // the bulge at (q + 2, q)
                         eq = cs * en;      // e[q + 1] after the row rotation
@@ -469,49 +608,63 @@ k_cone_big(DevView V, const int32_t* __restrict__ list, int nlist) {
                         en = en2;
                     }
                     d[hi] = dq;
+                    if (split > lo) {
+                        e[split - 1] = T(0);
+                        lo_cur = split;
+                    }
                     ++steps;
                 }
-                s_lo[buf] = lo;
-                s_hi[buf] = step ? hi : -1;
-                s_more = step ? 1 : 0;
+                s_lo[slot] = lo;
+                s_hi[slot] = step ? hi : -1;   // -1: no more steps
+                mbar_arrive(&full_bar[slot]);  // release: the slot's writes are visible to the waiters
+                if (!step) break;
             }
-        } else {
-            // apply step p - 1 (buffer buf ^ 1) to rows lo .. hi of QT
-            const int ob = buf ^ 1;
-            const int lo = s_lo[ob], h1 = s_hi[ob];
-            if (p > 0 && h1 >= 0) {
-                const T* cb = rc + ob * ld;
-                const T* sb = rs + ob * ld;
-                constexpr int R = 16;   // rows of a column loaded together
-                for (int i = tid - 32; i < c; i += BIG_NT - 32) {
-                    T* col = QT + i;
-                    T q = col[(size_t)lo * ld];
-                    for (int r0 = lo; r0 < h1; r0 += R) {
-                        const int n = h1 - r0 < R ? h1 - r0 : R;
-                        T nx[R];
+            s_steps = steps;
+        }
+        __syncwarp();
+    } else {
+        using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+        constexpr int R = 16;   // rows of a column loaded together
+        for (int t = 0;; ++t) {
+            const int slot = t % QR_SLOTS, use = t / QR_SLOTS;
+            if (!mbar_wait(&full_bar[slot], use & 1)) {
+                s_fail = 1;
+                break;
+            }
+            const int lo = s_lo[slot], h1 = s_hi[slot];
+            if (h1 < 0) break;
+            const T2* rt = reinterpret_cast<const T2*>(ring + (size_t)slot * 2 * ld);
+            for (int i = tid - 32; i < c; i += BIG_NT - 32) {
+                T* col = QT + i;
+                T q = col[(size_t)lo * ld];
+                // rows r0 + 1 .. r0 + R in nx; the next chunk's rows are
+                // loaded before this chunk's rotations
+                T nx[R];
 #pragma unroll
-                        for (int u = 0; u < R; ++u) nx[u] = u < n ? col[(size_t)(r0 + 1 + u) * ld] : T(0);
+                for (int u = 0; u < R; ++u) nx[u] = lo + 1 + u <= h1 ? col[(size_t)(lo + 1 + u) * ld] : T(0);
+                for (int r0 = lo; r0 < h1; r0 += R) {
+                    const int n = h1 - r0 < R ? h1 - r0 : R;
+                    T nn[R];
 #pragma unroll
-                        for (int u = 0; u < R; ++u) {
-                            if (u < n) {
-                                const T cs = cb[r0 + u], sn = sb[r0 + u];
-                                col[(size_t)(r0 + u) * ld] = cs * q + sn * nx[u];
-                                q = cs * nx[u] - sn * q;
-                            }
+                    for (int u = 0; u < R; ++u) nn[u] = r0 + R + 1 + u <= h1 ? col[(size_t)(r0 + R + 1 + u) * ld] : T(0);
+#pragma unroll
+                    for (int u = 0; u < R; ++u) {
+                        if (u < n) {
+                            const T2 g = rt[r0 + u];
+                            col[(size_t)(r0 + u) * ld] = g.x * q + g.y * nx[u];
+                            q = g.x * nx[u] - g.y * q;
                         }
                     }
-                    col[(size_t)h1 * ld] = q;
+#pragma unroll
+                    for (int u = 0; u < R; ++u) nx[u] = nn[u];
                 }
+                col[(size_t)h1 * ld] = q;
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty_bar[slot]);
         }
-        __syncthreads();
-        if (!s_more) {
-            // the step of this phase was empty; the previous one has been applied
-            break;
-        }
-        __syncthreads();   // s_more read by all before the chaser writes it again
     }
-    if (tid == 0) s_steps = steps;
+    __syncthreads();
 
     // ---- 4. rebuild s = Q max(Lambda, 0) Q^T (lower triangle into W) ----
     for (int q = tid; q < ld; q += BIG_NT) lam[q] = (q < c && d[q] > T(0)) ? d[q] : T(0);
@@ -566,11 +719,10 @@ k_cone_big(DevView V, const int32_t* __restrict__ list, int nlist) {
     }
 }
 
-template <typename T>
-size_t big_smem(int cmax) {
-    const int ld = (cmax + 15) / 16 * 16;
-    return (size_t)9 * ld * sizeof(T) + BIG_WARPS * sizeof(double) + (size_t)ld * sizeof(int);
-}
+// Dynamic shared memory a CTA of the kernel may take in each precision (the
+// opt-in maximum less the kernel's static shared memory; set up once).
+int g_big_dyn[2] = {0, 0};
+
 
 }  // namespace
 
@@ -579,23 +731,42 @@ int64_t cone_big_ws_elems(int c) {
     return 2 * ld * ld;
 }
 
-int cone_big_prepare(bool mixed) {
-    const size_t sm = mixed ? big_smem<float>(CONE_BIG) : big_smem<double>(CONE_BIG);
-    const cudaError_t e = mixed ? cudaFuncSetAttribute(k_cone_big<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)sm)
-                                : cudaFuncSetAttribute(k_cone_big<double>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    return e == cudaSuccess ? HSDE_OK : HSDE_ECUDA;
+template <typename T>
+static int prepare_big() {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, k_cone_big<T>) != cudaSuccess)
+        return HSDE_ECUDA;
+    const int dyn = optin - (int)fa.sharedSizeBytes;
+    if (dyn <= 0 || cudaFuncSetAttribute(k_cone_big<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess)
+        return HSDE_ECUDA;
+    g_big_dyn[sizeof(T) == 4 ? 0 : 1] = dyn;
+    return HSDE_OK;
+}
+
+int cone_big_prepare(bool mixed) { return mixed ? prepare_big<float>() : prepare_big<double>(); }
+
+template <typename T>
+static int launch_big(const DevView& V, const Bucket& bk, cudaStream_t st) {
+    // every CTA takes the whole opt-in shared memory (one clique per SM):
+    // the per-clique arrays for the bucket's largest clique, the rest for
+    // the trailing blocks
+    const int ldmax = (bk.csize_max + 15) / 16 * 16;
+    const size_t base = big_smem_base<T>(ldmax);
+    const int dyn = g_big_dyn[sizeof(T) == 4 ? 0 : 1];
+    if (dyn <= 0 || base > (size_t)dyn) return HSDE_ECUDA;
+    const int cap = (int)(((size_t)dyn - base) / sizeof(T));
+    k_cone_big<T><<<bk.count, BIG_NT, (size_t)dyn, st>>>(V, bk.list, bk.count, ldmax, cap);
+    return HSDE_OK;
 }
 
 int launch_cone_big(const DevView& V, const Bucket& bk, bool mixed, void* stp) {
     if (bk.count == 0) return HSDE_OK;
     if (V.big_ws == nullptr || V.big_off == nullptr) return HSDE_ECUDA;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stp);
-    // shared memory sized for the largest clique the path takes
-    if (mixed) k_cone_big<float><<<bk.count, BIG_NT, big_smem<float>(CONE_BIG), st>>>(V, bk.list, bk.count);
-    else k_cone_big<double><<<bk.count, BIG_NT, big_smem<double>(CONE_BIG), st>>>(V, bk.list, bk.count);
-    return HSDE_OK;
+    return mixed ? launch_big<float>(V, bk, st) : launch_big<double>(V, bk, st);
 }
 
 }  // namespace hsde

@@ -227,6 +227,7 @@ struct Bucket {
     int32_t count;
     int32_t variant;         // 0 latency, 1 throughput, 2 register-V variant (cone.cu)
     int32_t* list;           // device array of clique ids (largest first)
+    int32_t csize_max;       // size of the bucket's largest clique
 };
 
 // ---------------------------------------------------------------------------
