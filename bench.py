@@ -68,7 +68,9 @@ def parse():
     ap.add_argument("--batched-instances", type=int, default=0,
                     help="0: all 256; else the first k instances (smaller profiling case)")
     ap.add_argument("--no-legs", action="store_true", help="skip the n = 50, l = 2000 and gradient legs")
-    ap.add_argument("--only-leg", default="", help="run one leg only: arrow2000, n50, gradient (profiling)")
+    ap.add_argument("--only-leg", default="",
+                    help="run one leg only: arrow2000, n50, gradient, large_clique (profiling)")
+    ap.add_argument("--large-steps", type=int, default=20, help="timed steps of the large-clique leg")
     ap.add_argument("--arrow-l", type=int, default=2000, help="l of the eigensolve-throughput block-arrow leg")
     ap.add_argument("--arrow-d", type=int, default=50)
     ap.add_argument("--arrow-steps", type=int, default=20)
@@ -276,7 +278,9 @@ def phase_roofline(phases, sizes_list, nnzA_list, mixed, traffic_tag=None):
     if dom.startswith("cone_"):
         peak = fp32_peak_tflops(2070.0)
         ach = cone_flops(dom_units) / (dom_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": f"k_cone ({dom}, {'FP32' if mixed else 'FP64'} Jacobi)", "achieved": ach,
+        kern = (f"k_cone_big ({dom}: Householder + implicit QR + split-TF32 rebuild)" if dom == "cone_qr"
+                else f"k_cone ({dom}, {'FP32' if mixed else 'FP64'} Jacobi)")
+        roof = {"bound": "alu", "kernel": kern, "achieved": ach,
                 "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (max SM clock)",
                 "algorithmic_flops_per_launch": cone_flops(dom_units)}
@@ -591,6 +595,50 @@ def arrow_leg(R, args):
                                     dres=infos[0]["dres"])}
 
 
+def large_clique_leg(R, args):
+    """The qpG51-shaped box-QP relaxation (n = 2000, m = 1000, 1691 cliques of
+    1 to 309; 21 above the Jacobi sizes go to the tridiagonal QR path):
+    mixed and FP64 iterations/s, the phase split with the QR bucket's FP32
+    roofline, the mixed run to its verdict, and the oracle's iterations/s on
+    the same instance (one host core)."""
+    import synth
+    t0 = time.perf_counter()
+    p = synth.box_qp_large_clique()
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    H = R.handle(p, precision="mixed", profile=0, max_iter=BIG, eps_tol=NEVER)
+    setup_s = time.perf_counter() - t0
+    sizes = H.sizes[0]
+    K = args.large_steps
+    ms, _ = R.timed_steps(H, K, 3, settle=5)
+    H.close()
+    Hp = R.handle(p, precision="mixed", profile=1, max_iter=BIG, eps_tol=NEVER)
+    _, phases = R.timed_steps(Hp, max(3, K // 2), 2, profile=True, settle=2)
+    Hp.close()
+    roof, phase_us = phase_roofline(phases, [sizes], [int(p.A_ptr[-1])], True)
+    v = K / (ms / 1e3)
+    Hd = R.handle(p, precision="fp64", warm_start=0, max_iter=BIG, eps_tol=NEVER)
+    K64 = 3
+    m64, _ = R.timed_steps(Hd, K64, 1, settle=1)
+    Hd.close()
+    f64 = K64 / (m64 / 1e3)
+    out = {"workload": "box_qp_n2000_E2700 (qpG51 shape)", "n": int(sizes.n), "m": int(sizes.m),
+           "cliques": int(sizes.p), "c_max": int(sizes.c_max), "N_pattern_lower": int(sizes.N),
+           "P_packed": int(sizes.P), "value": v, "unit": UNIT, "steps": K, "ms_per_step": ms / K,
+           "fp64": {"value": f64, "unit": UNIT, "steps": K64, "ms_per_step": m64 / K64},
+           "mixed_over_fp64": v / f64, "setup_s": setup_s, "generate_s": gen_s, "phase_us": phase_us,
+           "roofline": roof}
+    if not args.skip_verdict:
+        st, infos, ttv = R.to_verdict(p, "mixed", chunk=200)
+        out["time_to_verdict"] = dict(verdict=R.hsde.STATUS_NAMES[int(st[0])], iterations=infos[0]["iterations"],
+                                      seconds=ttv, pobj=infos[0]["pobj"], dobj=infos[0]["dobj"],
+                                      pres=infos[0]["pres"], dres=infos[0]["dres"], gap=infos[0]["gap"])
+    if R.rank == 0 and not args.no_cpu_baseline:
+        d = oracle_sample(args.oracle_seconds / 2, warm=1, min_it=2, make="synth.box_qp_large_clique()")
+        out["oracle_1core"] = {"value": d["value"], "unit": UNIT, "iterations": d["iters"], "seconds": d["seconds"]}
+    return out
+
+
 def gradient_leg(R):
     """Gradient of f(C, b) = c^T x_K / (tau_K + kappa_K) after K = 200
     unrolled iterations (checkpoint every 20) on the n = 1000 max-cut grid,
@@ -629,7 +677,8 @@ def run_ours(args):
 
     if args.only_batched or args.only_leg:
         leg = {"batched": lambda: batched_leg(R, args), "arrow2000": lambda: arrow_leg(R, args),
-               "n50": lambda: n50_leg(R), "gradient": lambda: gradient_leg(R)}
+               "n50": lambda: n50_leg(R), "gradient": lambda: gradient_leg(R),
+               "large_clique": lambda: large_clique_leg(R, args)}
         key = "batched" if args.only_batched else args.only_leg
         print(json.dumps({key: leg[key]()}), flush=True)
         return
@@ -642,6 +691,7 @@ def run_ours(args):
         legs["n50"] = n50_leg(R)
         legs["block_arrow"] = arrow_leg(R, args)
         legs["gradient"] = gradient_leg(R)
+        legs["large_clique"] = large_clique_leg(R, args)
 
     mixed_ms, p_ms, w_ms, e2e_s = reduce_max_over_ranks(
         [hl["mixed_ms"], hl["fp64"]["plain"], hl["fp64"]["warm_start"], hl["e2e_s"]], world, R.dev)

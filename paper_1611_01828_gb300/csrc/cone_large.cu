@@ -84,44 +84,41 @@ __device__ __forceinline__ T warp_sum(T v) {
 __device__ __forceinline__ float qr_hypot(float a, float b) { return hypotf(a, b); }
 __device__ __forceinline__ double qr_hypot(double a, double b) { return hypot(a, b); }
 
-// Rotation (cs, sn, r) with cs x + sn z = r = sqrt(x^2 + z^2), -sn x + cs z = 0.
-// FP32: from the reciprocal square root of x^2 + z^2 when that sum is a
-// normal number well inside the range (the chase's critical path), else by
-// hypot; FP64 by hypot and division.
+// Rotation (cs, sn, r) with cs x + sn z = r = sqrt(x^2 + z^2), -sn x + cs z = 0,
+// on the chase's critical path.  The tridiagonal is scaled before the QR
+// steps so that |x|, |z| <= 4, so x^2 + z^2 cannot overflow; a sum below
+// 1e-30 (FP32) or 1e-36 (FP64), both entries negligible against the matrix
+// norm 1, gives the identity rotation.  FP32: the hardware reciprocal square root (no
+// branch); FP64: its FP32 value refined by two Newton steps
+// y <- y (3 - q y^2) / 2 (each doubles the correct digits: ~2^-22 -> 2^-44
+// -> below 2^-53).
+__device__ __forceinline__ float rsqrt_hw(float q) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(q));
+    return y;
+}
 __device__ __forceinline__ void givens(float x, float z, float& cs, float& sn, float& r) {
     const float q = fmaf(x, x, z * z);
-    if (q > 1e-30f && q < 1e30f) {
-        const float iq = rsqrtf(q);
-        cs = x * iq;
-        sn = z * iq;
-        r = q * iq;
-    } else {
-        r = hypotf(x, z);
-        cs = 1.f;
-        sn = 0.f;
-        if (r != 0.f) {
-            cs = x / r;
-            sn = z / r;
-        }
-    }
+    const bool ok = q > 1e-30f;
+    const float iq = rsqrt_hw(ok ? q : 1.f);
+    cs = ok ? x * iq : 1.f;
+    sn = ok ? z * iq : 0.f;
+    r = ok ? q * iq : 0.f;
 }
 __device__ __forceinline__ void givens(double x, double z, double& cs, double& sn, double& r) {
     const double q = fma(x, x, z * z);
-    if (q > 1e-290 && q < 1e290) {
-        const double iq = rsqrt(q);
-        cs = x * iq;
-        sn = z * iq;
-        r = q * iq;
-    } else {
-        r = hypot(x, z);
-        cs = 1.0;
-        sn = 0.0;
-        if (r != 0.0) {
-            cs = x / r;
-            sn = z / r;
-        }
-    }
+    const bool ok = q > 1e-36;   // (float)q stays a normal number
+    const double qq = ok ? q : 1.0;
+    double y = (double)rsqrt_hw((float)qq);
+    y = y * fma(-0.5 * qq, y * y, 1.5);
+    y = y * fma(-0.5 * qq, y * y, 1.5);
+    cs = ok ? x * y : 1.0;
+    sn = ok ? z * y : 0.0;
+    r = ok ? q * y : 0.0;
 }
+
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 
 // mbarrier helpers (CTA scope) for the chase / apply pipeline.  A wait
 // polls at most QR_WAIT_LIMIT times and reports failure instead of
@@ -524,6 +521,21 @@ k_cone_big(DevView V, const int32_t* __restrict__ list, int nlist, int ldmax, in
                 hi = 0;
                 s_fail = 1;
             }
+            // scale (d, e) by a power of two to max_k |d_k| + |e_k| + |e_{k-1}|
+            // in [1, 2) (exact; the eigenvectors do not change, the
+            // eigenvalues are scaled back after the steps)
+            T tsc = T(1);
+            if (finite && tnorm > T(0)) {
+                int ex;
+                frexp(tnorm, &ex);
+                tsc = ldexp(T(1), ex - 1);
+                const T inv = T(1) / tsc;
+                for (int q = 0; q < c; ++q) {
+                    d[q] *= inv;
+                    if (q + 1 < c) e[q] *= inv;
+                }
+                tnorm *= inv;
+            }
             int steps = 0;
             const int max_steps = 30 * c;
             int lo_cur = -1;   // start of the unreduced block being reduced (-1: none yet)
@@ -586,10 +598,13 @@ k_cone_big(DevView V, const int32_t* __restrict__ list, int nlist, int ldmax, in
                         T cs, sn, r;
                         givens(x, zb, cs, sn, r);
                         if (q > lo) e[q - 1] = r;
-                        const T c2 = cs * cs, s2 = sn * sn, csb = T(2) * cs * sn * eq;
-                        const T nd0 = c2 * dq + csb + s2 * dn;
-                        const T nd1 = s2 * dq - csb + c2 * dn;
-                        const T ne = cs * sn * (dn - dq) + (c2 - s2) * eq;
+                        // J^T [[a, b], [b, g]] J with a = dq, b = eq, g = dn:
+                        // d'_q = a + s^2 (g - a) + 2 c s b, d'_{q+1} = a + g - d'_q,
+                        // e'_q = c s (g - a) + (c^2 - s^2) b
+                        const T ga = dn - dq, csn = cs * sn;
+                        const T nd0 = dq + fma_t(sn * sn, ga, T(2) * csn * eq);
+                        const T nd1 = (dq + dn) - nd0;
+                        const T ne = fma_t(csn, ga, (cs - sn) * (cs + sn) * eq);
                         if (q > lo) {
                             const T ar = r < T(0) ? -r : r;
                             const T ad = (dprev < T(0) ? -dprev : dprev) + (nd0 < T(0) ? -nd0 : nd0);
@@ -620,6 +635,7 @@ k_cone_big(DevView V, const int32_t* __restrict__ list, int nlist, int ldmax, in
                 if (!step) break;
             }
             s_steps = steps;
+            for (int q = 0; q < c; ++q) d[q] *= tsc;
         }
         __syncwarp();
     } else {
