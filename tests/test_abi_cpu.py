@@ -44,7 +44,7 @@ def test_default_options(hs):
 def _cases():
     rng = np.random.default_rng(0)
     out = [synth.block_arrow_n50(), synth.block_arrow_n50(True), synth.maxcut_grid(7, 9, rng), synth.differentiation_maxcut_grid(),
-           synth.block_arrow(5, 4, 3, 6, rng), synth.maxcut_grid_instance()]
+           synth.block_arrow(5, 4, 3, 6, rng), synth.maxcut_grid_instance(), synth.box_qp_large_clique()]
     # random sparse patterns with fill
     for seed in range(4):
         n = 30 + 17 * seed
@@ -58,7 +58,7 @@ def _cases():
     return out
 
 
-@pytest.mark.parametrize("k", range(10))
+@pytest.mark.parametrize("k", range(11))
 def test_symbolic_bit_exact_against_oracle(hs, k):
     p = _cases()[k]
     got = hs.hsde_analyze(p)
