@@ -89,7 +89,7 @@ def sweep_stats(phases):
     out["bucket_max"] = {k: round(a[3] / a[2], 2) for k, a in phases.items()
                          if k.startswith("cone_") and a[2]}
     # eigensolver variant of each bucket (the setup autotuner's choice)
-    names = {0: "latency", 1: "throughput", 2: "register-V"}
+    names = {0: "latency", 1: "throughput", 2: "register-V", 3: "warp-QR"}
     out["bucket_variant"] = {k: names.get(v, str(v)) for k, v in phases.get("_variants", {}).items()}
     return out
 
@@ -278,8 +278,12 @@ def phase_roofline(phases, sizes_list, nnzA_list, mixed, traffic_tag=None):
     if dom.startswith("cone_"):
         peak = fp32_peak_tflops(2070.0)
         ach = cone_flops(dom_units) / (dom_ms / 1e3) / 1e12
-        kern = (f"k_cone_big ({dom}: Householder + implicit QR + split-TF32 rebuild)" if dom == "cone_qr"
-                else f"k_cone ({dom}, {'FP32' if mixed else 'FP64'} Jacobi)")
+        if dom == "cone_qr":
+            kern = f"k_cone_big ({dom}: Householder + implicit QR + split-TF32 rebuild)"
+        elif phases.get("_variants", {}).get(dom) == 3:
+            kern = f"k_cone_qrw ({dom}: warp tridiagonal QR, FP32)"
+        else:
+            kern = f"k_cone ({dom}, {'FP32' if mixed else 'FP64'} Jacobi)"
         roof = {"bound": "alu", "kernel": kern, "achieved": ach,
                 "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (max SM clock)",

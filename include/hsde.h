@@ -150,6 +150,17 @@ typedef struct hsde_options {
                              3: always throughput; 4: register-V where the
                              bucket has it.  A bucket of few large cliques
                              always runs the latency variant.               */
+    int32_t eigensolver;  /* HSDE_MIXED cliques of 33 to 64: 0 (default) the
+                             tridiagonal QR with one warp per clique (all in
+                             shared memory) for a bucket of at least three
+                             cliques per SM, Jacobi otherwise (a rule of the
+                             clique count, so the choice and the results do
+                             not depend on timings); 1 Jacobi everywhere;
+                             2 the warp QR wherever it exists.  The two
+                             eigensolvers agree to FP32 rounding, not bitwise:
+                             a batch whose bucket crosses the count threshold
+                             may then differ from its instances run alone in
+                             the last bits.                                  */
 } hsde_options;
 
 typedef struct hsde_sizes {
@@ -201,7 +212,9 @@ typedef struct hsde_profile {
                                                 variant the bucket runs (0
                                                 latency, 1 throughput, 2
                                                 register-V; see
-                                                options.autotune)           */
+                                                options.autotune; 3 the
+                                                warp tridiagonal QR, see
+                                                options.eigensolver)        */
 } hsde_profile;
 
 typedef struct hsde_handle hsde_handle;

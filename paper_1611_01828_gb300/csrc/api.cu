@@ -493,6 +493,15 @@ int choose_variants(hsde_handle* h) {
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
     for (Bucket& bk : h->buckets) {
         bk.variant = 0;
+        // mixed cliques of 33 to 64: the warp tridiagonal QR by a rule of
+        // the clique count (options.eigensolver), not by timing
+        if (h->mixed && cone_qrw_has(bk.cmax)) {
+            const int es = h->opt.eigensolver;
+            if (es == 2 || (es == 0 && (int64_t)bk.count >= (int64_t)QRW_MIN_PER_SM * nsm)) {
+                bk.variant = 3;
+                continue;
+            }
+        }
         bool has[3];
         int nv = 0;
         for (int v = 0; v < 3; ++v) nv += (has[v] = cone_has_variant(bk.cmax, h->mixed, v)) ? 1 : 0;
@@ -548,7 +557,8 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         opt.jacobi_tol < 0 || opt.warm_start < -1 || opt.warm_start > 1 || opt.warm_refresh < 0 ||
         (opt.scaling != 0 && opt.scaling != 1) || (opt.structured_factor != 0 && opt.structured_factor != 1) || !(opt.alpha > 0.0 && opt.alpha < 2.0) ||
         !(opt.scale_norm > 0.0) || !(opt.dual_weight > 0.0) || !std::isfinite(opt.scale_norm) ||
-        !std::isfinite(opt.dual_weight) || opt.autotune < 0 || opt.autotune > 4)
+        !std::isfinite(opt.dual_weight) || opt.autotune < 0 || opt.autotune > 4 || opt.eigensolver < 0 ||
+        opt.eigensolver > 2)
         return fail(HSDE_EINVAL, "invalid options");
 
     auto* h = new hsde_handle();
@@ -1129,6 +1139,7 @@ void hsde_default_options(hsde_options* o) {
     o->scale_norm = 10.0;
     o->dual_weight = 1.5;
     o->autotune = 1;
+    o->eigensolver = 0;
 }
 
 const char* hsde_last_error(void) { return g_err.c_str(); }

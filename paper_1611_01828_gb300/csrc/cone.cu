@@ -1110,6 +1110,7 @@ int launch_cone(const DevView& V, const Bucket& bk, bool mixed, int max_sweeps, 
                 void* stp, int dry) {
     if (bk.count == 0) return HSDE_OK;
     if (bk.cmax == CONE_BIG) return dry ? HSDE_OK : launch_cone_big(V, bk, mixed, stp);
+    if (bk.variant == 3) return dry ? HSDE_OK : (mixed ? launch_cone_qrw(V, bk, stp) : HSDE_ERANGE);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stp);
 #define X(cp, g, gt, gr)                                                                                   \
     if (bk.cmax == cp) {                                                                                   \

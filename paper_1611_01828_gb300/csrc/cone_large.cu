@@ -740,6 +740,338 @@ k_cone_big(DevView V, const int32_t* __restrict__ list, int nlist, int ldmax, in
 int g_big_dyn[2] = {0, 0};
 
 
+
+// ---------------------------------------------------------------------------
+// Tridiagonal QR with one warp per clique, all in shared memory (FP32, the
+// mixed form), for the throughput case: many cliques of 33 to 64.  The
+// serial part of the method (each QR step's bulge chase, one lane) is
+// hidden by the other cliques' warps on the same SM (about fourteen per
+// SM), where the Jacobi sweeps move the whole matrix through shared memory
+// every round.
+//  - the clique matrix in a CP x (CP + 1) buffer (odd stride: a lane per
+//    row or per column is conflict-free);
+//  - Householder tridiagonalisation, a lane per row of the trailing block;
+//  - Q^T formed in place of the reflectors (backward accumulation: before
+//    the step of reflector j, rows and columns j+1 .. hold the product of
+//    the later reflectors, bordered by a unit row and column);
+//  - QR steps as in k_cone_big (lane 0 chases, then every lane applies the
+//    step's rotations to its columns of Q^T);
+//  - the rebuild s = Q max(Lambda, 0) Q^T fused with the scatter: each lane
+//    forms its packed entries from the positive eigenpairs.
+// ---------------------------------------------------------------------------
+template <int CP>
+constexpr size_t qrw_smem() {
+    return (size_t)CP * sizeof(float2) + ((size_t)CP * (CP + 1) + 5 * CP) * sizeof(float);
+}
+
+template <int CP>
+__global__ void __launch_bounds__(32, 16)
+k_cone_qrw(DevView V, const int32_t* __restrict__ list, int nlist) {
+    constexpr int LDA = CP + 1;
+    const int li = blockIdx.x;
+    if (li >= nlist) return;
+    const int k = list[li];
+    const InstDev& I = V.inst[V.cl_inst[k]];
+    if (I.status != HSDE_RUNNING) return;
+    const int lane = threadIdx.x;
+    const int c = V.cl_size[k];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* rot = reinterpret_cast<float2*>(smem_raw);          // [CP] (cs, sn) of the current QR step
+    float* A = reinterpret_cast<float*>(rot + CP);               // [CP x LDA]
+    float* d = A + CP * LDA;                                     // [CP]
+    float* e = d + CP;                                           // [CP]
+    float* beta = e + CP;                                        // [CP]
+    float* hv = beta + CP;                                       // [CP]
+    float* pw = hv + CP;                                         // [CP]
+    int* pos = reinterpret_cast<int*>(hv);                       // eigenvalues kept (after the QR steps)
+    __shared__ int s_lo, s_hi, s_steps, s_fail, s_npos;
+
+    float* s = reinterpret_cast<float*>(V.s);
+    float* z = reinterpret_cast<float*>(V.z);
+    float* v = reinterpret_cast<float*>(V.v);
+    const int nlow = c * (c + 1) / 2;
+    const int64_t off = V.cl_off[k];
+    const double eta = I.eta;
+    const double al = V.alpha;
+
+    // ---- gather + rank-one correction, both triangles ----
+    for (int en = lane; en < nlow; en += 32) {
+        const int b = packed_column(en, c);
+        const int arow = b + (en - (b * c - b * (b - 1) / 2));
+        const int gi = V.gmap[off + en];
+        const double gx = V.xw[gi] - eta * V.xp[gi];
+        float av, vn, hx;
+        cone_inputs<float>(s[off + en], z[off + en], v[off + en], (float)gx, (float)al, V.x, gi, av, vn, hx);
+        A[arow * LDA + b] = av;
+        A[b * LDA + arow] = av;
+    }
+    __syncwarp();
+
+    // ---- Householder tridiagonalisation ----
+    for (int j = 0; j + 2 < c; ++j) {
+        const int L = c - j - 1;
+        const float* rowj = A + j * LDA + j + 1;
+        float ss = 0.f;
+        for (int i = lane; i < L; i += 32) {
+            const float xi = rowj[i];
+            hv[i] = xi;
+            ss = fmaf(xi, xi, ss);
+        }
+        const float nx2 = warp_sum(ss);
+        __syncwarp();
+        if (nx2 == 0.f) {
+            if (lane == 0) { beta[j] = 0.f; e[j] = 0.f; d[j] = A[j * LDA + j]; }
+            __syncwarp();
+            continue;
+        }
+        const float x0 = hv[0];
+        const float nx = sqrtf(nx2);
+        const float alpha = x0 >= 0.f ? -nx : nx;
+        const float bj = 1.f / (nx * (nx + fabsf(x0)));
+        __syncwarp();
+        if (lane == 0) hv[0] = x0 - alpha;
+        __syncwarp();
+        float* B0 = A + (j + 1) * LDA + j + 1;
+        for (int r = lane; r < L; r += 32) {
+            const float* br = B0 + r * LDA;
+            float a = 0.f;
+            for (int i = 0; i < L; ++i) a = fmaf(br[i], hv[i], a);
+            pw[r] = bj * a;
+        }
+        __syncwarp();
+        float pv = 0.f;
+        for (int i = lane; i < L; i += 32) pv = fmaf(pw[i], hv[i], pv);
+        const float Kc = 0.5f * bj * warp_sum(pv);
+        for (int i = lane; i < L; i += 32) pw[i] = fmaf(-Kc, hv[i], pw[i]);
+        __syncwarp();
+        for (int r = lane; r < L; r += 32) {
+            float* br = B0 + r * LDA;
+            const float vr = hv[r], wr = pw[r];
+            for (int i = 0; i < L; ++i) br[i] -= vr * pw[i] + wr * hv[i];
+        }
+        for (int i = lane; i < L; i += 32) A[j * LDA + j + 1 + i] = hv[i];
+        if (lane == 0) { beta[j] = bj; e[j] = alpha; d[j] = A[j * LDA + j]; }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        if (c >= 2) {
+            d[c - 2] = A[(c - 2) * LDA + c - 2];
+            e[c - 2] = A[(c - 1) * LDA + c - 2];
+        }
+        d[c - 1] = A[(c - 1) * LDA + c - 1];
+    }
+    __syncwarp();
+
+    // ---- Q^T in place of the reflectors ----
+    {
+        const int t0 = c >= 2 ? c - 2 : 0, tn = c - t0;
+        for (int idx = lane; idx < tn * tn; idx += 32) {
+            const int r = idx / tn, q = idx - (idx / tn) * tn;
+            A[(t0 + r) * LDA + t0 + q] = r == q ? 1.f : 0.f;
+        }
+        __syncwarp();
+    }
+    for (int j = c - 3; j >= 0; --j) {
+        const int L = c - j - 1;
+        float* Q0 = A + (j + 1) * LDA + j + 1;
+        for (int i = lane; i < L; i += 32) hv[i] = A[j * LDA + j + 1 + i];
+        __syncwarp();
+        for (int i = lane; i < L; i += 32) {
+            Q0[i] = i == 0 ? 1.f : 0.f;
+            Q0[i * LDA] = i == 0 ? 1.f : 0.f;
+        }
+        __syncwarp();
+        const float bj = beta[j];
+        if (bj != 0.f) {
+            for (int r = lane; r < L; r += 32) {
+                const float* qr = Q0 + r * LDA;
+                float a = 0.f;
+                for (int i = 0; i < L; ++i) a = fmaf(qr[i], hv[i], a);
+                pw[r] = bj * a;
+            }
+            __syncwarp();
+            for (int r = lane; r < L; r += 32) {
+                float* qr = Q0 + r * LDA;
+                const float u = pw[r];
+                for (int i = 0; i < L; ++i) qr[i] = fmaf(-u, hv[i], qr[i]);
+            }
+            __syncwarp();
+        }
+    }
+    for (int i = lane; i < c; i += 32) {
+        A[i] = i == 0 ? 1.f : 0.f;
+        A[i * LDA] = i == 0 ? 1.f : 0.f;
+    }
+    if (lane == 0) { s_fail = 0; s_steps = 0; }
+    __syncwarp();
+
+    // ---- implicit QR steps (Wilkinson shift): lane 0 chases, all apply ----
+    const float eps = QrEps<float>::value;
+    float tnorm = 0.f, tsc = 1.f;
+    int hi = c - 1, steps = 0, lo_cur = -1;
+    const int max_steps = 30 * c;
+    if (lane == 0) {
+        bool finite = true;
+        for (int q = 0; q < c; ++q) {
+            const float a = fabsf(d[q]) + (q + 1 < c ? fabsf(e[q]) : 0.f) + (q > 0 ? fabsf(e[q - 1]) : 0.f);
+            finite = finite && isfinite(a);
+            tnorm = fmaxf(tnorm, a);
+        }
+        if (!finite) {
+            hi = 0;
+            s_fail = 1;
+        } else if (tnorm > 0.f) {
+            int ex;
+            frexpf(tnorm, &ex);
+            tsc = ldexpf(1.f, ex - 1);
+            const float inv = 1.f / tsc;
+            for (int q = 0; q < c; ++q) {
+                d[q] *= inv;
+                if (q + 1 < c) e[q] *= inv;
+            }
+            tnorm *= inv;
+        }
+    }
+    for (;;) {
+        if (lane == 0) {
+            int lo = 0;
+            bool step = false;
+            while (hi > 0) {
+                const float ae = fabsf(e[hi - 1]);
+                if (ae <= eps * (fabsf(d[hi - 1]) + fabsf(d[hi])) || ae <= eps * tnorm) {
+                    e[hi - 1] = 0.f;
+                    --hi;
+                    continue;
+                }
+                step = true;
+                break;
+            }
+            if (step && steps >= max_steps) {
+                step = false;
+                s_fail = 1;
+            }
+            if (step) {
+                if (lo_cur < 0 || lo_cur >= hi) {
+                    lo = hi - 1;
+                    while (lo > 0) {
+                        const float ae = fabsf(e[lo - 1]);
+                        if (ae <= eps * (fabsf(d[lo - 1]) + fabsf(d[lo])) || ae <= eps * tnorm) break;
+                        --lo;
+                    }
+                    if (lo > 0) e[lo - 1] = 0.f;
+                    lo_cur = lo;
+                }
+                lo = lo_cur;
+                int split = lo;
+                float dprev = 0.f;
+                const float dl = (d[hi - 1] - d[hi]) * 0.5f;
+                const float eh = e[hi - 1];
+                const float hy = hypotf(dl, eh);
+                const float mu = d[hi] - eh * (eh / (dl + (dl >= 0.f ? hy : -hy)));
+                float x = d[lo] - mu, zb = e[lo];
+                float dq = d[lo], eq = e[lo];
+                float dn = d[lo + 1], en = lo + 1 < hi ? e[lo + 1] : 0.f;
+                for (int q = lo; q < hi; ++q) {
+                    const float dn2 = q + 2 <= hi ? d[q + 2] : 0.f;
+                    const float en2 = q + 2 < hi ? e[q + 2] : 0.f;
+                    float cs, sn, r;
+                    givens(x, zb, cs, sn, r);
+                    if (q > lo) e[q - 1] = r;
+                    const float ga = dn - dq, csn = cs * sn;
+                    const float nd0 = dq + fmaf(sn * sn, ga, 2.f * csn * eq);
+                    const float nd1 = (dq + dn) - nd0;
+                    const float ne = fmaf(csn, ga, (cs - sn) * (cs + sn) * eq);
+                    if (q > lo && (fabsf(r) <= eps * (fabsf(dprev) + fabsf(nd0)) || fabsf(r) <= eps * tnorm))
+                        split = q;
+                    dprev = nd0;
+                    d[q] = nd0;
+                    e[q] = ne;
+                    rot[q] = make_float2(cs, sn);
+                    x = ne;
+                    zb = sn * en;
+                    eq = cs * en;
+                    dq = nd1;
+                    dn = dn2;
+                    en = en2;
+                }
+                d[hi] = dq;
+                if (split > lo) {
+                    e[split - 1] = 0.f;
+                    lo_cur = split;
+                }
+                ++steps;
+            }
+            s_lo = lo;
+            s_hi = step ? hi : -1;
+        }
+        __syncwarp();
+        const int lo = s_lo, h1 = s_hi;
+        if (h1 < 0) break;
+        for (int i = lane; i < c; i += 32) {
+            float q = A[lo * LDA + i];
+            for (int r = lo; r < h1; ++r) {
+                const float nx = A[(r + 1) * LDA + i];
+                const float2 g = rot[r];
+                A[r * LDA + i] = fmaf(g.x, q, g.y * nx);
+                q = fmaf(g.x, nx, -g.y * q);
+            }
+            A[h1 * LDA + i] = q;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        s_steps = steps;
+        for (int q = 0; q < c; ++q) d[q] *= tsc;
+    }
+    __syncwarp();
+
+    // ---- rebuild with the scatter, s, z, v and the stopping-rule partials ----
+    {
+        int base = 0;
+        for (int c0 = 0; c0 < c; c0 += 32) {
+            const int q = c0 + lane;
+            const bool pp = q < c && d[q] > 0.f;
+            const unsigned m = __ballot_sync(0xffffffffu, pp);
+            if (pp) pos[base + __popc(m & ((1u << lane) - 1u))] = q;
+            base += __popc(m);
+        }
+        if (lane == 0) s_npos = base;
+    }
+    __syncwarp();
+    const int npos = s_npos;
+    float res = 0.f, sres = 0.f;
+    for (int en = lane; en < nlow; en += 32) {
+        const int b = packed_column(en, c);
+        const int arow = b + (en - (b * c - b * (b - 1) / 2));
+        float sn = 0.f;
+        for (int t = 0; t < npos; ++t) {
+            const int q = pos[t];
+            const float* qr = A + q * LDA;
+            sn = fmaf(d[q] * qr[arow], qr[b], sn);
+        }
+        const int64_t jj = off + en;
+        const int gi = V.gmap[jj];
+        const double gx = V.xw[gi] - eta * V.xp[gi];
+        float av, vn, hx;
+        cone_inputs<float>(s[jj], z[jj], v[jj], (float)gx, (float)al, V.x, gi, av, vn, hx);
+        s[jj] = sn;
+        z[jj] = sn - av;
+        v[jj] = vn;
+        const float dd = hx - sn;
+        const float w = arow == b ? 1.f : 2.f;
+        res = fmaf(w * dd, dd, res);
+        sres = fmaf(w * sn, sn, sres);
+    }
+    const double rsum = (double)warp_sum(res);
+    const double ssum = (double)warp_sum(sres);
+    if (lane == 0) {
+        V.cl_part[2 * k] = rsum;
+        V.cl_part[2 * k + 1] = ssum;
+        V.cl_sweeps[k] = (s_steps + c - 1) / c;
+        if (s_fail) atomicAdd(&V.inst[V.cl_inst[k]].unconv, 1);
+    }
+}
+
 }  // namespace
 
 int64_t cone_big_ws_elems(int c) {
@@ -783,6 +1115,23 @@ int launch_cone_big(const DevView& V, const Bucket& bk, bool mixed, void* stp) {
     if (V.big_ws == nullptr || V.big_off == nullptr) return HSDE_ECUDA;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stp);
     return mixed ? launch_big<float>(V, bk, st) : launch_big<double>(V, bk, st);
+}
+
+bool cone_qrw_has(int cp) { return cp == 36 || cp == 40 || cp == 44 || cp == 48 || cp == 56 || cp == 64; }
+
+int launch_cone_qrw(const DevView& V, const Bucket& bk, void* stp) {
+    if (bk.count == 0) return HSDE_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stp);
+    switch (bk.cmax) {
+#define QRW(cp)                                                                                     \
+    case cp:                                                                                        \
+        k_cone_qrw<cp><<<bk.count, 32, qrw_smem<cp>(), st>>>(V, bk.list, bk.count);                \
+        return HSDE_OK;
+        QRW(36) QRW(40) QRW(44) QRW(48) QRW(56) QRW(64)
+#undef QRW
+        default:
+            return HSDE_ERANGE;
+    }
 }
 
 }  // namespace hsde

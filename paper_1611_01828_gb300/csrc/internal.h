@@ -225,7 +225,8 @@ constexpr int CONE_BIG = 1024;
 struct Bucket {
     int32_t cmax;            // padded size CP of the bucket (4 ... 112), CONE_BIG for the QR path
     int32_t count;
-    int32_t variant;         // 0 latency, 1 throughput, 2 register-V variant (cone.cu)
+    int32_t variant;         // 0 latency, 1 throughput, 2 register-V variant (cone.cu),
+                             // 3 warp tridiagonal QR (cone_large.cu)
     int32_t* list;           // device array of clique ids (largest first)
     int32_t csize_max;       // size of the bucket's largest clique
 };
@@ -290,6 +291,12 @@ int  cone_prepare(bool mixed);
 int64_t cone_big_ws_elems(int c);
 int  cone_big_prepare(bool mixed);
 int  launch_cone_big(const DevView& V, const Bucket& bk, bool mixed, void* st);
+// tridiagonal QR with one warp per clique (cone_large.cu; FP32, padded
+// sizes 36 ... 64): whether a bucket size has it, and its launch (variant 3)
+bool cone_qrw_has(int cp);
+int  launch_cone_qrw(const DevView& V, const Bucket& bk, void* st);
+// cliques per SM from which options.eigensolver = 0 takes the warp QR
+constexpr int QRW_MIN_PER_SM = 3;
 // reverse mode (unrolled.cu)
 void launch_apply(const DevView& V, const ApplyArgs& A, bool mixed, bool setup_only, void* st);
 int  rev_prepare(bool mixed);

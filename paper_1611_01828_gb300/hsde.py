@@ -40,7 +40,7 @@ class hsde_options(C.Structure):
                 ("jacobi_max_sweeps", C.c_int32), ("use_graph", C.c_int32), ("jacobi_tol", C.c_double),
                 ("profile", C.c_int32), ("warm_start", C.c_int32), ("warm_refresh", C.c_int32),
                 ("scaling", C.c_int32), ("structured_factor", C.c_int32), ("alpha", C.c_double), ("scale_norm", C.c_double),
-                ("dual_weight", C.c_double), ("autotune", C.c_int32)]
+                ("dual_weight", C.c_double), ("autotune", C.c_int32), ("eigensolver", C.c_int32)]
 
 
 class hsde_sizes(C.Structure):

@@ -174,3 +174,70 @@ def test_unrolled_differentiation_rejects_qr_path_cliques(hs):
         with pytest.raises(hs.HSDEError) as ei:
             H.hsde_unrolled_forward(5)
         assert ei.value.code == hs.HSDE_ERANGE
+
+
+# ---------------------------------------------------------------------------
+# the warp tridiagonal QR (one warp per clique, shared memory; mixed cliques
+# of 33 to 64): options.eigensolver = 2 forces it, 1 forces Jacobi, 0 takes
+# it for buckets of at least three cliques per SM
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("c", [33, 41, 55, 64])
+def test_warp_qr_one_step_from_random_state(hs, c):
+    p = synth.block_arrow(3, c - 5, 5, 6, np.random.default_rng(100 + c))
+    ref = ohsde.HSDE(p)
+    state = random_state(ref, np.random.default_rng(13), f32=True)
+    with hs.Handle(p, precision="mixed", eigensolver=2, profile=1) as H:
+        H.hsde_set_state(0, state, 0)
+        H.hsde_iterate(1)
+        got = H.hsde_get_state(0)
+        sz = H.sizes[0]
+        variants = H.hsde_get_profile()["phase_variant"]
+        info = H.hsde_get_info(0)
+    assert 3 in variants.values(), variants
+    assert info["jacobi_unconverged"] == 0
+    u0, nu0 = from_state(ref, state, sz)
+    u1, nu1, _ = ref.step(u0, nu0)
+    close(ref, got, to_state(ref, u1, nu1), 1e-4, f"warp QR, c = {c}")
+
+
+def test_warp_qr_first_iterations_vs_oracle(hs):
+    """The l = 100, d = 50 block-arrow (100 cliques of 55), 20 iterations from
+    the standard start, warp QR forced, against the FP64 oracle."""
+    p = synth.block_arrow_sweep(100, 50)
+    ref = ohsde.HSDE(p)
+    u, nu = ref.initial()
+    for _ in range(20):
+        u, nu, _ = ref.step(u, nu)
+    with hs.Handle(p, precision="mixed", eigensolver=2) as H:
+        H.hsde_iterate(20)
+        close(ref, H.hsde_get_state(0), to_state(ref, u, nu), 1e-4, "warp QR after 20",
+              scalar_scale=inner_product_scale(ref, u))
+
+
+def test_warp_qr_and_jacobi_reach_the_same_verdict(hs):
+    p = synth.block_arrow_sweep(100, 50)
+    out = {}
+    for es in (1, 2):
+        with hs.Handle(p, precision="mixed", eigensolver=es) as H:
+            st = H.solve(chunk=200)
+            out[es] = (int(st[0]), H.hsde_get_info(0))
+    assert out[1][0] == out[2][0] == hs.SOLVED
+    o1, o2 = out[1][1]["pobj"], out[2][1]["pobj"]
+    assert abs(o1 - o2) <= 2e-3 * (1.0 + abs(o1))
+    it1, it2 = out[1][1]["iterations"], out[2][1]["iterations"]
+    assert abs(it1 - it2) <= max(2, 0.1 * it1)
+
+
+def test_warp_qr_default_rule_follows_the_clique_count(hs):
+    """options.eigensolver = 0: the 55-bucket of the l = 500 block-arrow (500
+    cliques, at least three per SM on a 152-SM GB300) runs the warp QR; the
+    l = 100 one (100 cliques) runs Jacobi; eigensolver = 1 keeps Jacobi."""
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    for l, es in ((500, 0), (100, 0), (500, 1)):
+        p = synth.block_arrow_sweep(l, 50)
+        with hs.Handle(p, precision="mixed", eigensolver=es, profile=1) as H:
+            H.hsde_iterate(2)
+            var = H.hsde_get_profile()["phase_variant"]["cone_c56"]
+        want_qr = es == 0 and l >= 3 * nsm
+        assert (var == 3) == want_qr, (l, es, var)
