@@ -588,6 +588,20 @@ def arrow_leg(R, args):
         Hd.close()
         f64[tag] = max(3, K // 4) / (m64 / 1e3)
     st, infos, ttv = R.to_verdict(p, "mixed", chunk=100)
+    # the same with the warp tridiagonal QR instead of the warm-started Jacobi
+    Hq = R.handle(p, precision="mixed", eigensolver=1, profile=0, max_iter=BIG, eps_tol=NEVER)
+    msq, _ = R.timed_steps(Hq, K, 3, settle=20)
+    Hq.close()
+    Hqp = R.handle(p, precision="mixed", eigensolver=1, profile=1, max_iter=BIG, eps_tol=NEVER)
+    _, phq = R.timed_steps(Hqp, max(5, K // 2), 2, profile=True, settle=20)
+    Hqp.close()
+    roof_q, phase_q = phase_roofline(phq, [sizes], [int(p.A_ptr[-1])], True)
+    stq, infq, ttvq = R.to_verdict(p, "mixed", chunk=100, eigensolver=1)
+    warp_qr = {"value": K / (msq / 1e3), "unit": UNIT, "ms_per_step": msq / K, "phase_us": phase_q,
+               "roofline": roof_q,
+               "time_to_verdict": dict(verdict=R.hsde.STATUS_NAMES[int(stq[0])], iterations=infq[0]["iterations"],
+                                       seconds=ttvq, pobj=infq[0]["pobj"], pres=infq[0]["pres"],
+                                       dres=infq[0]["dres"])}
     return {"workload": f"block_arrow_l{l}_d{d}_h5", "n": int(sizes.n), "m": int(sizes.m), "cliques": int(sizes.p),
             "c_max": int(sizes.c_max), "N_pattern_lower": int(sizes.N), "P_packed": int(sizes.P),
             "S_dense": int(sizes.S_dense), "value": v, "unit": UNIT, "steps": K, "ms_per_step": ms / K,
@@ -596,7 +610,8 @@ def arrow_leg(R, args):
             "roofline": roof,
             "time_to_verdict": dict(verdict=R.hsde.STATUS_NAMES[int(st[0])], iterations=infos[0]["iterations"],
                                     seconds=ttv, pobj=infos[0]["pobj"], pres=infos[0]["pres"],
-                                    dres=infos[0]["dres"])}
+                                    dres=infos[0]["dres"]),
+            "warp_qr": warp_qr}
 
 
 def large_clique_leg(R, args):

@@ -151,16 +151,12 @@ typedef struct hsde_options {
                              bucket has it.  A bucket of few large cliques
                              always runs the latency variant.               */
     int32_t eigensolver;  /* HSDE_MIXED cliques of 33 to 64: 0 (default) the
-                             tridiagonal QR with one warp per clique (all in
-                             shared memory) for a bucket of at least three
-                             cliques per SM, Jacobi otherwise (a rule of the
-                             clique count, so the choice and the results do
-                             not depend on timings); 1 Jacobi everywhere;
-                             2 the warp QR wherever it exists.  The two
-                             eigensolvers agree to FP32 rounding, not bitwise:
-                             a batch whose bucket crosses the count threshold
-                             may then differ from its instances run alone in
-                             the last bits.                                  */
+                             warm-started Jacobi; 1 the tridiagonal QR with
+                             one warp per clique, all in shared memory (a
+                             constant cost per iteration: faster than the
+                             Jacobi while the warm start still needs ~3
+                             sweeps a clique, slower once it settles to ~1).
+                             The two agree to FP32 rounding, not bitwise.    */
 } hsde_options;
 
 typedef struct hsde_sizes {

@@ -493,14 +493,11 @@ int choose_variants(hsde_handle* h) {
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
     for (Bucket& bk : h->buckets) {
         bk.variant = 0;
-        // mixed cliques of 33 to 64: the warp tridiagonal QR by a rule of
-        // the clique count (options.eigensolver), not by timing
-        if (h->mixed && cone_qrw_has(bk.cmax)) {
-            const int es = h->opt.eigensolver;
-            if (es == 2 || (es == 0 && (int64_t)bk.count >= (int64_t)QRW_MIN_PER_SM * nsm)) {
-                bk.variant = 3;
-                continue;
-            }
+        // mixed cliques of 33 to 64: the warp tridiagonal QR when asked for
+        // (options.eigensolver = 1)
+        if (h->mixed && cone_qrw_has(bk.cmax) && h->opt.eigensolver == 1) {
+            bk.variant = 3;
+            continue;
         }
         bool has[3];
         int nv = 0;
@@ -558,7 +555,7 @@ int setup_impl(const hsde_problem* P, int32_t B, const hsde_options* O, hsde_han
         (opt.scaling != 0 && opt.scaling != 1) || (opt.structured_factor != 0 && opt.structured_factor != 1) || !(opt.alpha > 0.0 && opt.alpha < 2.0) ||
         !(opt.scale_norm > 0.0) || !(opt.dual_weight > 0.0) || !std::isfinite(opt.scale_norm) ||
         !std::isfinite(opt.dual_weight) || opt.autotune < 0 || opt.autotune > 4 || opt.eigensolver < 0 ||
-        opt.eigensolver > 2)
+        opt.eigensolver > 1)
         return fail(HSDE_EINVAL, "invalid options");
 
     auto* h = new hsde_handle();

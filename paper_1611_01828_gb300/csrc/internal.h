@@ -295,8 +295,6 @@ int  launch_cone_big(const DevView& V, const Bucket& bk, bool mixed, void* st);
 // sizes 36 ... 64): whether a bucket size has it, and its launch (variant 3)
 bool cone_qrw_has(int cp);
 int  launch_cone_qrw(const DevView& V, const Bucket& bk, void* st);
-// cliques per SM from which options.eigensolver = 0 takes the warp QR
-constexpr int QRW_MIN_PER_SM = 3;
 // reverse mode (unrolled.cu)
 void launch_apply(const DevView& V, const ApplyArgs& A, bool mixed, bool setup_only, void* st);
 int  rev_prepare(bool mixed);

@@ -111,7 +111,7 @@ def test_default_options_of_the_practical_form(hs):
 
 @pytest.mark.parametrize("kw", [dict(alpha=0.0), dict(alpha=2.0), dict(scaling=2), dict(scale_norm=0.0),
                                 dict(dual_weight=-1.0), dict(eps_tol=0.0), dict(max_iter=0), dict(autotune=5),
-                                dict(autotune=-1), dict(eigensolver=3), dict(eigensolver=-1)])
+                                dict(autotune=-1), dict(eigensolver=2), dict(eigensolver=-1)])
 def test_invalid_options_rejected_before_any_device_call(hs, kw):
     with pytest.raises(hs.HSDEError) as ei:
         hs.Handle(synth.block_arrow_n50(), **kw)

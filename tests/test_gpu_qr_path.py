@@ -178,15 +178,14 @@ def test_unrolled_differentiation_rejects_qr_path_cliques(hs):
 
 # ---------------------------------------------------------------------------
 # the warp tridiagonal QR (one warp per clique, shared memory; mixed cliques
-# of 33 to 64): options.eigensolver = 2 forces it, 1 forces Jacobi, 0 takes
-# it for buckets of at least three cliques per SM
+# of 33 to 64): options.eigensolver = 1 (the default 0 keeps the Jacobi)
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("c", [33, 41, 55, 64])
 def test_warp_qr_one_step_from_random_state(hs, c):
     p = synth.block_arrow(3, c - 5, 5, 6, np.random.default_rng(100 + c))
     ref = ohsde.HSDE(p)
     state = random_state(ref, np.random.default_rng(13), f32=True)
-    with hs.Handle(p, precision="mixed", eigensolver=2, profile=1) as H:
+    with hs.Handle(p, precision="mixed", eigensolver=1, profile=1) as H:
         H.hsde_set_state(0, state, 0)
         H.hsde_iterate(1)
         got = H.hsde_get_state(0)
@@ -208,7 +207,7 @@ def test_warp_qr_first_iterations_vs_oracle(hs):
     u, nu = ref.initial()
     for _ in range(20):
         u, nu, _ = ref.step(u, nu)
-    with hs.Handle(p, precision="mixed", eigensolver=2) as H:
+    with hs.Handle(p, precision="mixed", eigensolver=1) as H:
         H.hsde_iterate(20)
         close(ref, H.hsde_get_state(0), to_state(ref, u, nu), 1e-4, "warp QR after 20",
               scalar_scale=inner_product_scale(ref, u))
@@ -217,27 +216,28 @@ def test_warp_qr_first_iterations_vs_oracle(hs):
 def test_warp_qr_and_jacobi_reach_the_same_verdict(hs):
     p = synth.block_arrow_sweep(100, 50)
     out = {}
-    for es in (1, 2):
+    for es in (0, 1):
         with hs.Handle(p, precision="mixed", eigensolver=es) as H:
             st = H.solve(chunk=200)
             out[es] = (int(st[0]), H.hsde_get_info(0))
-    assert out[1][0] == out[2][0] == hs.SOLVED
-    o1, o2 = out[1][1]["pobj"], out[2][1]["pobj"]
-    assert abs(o1 - o2) <= 2e-3 * (1.0 + abs(o1))
-    it1, it2 = out[1][1]["iterations"], out[2][1]["iterations"]
-    assert abs(it1 - it2) <= max(2, 0.1 * it1)
+    assert out[0][0] == out[1][0] == hs.SOLVED
+    o0, o1 = out[0][1]["pobj"], out[1][1]["pobj"]
+    assert abs(o0 - o1) <= 2e-3 * (1.0 + abs(o0))
+    it0, it1 = out[0][1]["iterations"], out[1][1]["iterations"]
+    assert abs(it0 - it1) <= max(2, 0.1 * it0)
 
 
-def test_warp_qr_default_rule_follows_the_clique_count(hs):
-    """options.eigensolver = 0: the 55-bucket of the l = 500 block-arrow (500
-    cliques, at least three per SM on a 152-SM GB300) runs the warp QR; the
-    l = 100 one (100 cliques) runs Jacobi; eigensolver = 1 keeps Jacobi."""
-    import torch
-    nsm = torch.cuda.get_device_properties(0).multi_processor_count
-    for l, es in ((500, 0), (100, 0), (500, 1)):
-        p = synth.block_arrow_sweep(l, 50)
-        with hs.Handle(p, precision="mixed", eigensolver=es, profile=1) as H:
+def test_warp_qr_only_when_asked_for(hs):
+    """The default keeps the warm-started Jacobi on every bucket; with
+    eigensolver = 1 the buckets of 33 to 64 run the warp QR and the others
+    (and every FP64 bucket) the Jacobi."""
+    p = synth.block_arrow_sweep(100, 50)
+    q = synth.maxcut_grid(12, 30, np.random.default_rng(2))
+    for prob, es, prec in ((p, 0, "mixed"), (p, 1, "mixed"), (q, 1, "mixed"), (p, 1, "fp64")):
+        with hs.Handle(prob, precision=prec, eigensolver=es, profile=1) as H:
             H.hsde_iterate(2)
-            var = H.hsde_get_profile()["phase_variant"]["cone_c56"]
-        want_qr = es == 0 and l >= 3 * nsm
-        assert (var == 3) == want_qr, (l, es, var)
+            var = H.hsde_get_profile()["phase_variant"]
+        for name, v in var.items():
+            cp = int(name[len("cone_c"):]) if name.startswith("cone_c") else 0
+            want_qr = es == 1 and prec == "mixed" and 33 <= cp <= 64
+            assert (v == 3) == want_qr, (prob.name, es, prec, name, v)
