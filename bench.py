@@ -69,7 +69,7 @@ def parse():
                     help="0: all 256; else the first k instances (smaller profiling case)")
     ap.add_argument("--no-legs", action="store_true", help="skip the n = 50, l = 2000 and gradient legs")
     ap.add_argument("--only-leg", default="",
-                    help="run one leg only: arrow2000, n50, gradient, large_clique (profiling)")
+                    help="run one leg only: arrow2000, n50, gradient, large_clique, sweep (profiling)")
     ap.add_argument("--large-steps", type=int, default=20, help="timed steps of the large-clique leg")
     ap.add_argument("--arrow-l", type=int, default=2000, help="l of the eigensolve-throughput block-arrow leg")
     ap.add_argument("--arrow-d", type=int, default=50)
@@ -614,6 +614,44 @@ def arrow_leg(R, args):
             "warp_qr": warp_qr}
 
 
+def sweep_leg(R, args):
+    """The block-arrow sweep l in {100, 500, 2000} x d in {10, 25, 50} (h = 5,
+    m = 2l, constraints 2j, 2j+1 dense on clique j): mixed and plain-FP64
+    iterations/s (after settling), the mixed run to its verdict, and the FP64
+    run to its verdict for l = 100 (longer FP64 runs would take minutes).
+    One failing entry records its error instead of ending the bench."""
+    import synth
+    out = {}
+    for l in (100, 500, 2000):
+        for d in (10, 25, 50):
+            key = f"l{l}_d{d}"
+            try:
+                p = synth.block_arrow_sweep(l, d)
+                H = R.handle(p, precision="mixed", max_iter=BIG, eps_tol=NEVER)
+                sz = H.sizes[0]
+                K = 10
+                ms, _ = R.timed_steps(H, K, 3, settle=10)
+                H.close()
+                Hd = R.handle(p, precision="fp64", warm_start=0, max_iter=BIG, eps_tol=NEVER)
+                K64 = 3
+                m64, _ = R.timed_steps(Hd, K64, 1, settle=1)
+                Hd.close()
+                row = {"c": int(sz.c_max), "N": int(sz.N), "m": int(sz.m), "S_dense": int(sz.S_dense),
+                       "mixed": K / (ms / 1e3), "fp64_plain": K64 / (m64 / 1e3)}
+                row["mixed_over_fp64"] = row["mixed"] / row["fp64_plain"]
+                st, inf, t = R.to_verdict(p, "mixed", chunk=200)
+                row["mixed_to_verdict"] = dict(verdict=R.hsde.STATUS_NAMES[int(st[0])],
+                                               iterations=inf[0]["iterations"], seconds=t)
+                if l == 100:
+                    st, inf, t = R.to_verdict(p, "fp64", chunk=200)
+                    row["fp64_to_verdict"] = dict(verdict=R.hsde.STATUS_NAMES[int(st[0])],
+                                                  iterations=inf[0]["iterations"], seconds=t)
+                out[key] = row
+            except Exception as ex:   # noqa: BLE001 - recorded, the other entries still run
+                out[key] = {"error": f"{type(ex).__name__}: {ex}"[:300]}
+    return {"workload": "block_arrow_sweep (h = 5, m = 2l)", "unit": UNIT, "entries": out}
+
+
 def large_clique_leg(R, args):
     """The qpG51-shaped box-QP relaxation (n = 2000, m = 1000, 1691 cliques of
     1 to 309; 21 above the Jacobi sizes go to the tridiagonal QR path):
@@ -697,7 +735,7 @@ def run_ours(args):
     if args.only_batched or args.only_leg:
         leg = {"batched": lambda: batched_leg(R, args), "arrow2000": lambda: arrow_leg(R, args),
                "n50": lambda: n50_leg(R), "gradient": lambda: gradient_leg(R),
-               "large_clique": lambda: large_clique_leg(R, args)}
+               "large_clique": lambda: large_clique_leg(R, args), "sweep": lambda: sweep_leg(R, args)}
         key = "batched" if args.only_batched else args.only_leg
         print(json.dumps({key: leg[key]()}), flush=True)
         return
@@ -711,6 +749,7 @@ def run_ours(args):
         legs["block_arrow"] = arrow_leg(R, args)
         legs["gradient"] = gradient_leg(R)
         legs["large_clique"] = large_clique_leg(R, args)
+        legs["block_arrow_sweep"] = sweep_leg(R, args)
 
     mixed_ms, p_ms, w_ms, e2e_s = reduce_max_over_ranks(
         [hl["mixed_ms"], hl["fp64"]["plain"], hl["fp64"]["warm_start"], hl["e2e_s"]], world, R.dev)
