@@ -1,35 +1,43 @@
-// Cone projection of the cliques above the Jacobi bucket sizes (Eq. Step2 on
-// S = S_1 x ... x S_p for the large cliques of Table 1, e.g. the 304-vertex
-// clique of qpG51), fused with the gather, the rank-one correction of
+// Cone projections by tridiagonalisation + implicit QR (Eq. Step2 on
+// S = S_1 x ... x S_p), fused with the gather, the rank-one correction of
 // Eq. MatrixInverseResult and the nu update of Eq. Step3 exactly as the
 // Jacobi kernel in cone.cu does (same per-entry arithmetic, cone_common.cuh).
+// Two kernels:
 //
-// One CTA per clique; the c x c matrix and its eigenvectors live in a
-// per-clique workspace in global memory (L2-resident: 2 ld^2 elements, ld = c
-// rounded up to 16), the tridiagonal and the rotations in shared memory.
-//
+// k_cone_big<T>: the cliques above the Jacobi bucket sizes (the large cliques
+// of Table 1, e.g. the 304-vertex clique of qpG51), up to CONE_BIG.  One CTA
+// of 512 threads per clique; the c x c matrix and Q^T live in a per-clique
+// workspace in global memory (L2-resident: 2 ld^2 elements, ld = c rounded
+// up to 16), the tridiagonal and the rotations in shared memory.
 //  1. Householder tridiagonalisation (Golub & Van Loan, symmetric
 //     Householder tridiagonalisation): for j = 0 .. c-3 the reflection
 //     H_j = I - beta v v^T that zeroes row j beyond j+1 is applied to the
 //     trailing block as B <- B - v w^T - w v^T with p = beta B v,
 //     w = p - (beta p^T v / 2) v.  v is kept in row j of the workspace.
+//     From the first step whose trailing block fits the shared memory left
+//     over, that block is copied there and the steps continue on it.
 //  2. Q = H_0 H_1 ... H_{c-3}, accumulated backwards on Q^T (row k of QT is
-//     eigenvector k): QT_sub <- QT_sub - beta (QT_sub v) v^T.
+//     eigenvector k): QT_sub <- QT_sub - beta (QT_sub v) v^T, in shared
+//     memory while the growing block fits.
 //  3. Implicit symmetric QR with the Wilkinson shift on the tridiagonal
-//     (d, e), deflating from the bottom.  One lane chases the bulge of a
-//     step and records its rotations; the other warps apply the previous
-//     step's rotations to the rows of QT (each thread carries one column
-//     through the chain, coalesced over the threads), so chase and
-//     application overlap.  A step that would exceed 30 c steps in total
-//     stops the solve; the clique is then counted as unconverged.
+//     (d, e), scaled by a power of two to norm [1, 2), deflating from the
+//     bottom.  Lane 0 of warp 0 chases the bulge of each step and writes its
+//     rotations into a ring of QR_SLOTS slots; warps 1 .. apply them to the
+//     rows of QT (each thread carries whole columns through the chain,
+//     coalesced over the threads), meeting the chase on mbarriers whose
+//     waits are bounded.  A step that would exceed 30 c steps in total stops
+//     the solve; the clique is then counted as unconverged.
 //  4. Rebuild s = Q max(Lambda, 0) Q^T on the lower triangle: in FP32 with
 //     tensor cores as split-precision TF32 (each operand a = a_hi + a_lo,
 //     both TF32; a_hi b_hi + a_hi b_lo + a_lo b_hi accumulated in FP32,
 //     which keeps FP32 accuracy), in FP64 by FMA loops.
 //  5. s, z, v and the clique's stopping-rule partials as in cone.cu.
 //
-// The workspace of a clique is private to its CTA; nothing waits on another
-// CTA.
+// k_cone_qrw<CP>: many cliques of 33 to 64 in the mixed form (on request,
+// options.eigensolver): one warp per clique with everything in shared
+// memory (see the comment above it).
+//
+// A clique's workspace is private to its CTA; nothing waits on another CTA.
 #include <cuda_runtime.h>
 
 #include <cstdint>
