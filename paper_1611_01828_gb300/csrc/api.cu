@@ -151,27 +151,61 @@ int prepare(const hsde_problem* P, const hsde_options& O, HostPrep& H, std::stri
     std::vector<std::pair<int32_t, double>> row;
     H.A_col.reserve(m > 0 ? (size_t)(P->A_ptr[m] - a0) : 0);
     H.A_val.reserve(H.A_col.capacity());
+    // pattern position of each entry: a binary search in its column, or,
+    // for the next row of the same column (entries given column by column,
+    // rows ascending), a galloping search on from the previous position
+    const int32_t* pcol = S.pat_colptr.data();
+    const int32_t* prow = S.pat_row.data();
     for (int32_t i = 0; i < m; ++i) {
-        row.clear();
+        const size_t base = H.A_col.size();
         double nrm = 0.0;
+        bool sorted = true;   // entries given in (column, row) order are already in pattern order
+        int32_t cur_c = -1, cur_r = -1, cp = 0, ce = 0, prev_e = INT32_MIN;
         for (int64_t k = P->A_ptr[i] - a0; k < P->A_ptr[i + 1] - a0; ++k) {
             const int32_t r = P->A_row[k], c = P->A_col[k];
-            const int32_t e = S.pos(r, c);
-            row.push_back({e, P->A_val[k]});
+            if (c == cur_c && r > cur_r) {
+                if (cp < ce && prow[cp] < r) {
+                    int32_t lo = cp, step = 1;
+                    while (lo + step < ce && prow[lo + step] < r) {
+                        lo += step;
+                        step <<= 1;
+                    }
+                    const int32_t hi = std::min(lo + step, ce);
+                    cp = (int32_t)(std::lower_bound(prow + lo + 1, prow + hi, r) - prow);
+                }
+            } else {
+                cur_c = c;
+                ce = pcol[c + 1];
+                cp = (int32_t)(std::lower_bound(prow + pcol[c], prow + ce, r) - prow);
+            }
+            cur_r = r;
+            const int32_t e = (cp < ce && prow[cp] == r) ? cp : -1;
+            sorted = sorted && e >= prev_e;
+            prev_e = e;
+            H.A_col.push_back(e);
+            H.A_val.push_back(P->A_val[k]);
             nrm += (r == c ? 1.0 : 2.0) * P->A_val[k] * P->A_val[k];
         }
         if (O.scaling && nrm > 0.0) H.dscale[i] = 1.0 / std::sqrt(nrm);
-        for (auto& pr : row) pr.second *= H.dscale[i];
-        // entries given in (column, row) order are already in pattern order
-        const auto by_e = [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
-            return a.first < b.first;
-        };
-        if (!std::is_sorted(row.begin(), row.end(), by_e)) std::sort(row.begin(), row.end(), by_e);
-        for (auto& pr : row) {
-            H.A_col.push_back(pr.first);
-            H.A_val.push_back(H.diag[pr.first] ? pr.second : 2.0 * pr.second);
+        const double di = H.dscale[i];
+        const size_t end_i = H.A_col.size();
+        if (!sorted) {
+            row.clear();
+            for (size_t j = base; j < end_i; ++j) row.push_back({H.A_col[j], H.A_val[j]});
+            std::sort(row.begin(), row.end(),
+                      [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
+                          return a.first < b.first;
+                      });
+            for (size_t j = base; j < end_i; ++j) {
+                H.A_col[j] = row[j - base].first;
+                H.A_val[j] = row[j - base].second;
+            }
         }
-        H.A_ptr[i + 1] = (int32_t)H.A_col.size();
+        for (size_t j = base; j < end_i; ++j) {
+            const double v = H.A_val[j] * di;
+            H.A_val[j] = H.diag[H.A_col[j]] ? v : 2.0 * v;
+        }
+        H.A_ptr[i + 1] = (int32_t)end_i;
     }
     // internal order of the constraints: by the first pattern entry of each
     // row (stable, so an already ordered problem keeps the identity)
